@@ -1,0 +1,163 @@
+/*
+ * hdp.h - C ABI of the GB300 (sm_103a) implementation of hierarchical
+ * disparity prediction (HDP) stereo matching with non-local tree aggregation,
+ * Luo et al., "Fast Non-local Stereo Matching based on Hierarchical Disparity
+ * Prediction", arXiv 1509.08197.
+ *
+ * Problem statement (Sec. 1 and Sec. 2.1): rectified left/right RGB images and
+ * a disparity bound d in, a disparity map of the left view out.  The method
+ * runs top-down over a graph pyramid of L+1 layers (Sec. 3): at each layer it
+ * predicts per-pixel disparity sets (Sec. 3.1), builds the HDP forest of
+ * disparity trees (Sec. 3.2), aggregates the matching cost over the forest
+ * and takes the winner-takes-all label (Sec. 3.3).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; h_*
+ *     are host pointers owned by the caller.  The context owns its own device
+ *     workspace, allocated once by hdp_create and released by hdp_destroy.
+ *   - All device work is enqueued on the stream given to hdp_create, in order.
+ *     Calls return after enqueueing unless stated otherwise.
+ *   - Every call returns an hdp_status and never aborts the process.  Errors
+ *     raised asynchronously on the device (including a bounded wait that ran
+ *     out, HDP_ERR_TIMEOUT) are reported by the next call that synchronises
+ *     (hdp_sync, the *_host calls, hdp_get_stage) or by hdp_destroy.
+ *     hdp_last_error returns a text description of the last failure.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef HDP_H
+#define HDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdp_ctx hdp_ctx;
+
+typedef enum {
+    HDP_OK = 0,
+    HDP_ERR_ARG = -1,      /* invalid argument: the call did nothing */
+    HDP_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    HDP_ERR_OOM = -3,      /* device allocation failed */
+    HDP_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up */
+    HDP_ERR_STATE = -5     /* calls made in the wrong order */
+} hdp_status;
+
+enum { HDP_TREE_MST = 0, HDP_TREE_ST = 1 };
+enum { HDP_MODE_HDP = 0, HDP_MODE_FULL = 1 };
+enum { HDP_PRIOR_SAMPLED = 0, HDP_PRIOR_UNIFORM = 1 };
+enum { HDP_STORE_FP32 = 0, HDP_STORE_FP16 = 1 };
+
+#define HDP_MAX_LEVELS 8
+#define HDP_MAX_GMM 8
+#define HDP_MAX_DISP 255
+
+/*
+ * Parameters.  Sizes: width, height >= 2; 1 <= max_disp <= 255 (labels
+ * 0..max_disp); 1 <= levels <= 8.
+ *   levels  number of pyramid layers L+1 (Sec. 2.1, S = 2 fixed, as in Sec. 4.1);
+ *           mode HDP_MODE_FULL ignores it and aggregates one full-range layer.
+ *   tree    HDP_TREE_MST (the MST of [MST]) or HDP_TREE_ST (segment tree, [ST]):
+ *           Kruskal merging w <= Int(C) + st_k/|C| for both trees, then linking.
+ *   gamma   Eq. (S): similarity exp(-W/gamma), W in 0..255 intensity units.
+ *   alpha, tau_c, tau_g  matching cost of [Cost2] (Sec. 3.3); 20*alpha,
+ *           3*tau_c and 6*tau_g must be integers (the cost is evaluated exactly).
+ *   beta_num/beta_den  DT-Rule 2 threshold beta (Eq. DTrules) as a rational.
+ *   delta0  Eq. (crtr) threshold, delta_l = delta0 * 2^l (Sec. 4.1).
+ *   prior   P(D_l) sampled on 5x5 squares with a left-right check (Sec. 3.1)
+ *           or uniform.
+ *   gmm_k[l], gmm[l][k] = {pi, mu, sd}: GMM_l of Sec. 2.2 for predicted layer l;
+ *           gmm_k[l] = 0 selects the default single N(0, 1).
+ *   storage cost volume storage: FP32, or FP16 normalised by the per-node
+ *           support mass (arithmetic is FP32 either way).
+ */
+typedef struct {
+    int width, height;
+    int max_disp;
+    int levels;
+    int tree;
+    int mode;
+    float gamma;
+    float alpha, tau_c, tau_g;
+    int st_k;
+    int beta_num, beta_den;
+    double delta0;
+    int prior;
+    int gmm_k[HDP_MAX_LEVELS];
+    double gmm[HDP_MAX_LEVELS][HDP_MAX_GMM][3];
+    int storage;
+} hdp_params;
+
+/* Fill p with the paper's settings (Sec. 4.1) for a width x height image:
+ * S = 2, L = 3 (levels = 4), gamma = 25.5, alpha = 0.9, tau_c = 7, tau_g = 2,
+ * delta0/beta = 0.004/0.95 for images wider than 640 pixels, else 0.064/0.6;
+ * MST, HDP mode, sampled prior, default GMM, FP32 storage, st_k = 1200. */
+void hdp_default_params(hdp_params* p, int width, int height, int max_disp);
+
+/* Validate p, allocate the device workspace for it and bind `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  *out receives the context.
+ * HDP_ERR_ARG on invalid parameters, HDP_ERR_OOM if the workspace does not fit. */
+int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out);
+
+/* Bytes of device workspace held by the context. */
+size_t hdp_workspace_bytes(const hdp_ctx* ctx);
+
+/* Upload stage: read the caller's device images (interleaved RGB uint8, row
+ * pitch `pitch` bytes >= 3*width; they are copied, not retained), build both
+ * graph pyramids (Sec. 2.1) and the tree of the top layer (Sec. 3.2 with
+ * every PixelIntv = [0, d_L]; the only tree that does not depend on a
+ * predicted disparity). */
+int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch);
+
+/* Run every layer top-down (Sec. 3) and write the layer-0 disparity map,
+ * int32 [height][width], to d_disp_out.  Requires hdp_build_trees first. */
+int hdp_match(hdp_ctx* ctx, int32_t* d_disp_out);
+
+/* hdp_build_trees + hdp_match on host buffers: copies h_left/h_right (tightly
+ * packed RGB uint8) to the device, runs, copies the disparity map back into
+ * h_disp_out (int32 [height][width]) and synchronises the stream. */
+int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, int32_t* h_disp_out);
+
+/* Process one layer only (tests and tools): layer `level` must have its input
+ * ready, i.e. hdp_build_trees was called and, for level < L, the disparity map
+ * of level+1 exists (from hdp_run_level(level+1) or hdp_set_stage). */
+int hdp_run_level(hdp_ctx* ctx, int level);
+
+/* Wait for the context's stream; report device-side errors. */
+int hdp_sync(hdp_ctx* ctx);
+
+int hdp_destroy(hdp_ctx* ctx);
+const char* hdp_last_error(const hdp_ctx* ctx);
+
+/* Per-stage inspection and injection for tests.  `what` selects one of the
+ * HDP_STAGE_* buffers of layer `level`; `bytes` must equal its size exactly
+ * (query it with hdp_stage_bytes).  hdp_get_stage synchronises the stream.
+ * Only HDP_STAGE_DISP and HDP_STAGE_PRIOR can be set. */
+enum {
+    HDP_STAGE_PYR_LEFT = 0,   /* int32 [H][W][4]: R,G,B at scale 4^l, horizontal gradient g */
+    HDP_STAGE_PYR_RIGHT = 1,
+    HDP_STAGE_WEIGHTS = 2,    /* int32 [2N]: w of edge id e = 2*(y*W+x)+o, -1 if invalid */
+    HDP_STAGE_EDGES = 3,      /* int32 [count]: edges passing DT-Rule 1, in (w, id) order */
+    HDP_STAGE_IN_TREE = 4,    /* uint8 [2N]: 1 if edge id is in the forest */
+    HDP_STAGE_DT_ROOT = 5,    /* int32 [N]: smallest pixel id of the pixel's tree */
+    HDP_STAGE_TREE_INTV = 6,  /* uint32 [N][8]: TreeIntv of the pixel's tree */
+    HDP_STAGE_BFS = 7,        /* int32 [N]: breadth-first order of the forest */
+    HDP_STAGE_PARENT = 8,     /* int32 [N]: parent pixel, -1 for roots */
+    HDP_STAGE_DEPTH = 9,      /* int32 [N] */
+    HDP_STAGE_PRIOR = 10,     /* int64 [d_l+1]: prior weights (count + 1) */
+    HDP_STAGE_TABLE = 11,     /* uint32 [d_{l+1}+1][8]: PixelIntv per upper label */
+    HDP_STAGE_PIX_SET = 12,   /* int32 [N]: row of the table used by each pixel */
+    HDP_STAGE_COSTS = 13,     /* float [K]: aggregated cost, pixel-major, labels ascending */
+    HDP_STAGE_DISP = 14,      /* int32 [N]: D_l */
+    HDP_STAGE_INFO = 15       /* int64 [16]: K_l, edge count, tree count, engine, ... */
+};
+int64_t hdp_stage_bytes(hdp_ctx* ctx, int level, int what);
+int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, size_t bytes);
+int hdp_set_stage(hdp_ctx* ctx, int level, int what, const void* h_src, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDP_H */
