@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Benchmark of the HDP stereo hot path on one synthetic full-size pair.
+
+Workload: 1390x1110 RGB, disparity range 0-255, 5 pyramid layers, HDP with
+the segment tree, FP32 cost storage (the configuration the throughput metric
+is quoted on).  A step is one whole pass of the method over one pair: both
+pyramids, interval prediction, edge sort, forest, orders, aggregation and WTA
+on every layer, replayed as one CUDA graph with the inputs resident in HBM.
+L2 is flushed (512 MiB write) before every timed step.
+
+value    = aggregated pixel-disparity entries of all layers (sum of
+           |TreeIntv(DT(p))| over pixels and layers) per second, in Mpix*disp/s,
+           over the whole step.
+e2e      = the same through hdp_match_host (host images in, host map out).
+variants = full-range segment tree and FP16 storage on the same pair.
+roofline = the aggregation kernels (up + down pass with WTA) of the headline
+           configuration against the measured HBM copy bandwidth.
+
+--impl reference times the CPU oracle (FP64, one thread) on a bounded crop of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "1390x1110 RGB pair, disparity 0-255, 5 layers, HDP + segment tree (Middlebury-2006-full-size-like synthetic)"
+METRIC = "Mpix*disp aggregated/s and ms per 1390x1110 pair (HDP+ST, FP32)"
+UNIT = "Mpix*disp/s"
+W, H, D, LEVELS = 1390, 1110, 255, 5
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (clock, power, throttle reasons)."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("HDP_BENCH_GLOO") is None else "gloo")
+    return rank, ws
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregated_entries(hdp, ctx, left, right):
+    """Unpadded aggregated entries per layer (sum of |TreeIntv| over pixels), from one eager run."""
+    hdp.hdp_build_trees(ctx, left, right)
+    K = []
+    for l in range(ctx.top, -1, -1):
+        hdp.hdp_run_level(ctx, l)
+        K.append(int(hdp.load().hdp_stage_bytes(ctx.handle, l, hdp.STAGE["costs"])) // 4)
+    hdp.hdp_sync(ctx)
+    return list(reversed(K))   # index = layer
+
+
+def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=False, clocks=False):
+    stream = torch.cuda.Stream(device=dev)
+    ctx = hdp.hdp_create(params, stream)
+    try:
+        left = torch.from_numpy(pair.left).to(dev).contiguous()
+        right = torch.from_numpy(pair.right).to(dev).contiguous()
+        out = torch.empty((params.height, params.width), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            K = aggregated_entries(hdp, ctx, left, right)
+            hdp.hdp_set_timing(ctx, True)
+            n_kernels = hdp.hdp_graph_capture(ctx, left, right, out)
+            for _ in range(warmup):
+                hdp.hdp_graph_launch(ctx)
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            agg_ms, stage_ms = [], []
+            ck = Clocks(dev.index or 0) if clocks else None
+            for i in range(steps):
+                flush.zero_()                      # evict L2 before the step (outside the timed events)
+                ev[i][0].record(stream)
+                hdp.hdp_graph_launch(ctx)
+                ev[i][1].record(stream)
+                t = hdp.hdp_get_timings(ctx)      # synchronises; stage times of this replay
+                stage_ms.append(t)
+                agg_ms.append(float(t[:, 4].sum()))
+            stream.synchronize()
+            clk = ck.stop() if ck else None
+            step_ms = [a.elapsed_time(b) for a, b in ev]
+            D_dev = out.cpu().numpy()
+        e2e = None
+        if want_e2e:
+            hdp.hdp_set_timing(ctx, False)
+            hdp.hdp_match_host(ctx, pair.left, pair.right)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                D_host = hdp.hdp_match_host(ctx, pair.left, pair.right)
+            e2e_s = (time.perf_counter() - t0) / steps
+            assert np.array_equal(D_host, D_dev)
+            e2e = dict(seconds=e2e_s, h2d=pair.left.nbytes + pair.right.nbytes, d2h=D_host.nbytes)
+        return dict(K=K, step_ms=step_ms, agg_ms=agg_ms, stage_ms=np.mean(stage_ms, 0), n_kernels=n_kernels,
+                    e2e=e2e, clocks=clk, D=D_dev)
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def agg_bytes(K, dims, b):
+    """Algorithmic bytes of the two aggregation passes: 5 b per entry (U written once and
+    read twice, C written once and read once) plus 16 B of node data per node and pass."""
+    return sum(5 * b * k + 32 * (w * h) for k, (w, h, _) in zip(K, dims))
+
+
+def cpu_baseline(pair, params_full_hdp, crop=None):
+    from oracle.pipeline import OracleParams, match
+    left, right = pair.left, pair.right
+    if crop:
+        left, right = left[:crop[1], :crop[0]], right[:crop[1], :crop[0]]
+    op = OracleParams(max_disp=D, levels=LEVELS, tree="st", beta=(95, 100), delta0=0.004)
+    t0 = time.perf_counter()
+    _, recs = match(np.ascontiguousarray(left), np.ascontiguousarray(right), op, keep=True)
+    dt = time.perf_counter() - t0
+    K = sum(int(r["agg"]["row_off"][-1]) for r in recs.values())
+    return K, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, ws = dist_init()
+
+    from paper_1509_08197_gb300.scenes import workload_pair
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        pair = workload_pair("full")
+        crop = (695, 555)           # a quarter of the pair: ~seconds of FP64 work per step
+        for _ in range(args.warmup):
+            cpu_baseline(pair, None, crop)
+        Ks, ts = [], []
+        for _ in range(args.steps):
+            K, dt = cpu_baseline(pair, None, crop)
+            Ks.append(K)
+            ts.append(dt)
+        v = sum(Ks) / sum(ts) / 1e6
+        sample = f"oracle HDP+ST, 5 layers, on the top-left 695x555 crop of the pair, {args.steps} steps"
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(ts) / len(ts),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "695x555 crop"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_1509_08197_gb300 as hdp
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    try:
+        hdp.load()
+    except RuntimeError:
+        from paper_1509_08197_gb300 import build
+        build.build()
+        hdp.load()
+    pair = workload_pair("full", index=rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    base = dict(width=W, height=H, max_disp=D, levels=LEVELS, tree="st")
+    head_p = hdp.HDPParams(**base)
+    barrier(ws)
+    head = run_variant(hdp, torch, head_p, pair, args.steps, args.warmup, flush, dev, want_e2e=True, clocks=True)
+    step_ms = float(np.sum(head["step_ms"]))
+    step_ms = reduce_max(step_ms, ws) / args.steps
+    Ktot = sum(head["K"])
+    value = ws * Ktot / (step_ms / 1000.0) / 1e6
+    dims = hdp.Context(None, head_p).dims
+    hbm, peak_kind = peaks()
+    agg_ms = float(np.mean(head["agg_ms"]))
+    abytes = agg_bytes(head["K"], dims, 4)
+    achieved = abytes / (agg_ms / 1000.0) / 1e9
+    e2e = head["e2e"]
+    e2e_v = ws * Ktot / e2e["seconds"] / 1e6
+
+    variants = {}
+    if not args.no_variants:
+        specs = {"hdp_st_fp16": dict(base, storage="fp16"),
+                 "full_st_fp32": dict(base, mode="full", levels=1),
+                 "full_st_fp16": dict(base, mode="full", levels=1, storage="fp16")}
+        for name, kw in specs.items():
+            p = hdp.HDPParams(**kw)
+            r = run_variant(hdp, torch, p, pair, max(3, args.steps // 2), args.warmup, flush, dev)
+            ms = float(np.mean(r["step_ms"]))
+            b = 2 if kw.get("storage") == "fp16" else 4
+            vd = hdp.Context(None, p).dims
+            ag = float(np.mean(r["agg_ms"]))
+            entry = {"ms_per_pair": ms, "value": sum(r["K"]) / (ms / 1000.0) / 1e6,
+                     "aggregated_entries": sum(r["K"]), "aggregation_ms": ag,
+                     "aggregation_hbm_frac": agg_bytes(r["K"], vd, b) / (ag / 1000.0) / 1e9 / hbm,
+                     "stage_ms": {hdp.STAGE_NAMES[k]: float(r["stage_ms"][:, k].sum()) for k in range(5)},
+                     "disparity_agreement_with_headline": float((r["D"] == head["D"]).mean())}
+            variants[name] = entry
+        variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        Kc, tc = cpu_baseline(pair, None)
+        cpu = {"value": Kc / tc / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one whole pair (all 5 layers, {Kc} entries) in {tc:.1f} s, FP64, single thread"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "ms_per_pair": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_gpu": 1, "aggregated_entries_per_layer": head["K"],
+                   "l2": "flushed (512 MiB write) before every timed step", "graph": "one CUDA graph per step",
+                   "parallelism": f"replicas x{ws}"},
+        "stage_ms_per_layer": {hdp.STAGE_NAMES[k]: [float(x) for x in head["stage_ms"][:, k]] for k in range(5)},
+        "roofline": {"bound": "hbm", "kernel": "k_agg (up + down passes with WTA)", "achieved": achieved,
+                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "ms_per_pair": 1000 * e2e["seconds"]},
+        "gpu_launches": head["n_kernels"],
+        "clocks": head["clocks"],
+        "variants": variants,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

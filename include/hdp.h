@@ -131,6 +131,24 @@ int hdp_sync(hdp_ctx* ctx);
 int hdp_destroy(hdp_ctx* ctx);
 const char* hdp_last_error(const hdp_ctx* ctx);
 
+/* Device time of each stage, recorded with CUDA events on the context's
+ * stream while timing is on.  hdp_get_timings synchronises and writes
+ * ms[level * 5 + k] for k = 0 interval prediction, 1 edges + sort, 2 forest,
+ * 3 orders + layout, 4 aggregation + WTA (zero for stages that did not run);
+ * n_floats must be at least 5 * levels. */
+int hdp_set_timing(hdp_ctx* ctx, int on);
+int hdp_get_timings(hdp_ctx* ctx, float* ms, int n_floats);
+
+/* Capture hdp_build_trees + hdp_match on the given device buffers as one CUDA
+ * graph (the context's stream must not be the legacy default stream) and keep
+ * it in the context; *n_kernels receives the number of kernel launches in it.
+ * hdp_graph_launch replays it (same buffers, new contents allowed).  With
+ * timing on at capture time the graph records the stage events, so
+ * hdp_get_timings reports the stages of the last replay. */
+int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch, int32_t* d_disp_out,
+                      int* n_kernels);
+int hdp_graph_launch(hdp_ctx* ctx);
+
 /* Per-stage inspection and injection for tests.  `what` selects one of the
  * HDP_STAGE_* buffers of layer `level`; `bytes` must equal its size exactly
  * (query it with hdp_stage_bytes).  hdp_get_stage synchronises the stream.

@@ -1,0 +1,275 @@
+"""HDP stereo matching on GB300: Python binding of libhdp.so.
+
+The binding only marshals arguments to the C ABI declared in include/hdp.h
+(functions of the same names); every step of the method runs in the CUDA
+library.  There is no CPU fallback: if libhdp.so cannot be loaded the calls
+raise.  Device buffers are passed as torch CUDA tensors (PyTorch provides
+device memory and streams only); host buffers as numpy arrays.
+
+    ctx = hdp_create(params)               # params: HDPParams
+    hdp_build_trees(ctx, left, right)      # torch.uint8 (H, W, 3) on cuda
+    hdp_match(ctx, out)                    # torch.int32 (H, W) on cuda
+    hdp_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libhdp.so")
+
+MAX_LEVELS = 8
+MAX_GMM = 8
+
+HDP_OK, HDP_ERR_ARG, HDP_ERR_CUDA, HDP_ERR_OOM, HDP_ERR_TIMEOUT, HDP_ERR_STATE = 0, -1, -2, -3, -4, -5
+TREE = {"mst": 0, "st": 1}
+MODE = {"hdp": 0, "full": 1}
+PRIOR = {"sampled": 0, "uniform": 1}
+STORAGE = {"fp32": 0, "fp16": 1}
+STAGE = dict(pyr_left=0, pyr_right=1, weights=2, edges=3, in_tree=4, dt_root=5, tree_intv=6, bfs=7, parent=8,
+             depth=9, prior=10, table=11, pix_set=12, costs=13, disp=14, info=15)
+_STAGE_DTYPE = dict(pyr_left=np.int32, pyr_right=np.int32, weights=np.int32, edges=np.int32, in_tree=np.uint8,
+                    dt_root=np.int32, tree_intv=np.uint32, bfs=np.int32, parent=np.int32, depth=np.int32,
+                    prior=np.int64, table=np.uint32, pix_set=np.int32, costs=np.float32, disp=np.int32,
+                    info=np.int64)
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("max_disp", ctypes.c_int),
+                ("levels", ctypes.c_int), ("tree", ctypes.c_int), ("mode", ctypes.c_int),
+                ("gamma", ctypes.c_float), ("alpha", ctypes.c_float), ("tau_c", ctypes.c_float),
+                ("tau_g", ctypes.c_float), ("st_k", ctypes.c_int), ("beta_num", ctypes.c_int),
+                ("beta_den", ctypes.c_int), ("delta0", ctypes.c_double), ("prior", ctypes.c_int),
+                ("gmm_k", ctypes.c_int * MAX_LEVELS),
+                ("gmm", ((ctypes.c_double * 3) * MAX_GMM) * MAX_LEVELS),
+                ("storage", ctypes.c_int)]
+
+
+@dataclass
+class HDPParams:
+    width: int
+    height: int
+    max_disp: int
+    levels: int = 4
+    tree: str = "mst"
+    mode: str = "hdp"
+    gamma: float = 25.5
+    alpha: float = 0.9
+    tau_c: float = 7.0
+    tau_g: float = 2.0
+    st_k: int = 1200
+    beta: tuple = None            # (num, den); default by image width (Sec. 4.1)
+    delta0: float = None
+    prior: str = "sampled"
+    gmm: list = field(default_factory=list)   # per predicted layer: [[pi, mu, sd], ...] or None
+    storage: str = "fp32"
+
+    def to_c(self) -> _Params:
+        large = self.width > 640
+        beta = self.beta if self.beta is not None else ((95, 100) if large else (3, 5))
+        delta0 = self.delta0 if self.delta0 is not None else (0.004 if large else 0.064)
+        p = _Params()
+        p.width, p.height, p.max_disp, p.levels = self.width, self.height, self.max_disp, self.levels
+        p.tree, p.mode = TREE[self.tree], MODE[self.mode]
+        p.gamma, p.alpha, p.tau_c, p.tau_g = self.gamma, self.alpha, self.tau_c, self.tau_g
+        p.st_k = self.st_k
+        p.beta_num, p.beta_den = int(beta[0]), int(beta[1])
+        p.delta0 = float(delta0)
+        p.prior = PRIOR[self.prior]
+        for l, comp in enumerate(self.gmm[:MAX_LEVELS]):
+            if comp is None:
+                continue
+            comp = np.asarray(comp, np.float64).reshape(-1, 3)
+            p.gmm_k[l] = len(comp)
+            for k, (pi, mu, sd) in enumerate(comp):
+                p.gmm[l][k][0], p.gmm[l][k][1], p.gmm[l][k][2] = pi, mu, sd
+        p.storage = STORAGE[self.storage]
+        return p
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhdp.so (build it with paper_1509_08197_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run paper_1509_08197_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    P, I, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sigs = {
+        "hdp_default_params": (None, [P, I, I, I]),
+        "hdp_create": (I, [P, P, P]),
+        "hdp_workspace_bytes": (SZ, [P]),
+        "hdp_build_trees": (I, [P, P, P, I]),
+        "hdp_match": (I, [P, P]),
+        "hdp_match_host": (I, [P, P, P, P]),
+        "hdp_run_level": (I, [P, I]),
+        "hdp_sync": (I, [P]),
+        "hdp_destroy": (I, [P]),
+        "hdp_last_error": (ctypes.c_char_p, [P]),
+        "hdp_stage_bytes": (I64, [P, I, I]),
+        "hdp_get_stage": (I, [P, I, I, P, SZ]),
+        "hdp_set_stage": (I, [P, I, I, P, SZ]),
+        "hdp_set_timing": (I, [P, I]),
+        "hdp_get_timings": (I, [P, P, I]),
+        "hdp_graph_capture": (I, [P, P, P, I, P, P]),
+        "hdp_graph_launch": (I, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class HDPError(RuntimeError):
+    pass
+
+
+class Context:
+    """An hdp_ctx handle with the parameters and layer sizes it was created for."""
+
+    def __init__(self, handle, params: HDPParams):
+        self.handle = handle
+        self.params = params
+        self.dims = []
+        W, H, d = params.width, params.height, params.max_disp
+        n = 1 if params.mode == "full" else params.levels
+        for _ in range(n):
+            self.dims.append((W, H, d))
+            W, H, d = (W + 1) // 2, (H + 1) // 2, d // 2
+
+    @property
+    def top(self):
+        return len(self.dims) - 1
+
+
+def _check(ctx, rc, what):
+    if rc != HDP_OK:
+        msg = load().hdp_last_error(ctx.handle if ctx else None)
+        raise HDPError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hdp_create(params: HDPParams, stream=None) -> Context:
+    L = load()
+    h = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    cp = params.to_c()
+    rc = L.hdp_create(ctypes.byref(cp), s, ctypes.byref(h))
+    if rc != HDP_OK:
+        raise HDPError(f"hdp_create failed ({rc})")
+    return Context(h, params)
+
+
+def hdp_workspace_bytes(ctx: Context) -> int:
+    return load().hdp_workspace_bytes(ctx.handle)
+
+
+def hdp_build_trees(ctx: Context, left, right):
+    """left, right: torch.uint8 (H, W, 3) contiguous CUDA tensors."""
+    W = ctx.params.width
+    _check(ctx, load().hdp_build_trees(ctx.handle, _ptr(left), _ptr(right), 3 * W), "hdp_build_trees")
+
+
+def hdp_match(ctx: Context, out):
+    """out: torch.int32 (H, W) contiguous CUDA tensor."""
+    _check(ctx, load().hdp_match(ctx.handle, _ptr(out)), "hdp_match")
+
+
+def hdp_match_host(ctx: Context, left: np.ndarray, right: np.ndarray, out: np.ndarray = None) -> np.ndarray:
+    H, W = ctx.params.height, ctx.params.width
+    left = np.ascontiguousarray(left, np.uint8)
+    right = np.ascontiguousarray(right, np.uint8)
+    if out is None:
+        out = np.empty((H, W), np.int32)
+    _check(ctx, load().hdp_match_host(ctx.handle, left.ctypes.data, right.ctypes.data, out.ctypes.data),
+           "hdp_match_host")
+    return out
+
+
+def hdp_run_level(ctx: Context, level: int):
+    _check(ctx, load().hdp_run_level(ctx.handle, level), "hdp_run_level")
+
+
+def hdp_sync(ctx: Context):
+    _check(ctx, load().hdp_sync(ctx.handle), "hdp_sync")
+
+
+def hdp_destroy(ctx: Context):
+    if ctx.handle:
+        rc = load().hdp_destroy(ctx.handle)
+        ctx.handle = None
+        if rc != HDP_OK:
+            raise HDPError(f"hdp_destroy reported {rc}")
+
+
+def hdp_get_stage(ctx: Context, level: int, what: str) -> np.ndarray:
+    L = load()
+    n = L.hdp_stage_bytes(ctx.handle, level, STAGE[what])
+    if n < 0:
+        _check(ctx, int(n), f"hdp_stage_bytes({what})")
+    dt = np.dtype(_STAGE_DTYPE[what])
+    out = np.empty(int(n) // dt.itemsize, dt)
+    _check(ctx, L.hdp_get_stage(ctx.handle, level, STAGE[what], out.ctypes.data, int(n)), f"hdp_get_stage({what})")
+    W, H, d = ctx.dims[level]
+    if what in ("pyr_left", "pyr_right"):
+        out = out.reshape(H, W, 4)
+    elif what in ("tree_intv", "table"):
+        out = out.reshape(-1, 8)
+    return out
+
+
+def hdp_set_stage(ctx: Context, level: int, what: str, arr: np.ndarray):
+    dt = np.dtype(_STAGE_DTYPE[what])
+    arr = np.ascontiguousarray(arr, dt)
+    _check(ctx, load().hdp_set_stage(ctx.handle, level, STAGE[what], arr.ctypes.data, arr.nbytes),
+           f"hdp_set_stage({what})")
+
+
+def hdp_set_timing(ctx: Context, on: bool = True):
+    _check(ctx, load().hdp_set_timing(ctx.handle, 1 if on else 0), "hdp_set_timing")
+
+
+STAGE_NAMES = ("interval prediction", "edges + sort", "forest", "orders + layout", "aggregation + WTA")
+
+
+def hdp_get_timings(ctx: Context) -> np.ndarray:
+    """(levels, 5) device milliseconds of each stage of the last run (timing on)."""
+    out = np.zeros(5 * len(ctx.dims), np.float32)
+    _check(ctx, load().hdp_get_timings(ctx.handle, out.ctypes.data, out.size), "hdp_get_timings")
+    return out.reshape(len(ctx.dims), 5)
+
+
+def hdp_graph_capture(ctx: Context, left, right, out) -> int:
+    """Capture build + match on these device buffers as a CUDA graph; returns its kernel count."""
+    n = ctypes.c_int(0)
+    _check(ctx, load().hdp_graph_capture(ctx.handle, _ptr(left), _ptr(right), 3 * ctx.params.width, _ptr(out),
+                                         ctypes.byref(n)), "hdp_graph_capture")
+    return n.value
+
+
+def hdp_graph_launch(ctx: Context):
+    _check(ctx, load().hdp_graph_launch(ctx.handle), "hdp_graph_launch")
+
+
+def exported_symbols():
+    """Names declared in include/hdp.h (for the load/export check)."""
+    return ["hdp_default_params", "hdp_create", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
+            "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
+            "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
+            "hdp_graph_launch"]

@@ -1,0 +1,645 @@
+// C ABI of the HDP library: context, workspace and the per-layer pipeline
+// (Sec. 3: top-down over the layers; per layer interval prediction, forest
+// construction, aggregation and WTA).
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <vector>
+
+#include "hdp_impl.cuh"
+
+struct hdp_ctx {
+    Ctx c;
+    int prior_injected[HDP_MAX_LEVELS] = {};
+    int timing = 0;
+    cudaEvent_t ev[HDP_MAX_LEVELS][6] = {};
+    int ev_used[HDP_MAX_LEVELS][6] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void mark(hdp_ctx* ctx, int l, int k)
+{
+    if (!ctx->timing) return;
+    if (!ctx->ev[l][k]) cudaEventCreate(&ctx->ev[l][k]);
+    cudaEventRecord(ctx->ev[l][k], ctx->c.s);
+    ctx->ev_used[l][k] = 1;
+}
+
+#define TRY_CUDA(call)                                                               \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            ctx->c.err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return e_ == cudaErrorMemoryAllocation ? HDP_ERR_OOM : HDP_ERR_CUDA;     \
+        }                                                                            \
+    } while (0)
+
+static int fail(hdp_ctx* ctx, int code, const std::string& msg)
+{
+    if (ctx) ctx->c.err = msg;
+    return code;
+}
+
+extern "C" void hdp_default_params(hdp_params* p, int width, int height, int max_disp)
+{
+    memset(p, 0, sizeof(*p));
+    p->width = width;
+    p->height = height;
+    p->max_disp = max_disp;
+    p->levels = 4;
+    p->tree = HDP_TREE_MST;
+    p->mode = HDP_MODE_HDP;
+    p->gamma = 25.5f;
+    p->alpha = 0.9f;
+    p->tau_c = 7.0f;
+    p->tau_g = 2.0f;
+    p->st_k = 1200;
+    bool large = width > 640;
+    p->beta_num = large ? 95 : 3;
+    p->beta_den = large ? 100 : 5;
+    p->delta0 = large ? 0.004 : 0.064;
+    p->prior = HDP_PRIOR_SAMPLED;
+    p->storage = HDP_STORE_FP32;
+}
+
+static bool near_int(double v, int* out)
+{
+    double r = std::round(v);
+    if (std::fabs(v - r) > 1e-4) return false;
+    *out = (int)r;
+    return true;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+static T* carve(Ctx& c, size_t count)
+{
+    size_t bytes = align_up(sizeof(T) * (count ? count : 1));
+    T* p = (T*)(c.arena + c.arena_used);
+    c.arena_used += bytes;
+    return p;
+}
+
+// lay out every buffer; with c.arena == nullptr this only measures
+static void layout_buffers(Ctx& c)
+{
+    c.arena_used = 0;
+    const int N0 = c.dim[0].N;
+    const size_t E2 = 2 * (size_t)N0;
+    for (int l = 0; l < c.nlev; ++l) {
+        c.imL[l] = carve<int4>(c, c.dim[l].N);
+        c.imR[l] = carve<int4>(c, c.dim[l].N);
+        c.disp[l] = carve<int32_t>(c, c.dim[l].N);
+        c.prior[l] = carve<long long>(c, 256);
+        c.table[l] = carve<uint32_t>(c, 256 * HDP_WORDS);
+        c.canon[l] = carve<int>(c, 256);
+    }
+    c.stage_l = carve<uint8_t>(c, 3 * (size_t)N0);
+    c.stage_r = carve<uint8_t>(c, 3 * (size_t)N0);
+    c.disp_host_stage = carve<int32_t>(c, N0);
+    c.gmm = carve<double>(c, HDP_MAX_LEVELS * HDP_MAX_GMM * 3);
+    c.gmm_k = carve<int>(c, HDP_MAX_LEVELS);
+    c.full_mask = carve<uint32_t>(c, HDP_MAX_LEVELS * HDP_WORDS);
+    c.pixset = carve<int>(c, N0);
+    c.weights = carve<int>(c, E2);
+    c.keys0 = carve<uint32_t>(c, E2);
+    c.keys1 = carve<uint32_t>(c, E2);
+    c.cls_start = carve<int>(c, E2);
+    c.parent = carve<int>(c, N0);
+    c.csize = carve<int>(c, N0);
+    c.intw = carve<int>(c, N0);
+    c.best = carve<int>(c, N0);
+    c.rootof = carve<int>(c, N0);
+    c.minid = carve<int>(c, N0);
+    c.dtroot = carve<int>(c, N0);
+    c.T = carve<uint32_t>(c, (size_t)N0 * HDP_WORDS);
+    c.in_tree = carve<uint8_t>(c, E2);
+    c.listA = carve<int>(c, E2);
+    c.listB = carve<int>(c, E2);
+    c.raA = carve<int>(c, E2);
+    c.rbA = carve<int>(c, E2);
+    c.raB = carve<int>(c, E2);
+    c.rbB = carve<int>(c, E2);
+    c.hooked = carve<int>(c, N0);
+    c.win = carve<int>(c, 16384);
+    c.wtmp = carve<int>(c, 16384);
+    c.wra = carve<int>(c, 16384);
+    c.wrb = carve<int>(c, 16384);
+    c.wst = carve<int>(c, 16384);
+    c.adj = carve<uint8_t>(c, N0);
+    c.aoff = carve<uint32_t>(c, N0 + 1);
+    c.succ = carve<int>(c, E2);
+    c.val = carve<int>(c, E2);
+    c.succ2 = carve<int>(c, E2);
+    c.val2 = carve<int>(c, E2);
+    c.par = carve<int>(c, N0);
+    c.pdir = carve<int>(c, N0);
+    c.sub = carve<int>(c, N0);
+    c.hdir = carve<int>(c, N0);
+    c.tpos_down = carve<int>(c, N0);
+    c.tpos_up = carve<int>(c, N0);
+    c.vals4 = carve<I4>(c, N0);
+    c.tour = carve<I4>(c, E2);
+    c.tbase = carve<uint32_t>(c, N0);
+    c.nbase = carve<uint32_t>(c, N0);
+    c.depth = carve<int>(c, N0);
+    c.pre2 = carve<int>(c, N0);
+    c.pre3 = carve<int>(c, N0);
+    c.light = carve<int>(c, N0);
+    c.ka = carve<uint32_t>(c, N0 + 1);
+    c.va = carve<uint32_t>(c, N0 + 1);
+    c.kb = carve<uint32_t>(c, N0 + 1);
+    c.vb = carve<uint32_t>(c, N0 + 1);
+    c.bfs = carve<int>(c, N0);
+    c.lay = carve<int>(c, N0);
+    c.rowof = carve<int>(c, N0);
+    c.kp = carve<int>(c, N0);
+    c.roff = carve<uint32_t>(c, N0 + 1);
+    c.rs = carve<float>(c, N0);
+    c.prow = carve<int>(c, N0);
+    c.rdt = carve<int>(c, N0);
+    c.lcoff = carve<uint32_t>(c, N0 + 1);
+    c.lcrow = carve<int>(c, N0);
+    c.nexttop = carve<int>(c, N0);
+    c.ustart_flag = carve<uint32_t>(c, N0);
+    c.uid = carve<uint32_t>(c, N0);
+    c.ubeg = carve<int>(c, N0);
+    c.lvl_first = carve<int>(c, MAX_LIGHT_LEVELS);
+    c.lvl_count = carve<int>(c, MAX_LIGHT_LEVELS);
+    c.tickets = carve<int>(c, 2 * MAX_LIGHT_LEVELS);
+    c.nup = carve<float>(c, N0);
+    c.nfull = carve<float>(c, N0);
+    c.ints = carve<int>(c, IDX_COUNT);
+    c.st = carve<DevStatus>(c, 1);
+    c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
+    c.tmp = carve<uint32_t>(c, c.tmp_words);
+    size_t K = 0;
+    for (int l = 0; l < c.nlev; ++l) {
+        size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
+        K = std::max(K, (size_t)c.dim[l].N * kp);
+    }
+    c.vol_elems = K;
+    if (c.p.storage == HDP_STORE_FP16) c.volh = carve<__half>(c, K + 8);
+    else c.vol = carve<float>(c, K + 8);
+}
+
+extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
+{
+    if (!p || !out) return HDP_ERR_ARG;
+    *out = nullptr;
+    hdp_ctx* ctx = new hdp_ctx();
+    Ctx& c = ctx->c;
+    c.p = *p;
+    c.s = (cudaStream_t)stream;
+    auto bad = [&](const char* m) {
+        fprintf(stderr, "hdp_create: %s\n", m);
+        delete ctx;
+        return HDP_ERR_ARG;
+    };
+    if (p->width < 2 || p->height < 2) return bad("width and height must be >= 2");
+    if (p->max_disp < 1 || p->max_disp > HDP_MAX_DISP) return bad("max_disp must be in 1..255");
+    if (p->levels < 1 || p->levels > HDP_MAX_LEVELS) return bad("levels must be in 1..8");
+    if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST) return bad("unknown tree");
+    if (p->mode != HDP_MODE_HDP && p->mode != HDP_MODE_FULL) return bad("unknown mode");
+    if (!(p->gamma > 0)) return bad("gamma must be > 0");
+    if (!near_int(20.0 * p->alpha, &c.a20) || c.a20 < 0 || c.a20 > 20) return bad("20*alpha must be an integer in 0..20");
+    if (!near_int(3.0 * p->tau_c, &c.tc3) || c.tc3 < 0) return bad("3*tau_c must be a non-negative integer");
+    if (!near_int(6.0 * p->tau_g, &c.tg6) || c.tg6 < 0) return bad("6*tau_g must be a non-negative integer");
+    if (p->st_k < 0) return bad("st_k must be >= 0");
+    if (p->beta_den <= 0 || p->beta_num < 0 || p->beta_num > p->beta_den) return bad("beta must be in [0, 1]");
+    if (!(p->delta0 >= 0.0) || p->delta0 >= 1.0) return bad("delta0 must be in [0, 1)");
+    if (p->prior != HDP_PRIOR_SAMPLED && p->prior != HDP_PRIOR_UNIFORM) return bad("unknown prior");
+    if (p->storage != HDP_STORE_FP32 && p->storage != HDP_STORE_FP16) return bad("unknown storage");
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
+        if (p->gmm_k[l] < 0 || p->gmm_k[l] > HDP_MAX_GMM) return bad("gmm_k out of range");
+        for (int k = 0; k < p->gmm_k[l]; ++k)
+            if (!(p->gmm[l][k][2] > 0)) return bad("gmm standard deviations must be > 0");
+    }
+    if ((long long)p->width * p->height > (1 << 23)) return bad("images above 2^23 pixels are not supported");
+    c.nlev = p->mode == HDP_MODE_FULL ? 1 : p->levels;
+    c.top = c.nlev - 1;
+    int W = p->width, H = p->height, d = p->max_disp;
+    for (int l = 0; l < c.nlev; ++l) {
+        if (d < 0) return bad("too many levels for max_disp");
+        c.dim[l] = LayerDims{W, H, W * H, d};
+        if (8 + 2 * l + edge_bits(W * H) > 32) return bad("edge keys do not fit 32 bits");
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+        d = d / 2;
+    }
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
+        fprintf(stderr, "hdp_create: %s\n", cudaGetErrorString(ce));
+        delete ctx;
+        return HDP_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c.arena = nullptr;
+    layout_buffers(c);
+    c.arena_bytes = c.arena_used;
+    ce = cudaMalloc((void**)&c.arena, c.arena_bytes);
+    if (ce != cudaSuccess) {
+        fprintf(stderr, "hdp_create: cudaMalloc(%zu): %s\n", c.arena_bytes, cudaGetErrorString(ce));
+        cudaGetLastError();
+        delete ctx;
+        return ce == cudaErrorMemoryAllocation ? HDP_ERR_OOM : HDP_ERR_CUDA;
+    }
+    layout_buffers(c);
+    // constants: GMM parameters, full sets
+    std::vector<double> g(HDP_MAX_LEVELS * HDP_MAX_GMM * 3, 0.0);
+    std::vector<int> gk(HDP_MAX_LEVELS, 1);
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
+        if (p->gmm_k[l] == 0) {
+            g[(size_t)l * HDP_MAX_GMM * 3 + 0] = 1.0;
+            g[(size_t)l * HDP_MAX_GMM * 3 + 1] = 0.0;
+            g[(size_t)l * HDP_MAX_GMM * 3 + 2] = 1.0;
+        } else {
+            gk[l] = p->gmm_k[l];
+            for (int k = 0; k < p->gmm_k[l]; ++k)
+                for (int t = 0; t < 3; ++t) g[((size_t)l * HDP_MAX_GMM + k) * 3 + t] = p->gmm[l][k][t];
+        }
+    }
+    std::vector<uint32_t> fm(HDP_MAX_LEVELS * HDP_WORDS, 0u);
+    for (int l = 0; l < c.nlev; ++l)
+        for (int j = 0; j <= c.dim[l].d; ++j) fm[l * HDP_WORDS + (j >> 5)] |= 1u << (j & 31);
+    TRY_CUDA(cudaMemcpy(c.gmm, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(c.gmm_k, gk.data(), gk.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(c.full_mask, fm.data(), fm.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemset(c.st, 0, sizeof(DevStatus)));
+    TRY_CUDA(cudaMemset(c.ints, 0, sizeof(int) * IDX_COUNT));
+    *out = ctx;
+    return HDP_OK;
+}
+
+extern "C" size_t hdp_workspace_bytes(const hdp_ctx* ctx) { return ctx ? ctx->c.arena_bytes : 0; }
+
+static int check_launch(hdp_ctx* ctx, const char* where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, HDP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return HDP_OK;
+}
+
+static void build_layer_tree(hdp_ctx* ctx, int l)
+{
+    Ctx& c = ctx->c;
+    const bool hdp = c.p.mode == HDP_MODE_HDP && l < c.top;
+    launch_edges(c, l, hdp);
+    mark(ctx, l, 2);
+    launch_forest(c, l, hdp);
+    mark(ctx, l, 3);
+    launch_order(c, l);
+    mark(ctx, l, 4);
+    c.tree_level = l;
+}
+
+extern "C" int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!d_left || !d_right || pitch < 3 * c.p.width) return fail(ctx, HDP_ERR_ARG, "bad image pointers or pitch");
+    launch_level0(c, 0, d_left, pitch);
+    launch_level0(c, 1, d_right, pitch);
+    launch_pyramid(c);
+    mark(ctx, c.top, 0);
+    mark(ctx, c.top, 1);
+    build_layer_tree(ctx, c.top);
+    c.built = 1;
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) ctx->prior_injected[l] = 0;
+    return check_launch(ctx, "hdp_build_trees");
+}
+
+extern "C" int hdp_run_level(hdp_ctx* ctx, int level)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.built) return fail(ctx, HDP_ERR_STATE, "hdp_build_trees has not been called");
+    if (level < 0 || level > c.top) return fail(ctx, HDP_ERR_ARG, "level out of range");
+    const bool hdp = c.p.mode == HDP_MODE_HDP && level < c.top;
+    if (hdp || c.tree_level != level) mark(ctx, level, 0);
+    if (hdp) {
+        if (!ctx->prior_injected[level]) launch_prior(c, level);
+        ctx->prior_injected[level] = 0;
+        launch_table(c, level);
+        launch_pixsets(c, level);
+    }
+    if (c.tree_level != level || hdp) {
+        mark(ctx, level, 1);
+        build_layer_tree(ctx, level);
+    }
+    if (!ctx->ev_used[level][4]) mark(ctx, level, 4);
+    launch_aggregate(c, level);
+    mark(ctx, level, 5);
+    return check_launch(ctx, "hdp_run_level");
+}
+
+extern "C" int hdp_match(hdp_ctx* ctx, int32_t* d_disp_out)
+{
+    if (!ctx || !d_disp_out) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.built) return fail(ctx, HDP_ERR_STATE, "hdp_build_trees has not been called");
+    for (int l = c.top; l >= 0; --l) {
+        int rc = hdp_run_level(ctx, l);
+        if (rc) return rc;
+    }
+    TRY_CUDA(cudaMemcpyAsync(d_disp_out, c.disp[0], sizeof(int32_t) * c.dim[0].N, cudaMemcpyDeviceToDevice, c.s));
+    return HDP_OK;
+}
+
+extern "C" int hdp_sync(hdp_ctx* ctx)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    TRY_CUDA(cudaStreamSynchronize(c.s));
+    DevStatus st;
+    TRY_CUDA(cudaMemcpy(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.err == DEV_TIMEOUT) return fail(ctx, HDP_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(st.where) + ")");
+    if (st.err == DEV_BAD_INPUT) return fail(ctx, HDP_ERR_ARG, "invalid device input (site " + std::to_string(st.where) + ")");
+    return HDP_OK;
+}
+
+extern "C" int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, int32_t* h_disp_out)
+{
+    if (!ctx || !h_left || !h_right || !h_disp_out) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    const size_t bytes = 3 * (size_t)c.dim[0].N;
+    TRY_CUDA(cudaMemcpyAsync(c.stage_l, h_left, bytes, cudaMemcpyHostToDevice, c.s));
+    TRY_CUDA(cudaMemcpyAsync(c.stage_r, h_right, bytes, cudaMemcpyHostToDevice, c.s));
+    int rc = hdp_build_trees(ctx, c.stage_l, c.stage_r, 3 * c.p.width);
+    if (rc) return rc;
+    rc = hdp_match(ctx, c.disp_host_stage);
+    if (rc) return rc;
+    TRY_CUDA(cudaMemcpyAsync(h_disp_out, c.disp_host_stage, sizeof(int32_t) * c.dim[0].N, cudaMemcpyDeviceToHost, c.s));
+    return hdp_sync(ctx);
+}
+
+extern "C" int hdp_destroy(hdp_ctx* ctx)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    int rc = HDP_OK;
+    if (ctx->c.arena) {
+        cudaError_t e = cudaStreamSynchronize(ctx->c.s);
+        if (e != cudaSuccess) rc = HDP_ERR_CUDA;
+        else {
+            DevStatus st;
+            if (cudaMemcpy(&st, ctx->c.st, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess && st.err)
+                rc = st.err == DEV_TIMEOUT ? HDP_ERR_TIMEOUT : HDP_ERR_ARG;
+        }
+        cudaFree(ctx->c.arena);
+    }
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        for (int k = 0; k < 6; ++k)
+            if (ctx->ev[l][k]) cudaEventDestroy(ctx->ev[l][k]);
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    delete ctx;
+    return rc;
+}
+
+extern "C" const char* hdp_last_error(const hdp_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+// ------------------------------------------------------------ stages ---
+static int read_int(hdp_ctx* ctx, int idx, int* out)
+{
+    Ctx& c = ctx->c;
+    TRY_CUDA(cudaStreamSynchronize(c.s));
+    TRY_CUDA(cudaMemcpy(out, c.ints + idx, sizeof(int), cudaMemcpyDeviceToHost));
+    return HDP_OK;
+}
+
+static bool tree_stage(int what)
+{
+    return what == HDP_STAGE_WEIGHTS || what == HDP_STAGE_EDGES || what == HDP_STAGE_IN_TREE ||
+           what == HDP_STAGE_DT_ROOT || what == HDP_STAGE_TREE_INTV || what == HDP_STAGE_BFS ||
+           what == HDP_STAGE_PARENT || what == HDP_STAGE_DEPTH || what == HDP_STAGE_COSTS ||
+           what == HDP_STAGE_PIX_SET || what == HDP_STAGE_INFO;
+}
+
+extern "C" int64_t hdp_stage_bytes(hdp_ctx* ctx, int level, int what)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (level < 0 || level > c.top) return HDP_ERR_ARG;
+    const int64_t N = c.dim[level].N;
+    switch (what) {
+    case HDP_STAGE_PYR_LEFT:
+    case HDP_STAGE_PYR_RIGHT: return 16 * N;
+    case HDP_STAGE_WEIGHTS: return 8 * N;
+    case HDP_STAGE_EDGES: {
+        int n = 0;
+        int rc = read_int(ctx, IDX_NEDGES, &n);
+        return rc ? rc : 4 * (int64_t)n;
+    }
+    case HDP_STAGE_IN_TREE: return 2 * N;
+    case HDP_STAGE_DT_ROOT:
+    case HDP_STAGE_BFS:
+    case HDP_STAGE_PARENT:
+    case HDP_STAGE_DEPTH:
+    case HDP_STAGE_PIX_SET:
+    case HDP_STAGE_DISP: return 4 * N;
+    case HDP_STAGE_TREE_INTV: return 32 * N;
+    case HDP_STAGE_PRIOR: return 8 * (int64_t)(c.dim[level].d + 1);
+    case HDP_STAGE_TABLE: return level < c.top ? 32 * (int64_t)(c.dim[level + 1].d + 1) : HDP_ERR_ARG;
+    case HDP_STAGE_COSTS: {
+        if (c.tree_level != level) return HDP_ERR_STATE;
+        TRY_CUDA(cudaStreamSynchronize(c.s));
+        std::vector<int> rdt(N);
+        TRY_CUDA(cudaMemcpy(rdt.data(), c.rdt, 4 * N, cudaMemcpyDeviceToHost));
+        std::vector<uint32_t> T((size_t)N * HDP_WORDS);
+        TRY_CUDA(cudaMemcpy(T.data(), c.T, 32 * N, cudaMemcpyDeviceToHost));
+        int64_t K = 0;
+        for (int64_t i = 0; i < N; ++i)
+            for (int k = 0; k < HDP_WORDS; ++k) K += __builtin_popcount(T[(size_t)rdt[i] * HDP_WORDS + k]);
+        return 4 * K;
+    }
+    case HDP_STAGE_INFO: return 8 * 16;
+    default: return HDP_ERR_ARG;
+    }
+}
+
+extern "C" int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, size_t bytes)
+{
+    if (!ctx || !h_dst) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    int64_t need = hdp_stage_bytes(ctx, level, what);
+    if (need < 0) return (int)need;
+    if ((int64_t)bytes != need) return fail(ctx, HDP_ERR_ARG, "stage size mismatch");
+    if (tree_stage(what) && c.tree_level != level && what != HDP_STAGE_PIX_SET)
+        return fail(ctx, HDP_ERR_STATE, "the work buffers hold another layer");
+    int rc = hdp_sync(ctx);
+    if (rc) return rc;
+    const int N = c.dim[level].N;
+    switch (what) {
+    case HDP_STAGE_PYR_LEFT: TRY_CUDA(cudaMemcpy(h_dst, c.imL[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_PYR_RIGHT: TRY_CUDA(cudaMemcpy(h_dst, c.imR[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_WEIGHTS: TRY_CUDA(cudaMemcpy(h_dst, c.weights, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_EDGES: {
+        std::vector<uint32_t> k(bytes / 4);
+        TRY_CUDA(cudaMemcpy(k.data(), c.sorted, bytes, cudaMemcpyDeviceToHost));
+        uint32_t mask = (1u << edge_bits(N)) - 1u;
+        int32_t* o = (int32_t*)h_dst;
+        for (size_t i = 0; i < k.size(); ++i) o[i] = (int32_t)(k[i] & mask);
+        break;
+    }
+    case HDP_STAGE_IN_TREE: TRY_CUDA(cudaMemcpy(h_dst, c.in_tree, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_DT_ROOT: TRY_CUDA(cudaMemcpy(h_dst, c.dtroot, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_TREE_INTV: {
+        std::vector<int> r(N);
+        std::vector<uint32_t> T((size_t)N * HDP_WORDS);
+        TRY_CUDA(cudaMemcpy(r.data(), c.rootof, 4 * (size_t)N, cudaMemcpyDeviceToHost));
+        TRY_CUDA(cudaMemcpy(T.data(), c.T, 32 * (size_t)N, cudaMemcpyDeviceToHost));
+        uint32_t* o = (uint32_t*)h_dst;
+        for (int v = 0; v < N; ++v)
+            for (int k = 0; k < HDP_WORDS; ++k) o[(size_t)v * HDP_WORDS + k] = T[(size_t)r[v] * HDP_WORDS + k];
+        break;
+    }
+    case HDP_STAGE_BFS: TRY_CUDA(cudaMemcpy(h_dst, c.bfs, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_PARENT: TRY_CUDA(cudaMemcpy(h_dst, c.par, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_DEPTH: TRY_CUDA(cudaMemcpy(h_dst, c.depth, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_PRIOR: TRY_CUDA(cudaMemcpy(h_dst, c.prior[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_TABLE: TRY_CUDA(cudaMemcpy(h_dst, c.table[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_PIX_SET: TRY_CUDA(cudaMemcpy(h_dst, c.pixset, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_DISP: TRY_CUDA(cudaMemcpy(h_dst, c.disp[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_COSTS: {
+        std::vector<int> rowof(N), rdt(N);
+        std::vector<uint32_t> roff(N + 1), T((size_t)N * HDP_WORDS);
+        TRY_CUDA(cudaMemcpy(rowof.data(), c.rowof, 4 * (size_t)N, cudaMemcpyDeviceToHost));
+        TRY_CUDA(cudaMemcpy(rdt.data(), c.rdt, 4 * (size_t)N, cudaMemcpyDeviceToHost));
+        TRY_CUDA(cudaMemcpy(roff.data(), c.roff, 4 * (size_t)N, cudaMemcpyDeviceToHost));
+        TRY_CUDA(cudaMemcpy(T.data(), c.T, 32 * (size_t)N, cudaMemcpyDeviceToHost));
+        int Kp = 0;
+        TRY_CUDA(cudaMemcpy(&Kp, c.ints + IDX_K, sizeof(int), cudaMemcpyDeviceToHost));
+        std::vector<float> vol((size_t)(uint32_t)Kp);
+        std::vector<float> nd;
+        if (c.p.storage == HDP_STORE_FP16) {
+            std::vector<__half> h(vol.size());
+            TRY_CUDA(cudaMemcpy(h.data(), c.volh, 2 * h.size(), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < h.size(); ++i) vol[i] = __half2float(h[i]);
+            nd.resize(N);
+            TRY_CUDA(cudaMemcpy(nd.data(), c.nfull, 4 * (size_t)N, cudaMemcpyDeviceToHost));
+        } else {
+            TRY_CUDA(cudaMemcpy(vol.data(), c.vol, 4 * vol.size(), cudaMemcpyDeviceToHost));
+        }
+        float* o = (float*)h_dst;
+        size_t w = 0;
+        for (int v = 0; v < N; ++v) {
+            int r = rowof[v];
+            int k = 0;
+            for (int t = 0; t < HDP_WORDS; ++t) k += __builtin_popcount(T[(size_t)rdt[r] * HDP_WORDS + t]);
+            float sc = nd.empty() ? 1.f : nd[r];
+            for (int j = 0; j < k; ++j) o[w++] = vol[roff[r] + j] * sc;
+        }
+        break;
+    }
+    case HDP_STAGE_INFO: {
+        int v[IDX_COUNT];
+        TRY_CUDA(cudaMemcpy(v, c.ints, sizeof(v), cudaMemcpyDeviceToHost));
+        int64_t* o = (int64_t*)h_dst;
+        memset(o, 0, 16 * 8);
+        o[0] = (uint32_t)v[IDX_K];
+        o[1] = v[IDX_NEDGES];
+        o[2] = v[IDX_NTREES];
+        o[3] = v[IDX_ENGINE];
+        o[4] = v[IDX_NUNITS];
+        o[5] = v[IDX_RISKY];
+        o[6] = v[IDX_NARCS];
+        o[7] = v[IDX_NCLS];
+        o[8] = v[IDX_NLC];
+        break;
+    }
+    default: return HDP_ERR_ARG;
+    }
+    return HDP_OK;
+}
+
+extern "C" int hdp_set_stage(hdp_ctx* ctx, int level, int what, const void* h_src, size_t bytes)
+{
+    if (!ctx || !h_src) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (level < 0 || level > c.top) return fail(ctx, HDP_ERR_ARG, "level out of range");
+    int64_t need = hdp_stage_bytes(ctx, level, what);
+    if (need < 0) return (int)need;
+    if ((int64_t)bytes != need) return fail(ctx, HDP_ERR_ARG, "stage size mismatch");
+    if (what == HDP_STAGE_DISP) {
+        const int32_t* d = (const int32_t*)h_src;
+        for (int i = 0; i < c.dim[level].N; ++i)
+            if (d[i] < 0 || d[i] > c.dim[level].d) return fail(ctx, HDP_ERR_ARG, "disparity out of range");
+        TRY_CUDA(cudaMemcpyAsync(c.disp[level], h_src, bytes, cudaMemcpyHostToDevice, c.s));
+        TRY_CUDA(cudaStreamSynchronize(c.s));
+        return HDP_OK;
+    }
+    if (what == HDP_STAGE_PRIOR) {
+        TRY_CUDA(cudaMemcpyAsync(c.prior[level], h_src, bytes, cudaMemcpyHostToDevice, c.s));
+        TRY_CUDA(cudaStreamSynchronize(c.s));
+        ctx->prior_injected[level] = 1;
+        return HDP_OK;
+    }
+    return fail(ctx, HDP_ERR_ARG, "stage cannot be set");
+}
+
+extern "C" int hdp_set_timing(hdp_ctx* ctx, int on)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    ctx->timing = on ? 1 : 0;
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        for (int k = 0; k < 6; ++k) ctx->ev_used[l][k] = 0;
+    return HDP_OK;
+}
+
+extern "C" int hdp_get_timings(hdp_ctx* ctx, float* ms, int n)
+{
+    if (!ctx || !ms || n < 5 * ctx->c.nlev) return HDP_ERR_ARG;
+    int rc = hdp_sync(ctx);
+    if (rc) return rc;
+    for (int l = 0; l < ctx->c.nlev; ++l)
+        for (int k = 0; k < 5; ++k) {
+            float t = 0.f;
+            if (ctx->ev_used[l][k] && ctx->ev_used[l][k + 1]) cudaEventElapsedTime(&t, ctx->ev[l][k], ctx->ev[l][k + 1]);
+            ms[l * 5 + k] = t;
+        }
+    return HDP_OK;
+}
+
+extern "C" int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch,
+                                 int32_t* d_out, int* n_kernels)
+{
+    if (!ctx || !d_out) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.s) return fail(ctx, HDP_ERR_ARG, "graph capture needs a non-default stream");
+    if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        for (int k = 0; k < 6; ++k) ctx->ev_used[l][k] = 0;
+    TRY_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+    int rc = hdp_build_trees(ctx, d_left, d_right, pitch);
+    if (!rc) rc = hdp_match(ctx, d_out);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c.s, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, HDP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    ctx->graph = g;
+    size_t nn = 0;
+    TRY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    TRY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    if (n_kernels) *n_kernels = k;
+    TRY_CUDA(cudaGraphInstantiate(&ctx->exec, g, 0));
+    return HDP_OK;
+}
+
+extern "C" int hdp_graph_launch(hdp_ctx* ctx)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    if (!ctx->exec) return fail(ctx, HDP_ERR_STATE, "no captured graph");
+    TRY_CUDA(cudaGraphLaunch(ctx->exec, ctx->c.s));
+    return HDP_OK;
+}

@@ -1,0 +1,147 @@
+// Internal state of an HDP context and the per-stage launchers.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/hdp.h"
+#include "common.cuh"
+#include "prims.cuh"
+
+#define MAX_LIGHT_LEVELS 32
+
+struct LayerDims {
+    int W, H, N, d;   // size and largest label of the layer
+};
+
+// Per-layer cost arithmetic: Mq = A * min(sum|dI|, Tc) + B * min(|dg|, Tg) and
+// M = Mq * inv (the matching cost in 0..255 intensity units), exact integers.
+struct CostK {
+    int A, B, Tc, Tg;
+    float inv;
+};
+
+struct Ctx {
+    hdp_params p;
+    cudaStream_t s = nullptr;
+    int nlev = 0;     // layers processed
+    int top = 0;      // index of the top layer
+    LayerDims dim[HDP_MAX_LEVELS];
+    int num_sms = 0;
+    int a20 = 0, tc3 = 0, tg6 = 0;
+
+    // arena
+    char* arena = nullptr;
+    size_t arena_bytes = 0, arena_used = 0;
+
+    // images: int4 (R, G, B at scale 4^l, horizontal gradient g)
+    int4* imL[HDP_MAX_LEVELS] = {};
+    int4* imR[HDP_MAX_LEVELS] = {};
+    uint8_t* stage_l = nullptr;   // upload buffers (tightly packed RGB)
+    uint8_t* stage_r = nullptr;
+    int32_t* disp[HDP_MAX_LEVELS] = {};
+    int32_t* disp_host_stage = nullptr;
+
+    // interval prediction (layers below the top)
+    long long* prior[HDP_MAX_LEVELS] = {};
+    uint32_t* table[HDP_MAX_LEVELS] = {};
+    int* canon[HDP_MAX_LEVELS] = {};
+    double* gmm = nullptr;   // [HDP_MAX_LEVELS][HDP_MAX_GMM][3]
+    int* gmm_k = nullptr;    // [HDP_MAX_LEVELS]
+    uint32_t* full_mask = nullptr;   // per layer: the set {0..d_l}  [HDP_MAX_LEVELS][8]
+
+    // work buffers, sized for layer 0 and reused by every layer
+    int* pixset = nullptr;           // table row of each pixel (null use: full range)
+    int* weights = nullptr;          // [2N] edge weights (-1 invalid)
+    uint32_t *keys0 = nullptr, *keys1 = nullptr;   // sorted (w << ebits | e)
+    uint32_t* sorted = nullptr;      // points at keys0 or keys1
+    int* cls_start = nullptr;        // weight-class starts in the sorted list
+    int *parent = nullptr, *csize = nullptr, *intw = nullptr, *best = nullptr;
+    int *rootof = nullptr, *minid = nullptr, *dtroot = nullptr;
+    uint32_t* T = nullptr;           // [N][8] TreeIntv at union-find roots
+    uint8_t* in_tree = nullptr;      // [2N]
+    int *listA = nullptr, *listB = nullptr, *raA = nullptr, *rbA = nullptr, *raB = nullptr, *rbB = nullptr;
+    int* hooked = nullptr;
+    int *win = nullptr, *wtmp = nullptr, *wra = nullptr, *wrb = nullptr, *wst = nullptr;
+
+    // tree order / layout
+    uint8_t* adj = nullptr;          // 4-bit tree adjacency (up, left, right, down)
+    uint32_t* aoff = nullptr;        // arc offsets per node (N + 1)
+    int *succ = nullptr, *val = nullptr, *succ2 = nullptr, *val2 = nullptr;   // [2N] arcs
+    int *par = nullptr, *pdir = nullptr, *sub = nullptr, *hdir = nullptr;
+    int* tpos_down = nullptr;        // tour position of the arc parent->v
+    int* tpos_up = nullptr;
+    I4* vals4 = nullptr;             // per node (1, off2, off3, light)
+    I4* tour = nullptr;              // [2N]
+    uint32_t* tbase = nullptr;       // per node: exclusive scan of tour lengths of roots
+    uint32_t* nbase = nullptr;       // per node: exclusive scan of tree sizes of roots
+    int *depth = nullptr, *pre2 = nullptr, *pre3 = nullptr, *light = nullptr;
+    uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr;   // sort scratch [N]
+    int* bfs = nullptr;              // [N]
+    int* lay = nullptr;              // layout row -> pixel
+    int* rowof = nullptr;            // pixel -> layout row
+    int* kp = nullptr;               // padded width per row
+    uint32_t* roff = nullptr;        // row offsets in floats (N + 1)
+    float* rs = nullptr;             // similarity to parent, negative zero/sign for path tops
+    int* prow = nullptr;             // parent row (-1 root)
+    int* rdt = nullptr;              // union-find root of the row's tree (TreeIntv index)
+    uint32_t* lcoff = nullptr;       // light-children offsets (N + 1)
+    int* lcrow = nullptr;            // light-children rows
+    int* nexttop = nullptr;
+    int* runstart = nullptr;         // per (level, width) key: first row
+    uint32_t* ustart_flag = nullptr;
+    uint32_t* uid = nullptr;
+    int *ubeg = nullptr;             // unit first row
+    int* lvl_first = nullptr;        // [MAX_LIGHT_LEVELS] first unit of the level
+    int* lvl_count = nullptr;        // [MAX_LIGHT_LEVELS]
+    int* tickets = nullptr;          // [2][MAX_LIGHT_LEVELS]
+    int* nunits = nullptr;
+
+    // cost volume and masses
+    float* vol = nullptr;
+    __half* volh = nullptr;
+    float *nup = nullptr, *nfull = nullptr;
+    size_t vol_elems = 0;
+
+    // scalars on the device
+    int* ints = nullptr;   // see IDX_* below
+    uint32_t* tmp = nullptr;   // scan / sort scratch
+    size_t tmp_words = 0;
+    DevStatus* st = nullptr;
+
+    int tree_level = -1;       // layer whose forest/layout is in the work buffers
+    int built = 0;
+    std::string err;
+};
+
+// slots of Ctx::ints
+enum {
+    IDX_NEDGES = 0, IDX_RISKY, IDX_NCLS, IDX_NARCS, IDX_N, IDX_CTR0, IDX_CTR1, IDX_CTR2, IDX_CTR3, IDX_CTR4,
+    IDX_K, IDX_NTREES, IDX_NLC, IDX_NUNITS, IDX_ENGINE, IDX_CHANGED, IDX_DRROUNDS, IDX_TWICE_N, IDX_NNODES,
+    IDX_TMP0 = 24, IDX_TMP1, IDX_TMP2, IDX_TMP3, IDX_COUNT = 32
+};
+
+// image.cu
+void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch);
+void launch_pyramid(Ctx& c);
+void launch_edges(Ctx& c, int l, int hdp);
+
+// range.cu
+void launch_prior(Ctx& c, int l);
+void launch_table(Ctx& c, int l);
+void launch_pixsets(Ctx& c, int l);
+
+// forest.cu
+void launch_forest(Ctx& c, int l, int hdp);
+int edge_bits(int N);
+
+// order.cu
+void launch_order(Ctx& c, int l);
+
+// aggregate.cu
+void launch_aggregate(Ctx& c, int l);
+
+// helpers
+CostK cost_consts(const Ctx& c, int l);
+cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int max_blocks, int* used_blocks);

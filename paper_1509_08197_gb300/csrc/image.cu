@@ -1,0 +1,138 @@
+// Graph pyramid (Sec. 2.1), gradient plane and edge list (Eq. weight, DT-Rule 1).
+#include "hdp_impl.cuh"
+
+// layer 0: interleaved RGB uint8 (row pitch in bytes) -> int4 (R, G, B, 0)
+__global__ void k_level0(const uint8_t* __restrict__ img, int pitch, int W, int H, int4* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    int x = i % W, y = i / W;
+    const uint8_t* p = img + (size_t)y * pitch + 3 * x;
+    out[i] = make_int4(p[0], p[1], p[2], 0);
+}
+
+// S = 2 step: each node of layer l+1 averages the 2x2 square of layer l below
+// it; squares cut by the right/bottom border average the children that exist.
+// Values stay integers at scale 4^(l+1): dst = (4 / count) * sum(children).
+__global__ void k_pyr(const int4* __restrict__ src, int W, int H, int4* dst, int Wn, int Hn)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Wn * Hn) return;
+    int X = i % Wn, Y = i / Wn;
+    int sx = 0, sy = 0, sz = 0, cnt = 0;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+            int x = 2 * X + dx, y = 2 * Y + dy;
+            if (x < W && y < H) {
+                int4 v = src[y * W + x];
+                sx += v.x; sy += v.y; sz += v.z;
+                ++cnt;
+            }
+        }
+    int f = 4 / cnt;
+    dst[i] = make_int4(sx * f, sy * f, sz * f, 0);
+}
+
+// horizontal gradient of the grey sum, central difference, replicated border:
+// g = Sum(x+1) - Sum(x-1) with Sum = R + G + B (real gradient g / (6 * 4^l))
+__global__ void k_grad(int4* img, int W, int H)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    int x = i % W, y = i / W;
+    int4 a = img[y * W + min(x + 1, W - 1)];
+    int4 b = img[y * W + max(x - 1, 0)];
+    img[i].w = (a.x + a.y + a.z) - (b.x + b.y + b.z);
+}
+
+void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch)
+{
+    const LayerDims& d = c.dim[0];
+    int4* out = which ? c.imR[0] : c.imL[0];
+    k_level0<<<cdiv(d.N, 256), 256, 0, c.s>>>(d_img, pitch, d.W, d.H, out);
+    k_grad<<<cdiv(d.N, 256), 256, 0, c.s>>>(out, d.W, d.H);
+}
+
+void launch_pyramid(Ctx& c)
+{
+    for (int l = 1; l < c.nlev; ++l) {
+        const LayerDims& a = c.dim[l - 1];
+        const LayerDims& b = c.dim[l];
+        for (int side = 0; side < 2; ++side) {
+            int4* src = side ? c.imR[l - 1] : c.imL[l - 1];
+            int4* dst = side ? c.imR[l] : c.imL[l];
+            k_pyr<<<cdiv(b.N, 256), 256, 0, c.s>>>(src, a.W, a.H, dst, b.W, b.H);
+            k_grad<<<cdiv(b.N, 256), 256, 0, c.s>>>(dst, b.W, b.H);
+        }
+    }
+}
+
+// One thread per edge id e = 2*(y*W + x) + o (o = 0: right neighbour, 1: lower).
+// w = largest per-channel absolute difference (Eq. weight, integer at scale
+// 4^l).  With predicted sets (pixset != null), DT-Rule 1 (Eq. cri1) drops
+// edges whose end points' PixelIntv do not intersect; an edge between
+// different sets whose Jaccard ratio already reaches beta marks the layer as
+// "risky" (DT-Rule 2 may then merge different sets).  Surviving edges are
+// appended as keys (w << ebits | e); their order is fixed by the later sort.
+__global__ void k_edges(const int4* __restrict__ img, int W, int H, int ebits, const int* __restrict__ pixset,
+                        const uint32_t* __restrict__ table, const int* __restrict__ canon, int bnum, int bden,
+                        uint32_t* keys, int* count, int* weights, int* risky)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = W * H;
+    bool keep = false;
+    uint32_t key = 0;
+    if (e < 2 * N) {
+        int p = e >> 1, o = e & 1;
+        int x = p % W, y = p / W;
+        bool valid = o == 0 ? (x + 1 < W) : (y + 1 < H);
+        if (!valid) {
+            weights[e] = -1;
+        } else {
+            int q = o == 0 ? p + 1 : p + W;
+            int4 a = img[p], b = img[q];
+            int w = max(abs(a.x - b.x), max(abs(a.y - b.y), abs(a.z - b.z)));
+            weights[e] = w;
+            keep = true;
+            if (pixset) {
+                int ip = pixset[p], iq = pixset[q];
+                const uint32_t* mp = table + HDP_WORDS * ip;
+                const uint32_t* mq = table + HDP_WORDS * iq;
+                int inter = 0, uni = 0;
+#pragma unroll
+                for (int k = 0; k < HDP_WORDS; ++k) {
+                    inter += __popc(mp[k] & mq[k]);
+                    uni += __popc(mp[k] | mq[k]);
+                }
+                if (inter == 0) keep = false;                                  // DT-Rule 1
+                else if (canon[ip] != canon[iq] && (long long)inter * bden >= (long long)bnum * uni)
+                    *risky = 1;
+            }
+            key = ((uint32_t)w << ebits) | (uint32_t)e;
+        }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) keys[base + __popc(m & ((1u << lane) - 1u))] = key;
+    }
+}
+
+void launch_edges(Ctx& c, int l, int hdp)
+{
+    const LayerDims& d = c.dim[l];
+    int ebits = edge_bits(d.N);
+    cudaMemsetAsync(c.ints + IDX_NEDGES, 0, sizeof(int), c.s);
+    cudaMemsetAsync(c.ints + IDX_RISKY, 0, sizeof(int), c.s);
+    k_edges<<<cdiv(2 * d.N, 256), 256, 0, c.s>>>(c.imL[l], d.W, d.H, ebits, hdp ? c.pixset : nullptr,
+                                                   hdp ? c.table[l] : nullptr, hdp ? c.canon[l] : nullptr,
+                                                   c.p.beta_num, c.p.beta_den, c.keys0, c.ints + IDX_NEDGES,
+                                                   c.weights, c.ints + IDX_RISKY);
+    int bits = ebits + 8 + 2 * l;
+    int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, c.ints + IDX_NEDGES, 2 * d.N, bits, c.tmp, c.s);
+    c.sorted = where ? c.keys1 : c.keys0;
+}

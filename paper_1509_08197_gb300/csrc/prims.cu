@@ -1,0 +1,116 @@
+// Stable LSD radix sort and scans (see prims.cuh).
+#include "prims.cuh"
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, const int* d_n, int shift, uint32_t* hist, int nblocks)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = *d_n;
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+        long long idx = base + i;
+        if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Each warp owns 256 consecutive items of the tile (8 chunks of 32), so the
+// rank of an item is: items of the same digit in earlier tiles (hist), in
+// earlier warps of this tile, in earlier chunks of this warp, then in lower
+// lanes of the same chunk.  This keeps the sort stable.
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* kout,
+                             uint32_t* vout, const int* d_n, int shift, const uint32_t* hist, int nblocks)
+{
+    __shared__ uint32_t cnt[8][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int n = *d_n;
+    const long long wbase = (long long)blockIdx.x * RS_TILE + warp * 256;
+    for (int c = 0; c < 8; ++c) {
+        long long idx = wbase + c * 32 + lane;
+        bool valid = idx < n;
+        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            unsigned d = (kin[idx] >> shift) & 255u;
+            unsigned peers = __match_any_sync(vmask, d);
+            if (lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;   // RS_THREADS == 256 digits
+        uint32_t run = 0;
+        for (int w = 0; w < 8; ++w) {
+            uint32_t t = cnt[w][d];
+            cnt[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c = 0; c < 8; ++c) {
+        long long idx = wbase + c * 32 + lane;
+        bool valid = idx < n;
+        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        unsigned d = 0, peers = 0;
+        uint32_t key = 0, pos = 0;
+        if (valid) {
+            key = kin[idx];
+            d = (key >> shift) & 255u;
+            peers = __match_any_sync(vmask, d);
+            pos = hist[(size_t)d * nblocks + blockIdx.x] + cnt[warp][d] + __popc(peers & lt);
+            kout[pos] = key;
+            if (vin) vout[pos] = vin[idx];
+        }
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+size_t scan_tmp_words(int n_max) { return (size_t)cdiv<long long>(n_max > 0 ? n_max : 1, SCAN_TILE) + 1; }
+
+size_t radix_tmp_words(int n_max)
+{
+    size_t nb = (size_t)cdiv<long long>(n_max > 0 ? n_max : 1, RS_TILE);
+    return 256 * nb + scan_tmp_words((int)(256 * nb)) + 2;
+}
+
+__global__ void k_set_int(int* out, int v) { out[0] = v; }
+
+int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
+               uint32_t* tmp, cudaStream_t s)
+{
+    if (n_max <= 0 || key_bits <= 0) return 0;
+    int nb = (int)cdiv<long long>(n_max, RS_TILE);
+    // the histogram is laid out for nb_max tiles; unused tiles hold zeros and
+    // the device-side count limits the scan to the live part.
+    uint32_t* hist = tmp;
+    uint32_t* stmp = tmp + 256 * (size_t)nb;
+    int* hlen = (int*)(stmp + scan_tmp_words(256 * nb));
+    int cur = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        const uint32_t* ki = cur ? k1 : k0;
+        const uint32_t* vi = cur ? v1 : v0;
+        uint32_t* ko = cur ? k0 : k1;
+        uint32_t* vo = cur ? v0 : v1;
+        k_rs_hist<<<nb, RS_THREADS, 0, s>>>(ki, d_n, shift, hist, nb);
+        // digit-major histogram with a fixed stride of nb tiles (tiles past the
+        // live count hold zeros): scan all of it
+        k_set_int<<<1, 1, 0, s>>>(hlen, 256 * nb);
+        device_scan<uint32_t, OpSum>(hist, hist, hlen, 256 * nb, 0u, OpSum(), true, false, stmp, nullptr, s);
+        k_rs_scatter<<<nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, d_n, shift, hist, nb);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, uint32_t* tmp,
+              uint32_t* total, cudaStream_t s)
+{
+    device_scan<uint32_t, OpSum>(in, out, d_n, n_max, 0u, OpSum(), exclusive, false, tmp, total, s);
+}

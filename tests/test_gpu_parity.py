@@ -1,0 +1,155 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Each layer is run on the GPU with the oracle's upper-layer disparities
+injected, so every stage is compared on identical inputs: pyramid, edge
+weights and order, forest edges, tree roots and TreeIntv, BFS order, parents
+and depths, prior, interval table and pixel sets bit-exactly; aggregated
+costs within 1e-5 relative; WTA identical except near ties (counted).
+"""
+import numpy as np
+import pytest
+
+import paper_1509_08197_gb300 as hdp
+from paper_1509_08197_gb300.scenes import workload_pair
+
+from parity_util import GAP_TOL, REL_TOL, oracle_layer, oracle_params, pyramids, rel_err, wta_mismatch
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _run_layers(hp, pair, check_costs=True, layers=None):
+    """Run every layer on both sides; return per-layer comparison records."""
+    dev = torch.device("cuda:0")
+    ctx = hdp.hdp_create(hp)
+    try:
+        left = torch.from_numpy(pair.left).to(dev).contiguous()
+        right = torch.from_numpy(pair.right).to(dev).contiguous()
+        hdp.hdp_build_trees(ctx, left, right)
+        op = oracle_params(hp)
+        Ls, Rs = pyramids(pair.left, pair.right, len(ctx.dims))
+        out = {}
+        D_up = None
+        for l in range(ctx.top, -1, -1):
+            W, H, d = ctx.dims[l]
+            d_up = ctx.dims[l + 1][2] if l < ctx.top else 0
+            if l < ctx.top:
+                hdp.hdp_set_stage(ctx, l + 1, "disp", D_up.astype(np.int32).ravel())
+            hdp.hdp_run_level(ctx, l)
+            o = oracle_layer(op, Ls[l], Rs[l], l, ctx.top, d, d_up, D_up, want_costs=check_costs)
+            g = {k: hdp.hdp_get_stage(ctx, l, k) for k in
+                 ("pyr_left", "pyr_right", "weights", "edges", "in_tree", "dt_root", "tree_intv", "bfs", "parent",
+                  "depth", "disp", "info")}
+            if check_costs:
+                g["costs"] = hdp.hdp_get_stage(ctx, l, "costs")
+            if l < ctx.top and hp.mode == "hdp":
+                g["prior"] = hdp.hdp_get_stage(ctx, l, "prior")
+                g["table"] = hdp.hdp_get_stage(ctx, l, "table")
+                g["pix_set"] = hdp.hdp_get_stage(ctx, l, "pix_set")
+            out[l] = (g, o)
+            D_up = o["agg"]["wta"].reshape(H, W)
+        return out
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def _assert_layer(l, g, o, hp, d):
+    W = o["L"].shape[1]
+    assert np.array_equal(g["pyr_left"][..., :3], o["L"]), f"layer {l}: left pyramid"
+    assert np.array_equal(g["pyr_right"][..., :3], o["R"]), f"layer {l}: right pyramid"
+    assert np.array_equal(g["pyr_left"][..., 3], o["gL"]), f"layer {l}: gradient"
+    assert np.array_equal(g["weights"], o["weights"].astype(np.int32)), f"layer {l}: edge weights"
+    if "prior" in g:
+        assert np.array_equal(g["prior"], o["prior"]), f"layer {l}: prior"
+        assert np.array_equal(g["table"], o["table"]), f"layer {l}: interval table"
+        assert np.array_equal(g["pix_set"], o["pix_set"]), f"layer {l}: pixel sets"
+    assert np.array_equal(g["edges"], o["edges"]), f"layer {l}: sorted edges"
+    assert np.array_equal(g["in_tree"], o["in_tree"]), f"layer {l}: forest edges"
+    assert np.array_equal(g["dt_root"], o["dt_root"]), f"layer {l}: tree roots"
+    assert np.array_equal(g["tree_intv"], o["tree_intv"]), f"layer {l}: TreeIntv"
+    assert np.array_equal(g["bfs"], o["bfs"]), f"layer {l}: BFS order"
+    assert np.array_equal(g["parent"], o["parent"]), f"layer {l}: parents"
+    assert np.array_equal(g["depth"], o["depth"]), f"layer {l}: depths"
+    if "costs" in g:
+        assert g["costs"].shape == o["agg"]["costs"].shape
+        err = rel_err(g["costs"], o["agg"]["costs"])
+        assert err.max() <= REL_TOL, f"layer {l}: max relative cost error {err.max():.3g}"
+    n, allowed = wta_mismatch(g["disp"], o["agg"])
+    assert n == allowed, f"layer {l}: {n} WTA differences, only {allowed} are near ties (gap < {GAP_TOL})"
+
+
+def test_tiny_hdp_mst():
+    pair = workload_pair("tiny")
+    hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, tree="mst")
+    res = _run_layers(hp, pair)
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
+def test_tiny_hdp_st_and_full():
+    pair = workload_pair("tiny")
+    for hp in (hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, tree="st", st_k=300),
+               hdp.HDPParams(width=96, height=72, max_disp=15, levels=1, mode="full", tree="mst"),
+               hdp.HDPParams(width=96, height=72, max_disp=15, levels=1, mode="full", tree="st")):
+        res = _run_layers(hp, pair)
+        for l, (g, o) in res.items():
+            _assert_layer(l, g, o, hp, None)
+
+
+@pytest.mark.parametrize("tree", ["mst", "st"])
+def test_third_size_hdp(tree):
+    # 463x370, range 0-79, 4 layers (small-image delta0/beta: DT-Rule 2 can merge different sets)
+    pair = workload_pair("third")
+    hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=4, tree=tree)
+    res = _run_layers(hp, pair)
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
+def test_ragged_sizes_and_uniform_prior():
+    # odd sizes (partial pyramid squares, ragged tiles), uniform prior, beta 0.95
+    pair = workload_pair("tiny", width=77, height=41, max_disp=31)
+    hp = hdp.HDPParams(width=77, height=41, max_disp=31, levels=3, tree="mst", prior="uniform", beta=(19, 20),
+                       delta0=0.01)
+    res = _run_layers(hp, pair)
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
+def test_end_to_end_match_and_host_path():
+    from oracle.pipeline import match
+    pair = workload_pair("tiny")
+    hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2)
+    D_ref, _ = match(pair.left, pair.right, oracle_params(hp))
+    ctx = hdp.hdp_create(hp)
+    try:
+        dev = torch.device("cuda:0")
+        out = torch.empty((72, 96), dtype=torch.int32, device=dev)
+        hdp.hdp_build_trees(ctx, torch.from_numpy(pair.left).to(dev), torch.from_numpy(pair.right).to(dev))
+        hdp.hdp_match(ctx, out)
+        hdp.hdp_sync(ctx)
+        D = out.cpu().numpy()
+        D2 = hdp.hdp_match_host(ctx, pair.left, pair.right)
+    finally:
+        hdp.hdp_destroy(ctx)
+    assert np.array_equal(D, D2)
+    assert (D == D_ref).mean() > 0.995
+
+
+def test_fp16_storage_error():
+    pair = workload_pair("third")
+    base = dict(width=463, height=370, max_disp=79, levels=4, tree="mst")
+    r32 = _run_layers(hdp.HDPParams(**base), pair)
+    r16 = _run_layers(hdp.HDPParams(storage="fp16", **base), pair)
+    for l in r32:
+        g16, o = r16[l]
+        # storage rounds each stored entry to 11 significant bits (relative 2^-11);
+        # a value goes through at most two stores plus FP32 recurrences
+        err = rel_err(g16["costs"], o["agg"]["costs"])
+        assert err.max() < 2e-3, f"layer {l}: fp16 max relative error {err.max():.3g}"
+        # a WTA flip is only allowed where the FP64 top-two gap is within twice that bound
+        agg = o["agg"]
+        diff = np.flatnonzero(g16["disp"] != agg["wta"])
+        gap = (agg["second"][diff] - agg["best"][diff]) / np.maximum(np.abs(agg["best"][diff]), 1e-30)
+        assert (gap < 4e-3).all(), f"layer {l}: fp16 flips with gap up to {gap.max():.3g}"
