@@ -23,7 +23,11 @@ static void mark(hdp_ctx* ctx, int l, int k)
 {
     if (!ctx->timing) return;
     if (!ctx->ev[l][k]) cudaEventCreate(&ctx->ev[l][k]);
-    cudaEventRecord(ctx->ev[l][k], ctx->c.s);
+    // inside stream capture only an "external" record becomes a graph node
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->c.s, &cs);
+    cudaEventRecordWithFlags(ctx->ev[l][k], ctx->c.s,
+                             cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
     ctx->ev_used[l][k] = 1;
 }
 
@@ -598,7 +602,13 @@ extern "C" int hdp_get_timings(hdp_ctx* ctx, float* ms, int n)
     for (int l = 0; l < ctx->c.nlev; ++l)
         for (int k = 0; k < 5; ++k) {
             float t = 0.f;
-            if (ctx->ev_used[l][k] && ctx->ev_used[l][k + 1]) cudaEventElapsedTime(&t, ctx->ev[l][k], ctx->ev[l][k + 1]);
+            if (ctx->ev_used[l][k] && ctx->ev_used[l][k + 1]) {
+                cudaError_t e = cudaEventElapsedTime(&t, ctx->ev[l][k], ctx->ev[l][k + 1]);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, HDP_ERR_CUDA, std::string("timing events: ") + cudaGetErrorString(e));
+                }
+            }
             ms[l * 5 + k] = t;
         }
     return HDP_OK;
