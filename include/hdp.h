@@ -149,6 +149,31 @@ int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_righ
                       int* n_kernels);
 int hdp_graph_launch(hdp_ctx* ctx);
 
+/* hdp_build_trees + hdp_match without any allocation, for callers that cannot
+ * allocate device memory: code running where cudaMalloc is not allowed or
+ * would break an allocator they do not control (inside a memory pool or
+ * graph-building framework, a real-time loop, a plug-in that owns no
+ * allocator).  The paper has no counterpart; this is an interface of this
+ * library only.
+ *   - The workspace is a fixed 64 MiB device array inside the library
+ *     (held by every GPU that loads the library, until the process exits).
+ *     Problems whose workspace exceeds it (roughly above 256x256 pixels with
+ *     max_disp 63, FP32) are rejected with HDP_ERR_ARG and a message.
+ *   - d_left/d_right (interleaved RGB uint8, row pitch `pitch` bytes) and
+ *     d_disp_out (int32 [height][width]) are the caller's device buffers;
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.  Each call synchronises the stream once,
+ *     after uploading a few hundred bytes of constants, then enqueues the
+ *     pipeline and returns; device-side errors surface at the caller's next
+ *     synchronisation.
+ *   - Every call uses the same array: calls that overlap on the GPU (two
+ *     streams, two host threads) race and corrupt each other's results.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine. */
+int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, const uint8_t* d_right, int pitch,
+                      int32_t* d_disp_out, void* stream);
+
 /* Per-stage inspection and injection for tests.  `what` selects one of the
  * HDP_STAGE_* buffers of layer `level`; `bytes` must equal its size exactly
  * (query it with hdp_stage_bytes).  hdp_get_stage synchronises the stream.

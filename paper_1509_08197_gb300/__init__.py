@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "hdp_get_timings": (I, [P, P, I]),
         "hdp_graph_capture": (I, [P, P, P, I, P, P]),
         "hdp_graph_launch": (I, [P]),
+        "hdp_match_noalloc": (I, [P, P, P, I, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -267,9 +268,22 @@ def hdp_graph_launch(ctx: Context):
     _check(ctx, load().hdp_graph_launch(ctx.handle), "hdp_graph_launch")
 
 
+NOALLOC_BYTES = 64 << 20
+
+
+def hdp_match_noalloc(params: HDPParams, left, right, out, stream=None):
+    """Match without allocating: the workspace is a fixed 64 MiB array inside
+    libhdp.so (see include/hdp.h).  Calls that overlap on the GPU race."""
+    cp = params.to_c()
+    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    rc = load().hdp_match_noalloc(ctypes.byref(cp), _ptr(left), _ptr(right), 3 * params.width, _ptr(out), s)
+    if rc != HDP_OK:
+        raise HDPError(f"hdp_match_noalloc failed ({rc})")
+
+
 def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
     return ["hdp_default_params", "hdp_create", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
-            "hdp_graph_launch"]
+            "hdp_graph_launch", "hdp_match_noalloc"]

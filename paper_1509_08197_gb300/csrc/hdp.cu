@@ -190,49 +190,86 @@ static void layout_buffers(Ctx& c)
     else c.vol = carve<float>(c, K + 8);
 }
 
+// Checks p and fills the layer sizes of c; returns a message on failure.
+static const char* setup_params(Ctx& c, const hdp_params* p)
+{
+    c.p = *p;
+    if (p->width < 2 || p->height < 2) return "width and height must be >= 2";
+    if (p->max_disp < 1 || p->max_disp > HDP_MAX_DISP) return "max_disp must be in 1..255";
+    if (p->levels < 1 || p->levels > HDP_MAX_LEVELS) return "levels must be in 1..8";
+    if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST) return "unknown tree";
+    if (p->mode != HDP_MODE_HDP && p->mode != HDP_MODE_FULL) return "unknown mode";
+    if (!(p->gamma > 0)) return "gamma must be > 0";
+    if (!near_int(20.0 * p->alpha, &c.a20) || c.a20 < 0 || c.a20 > 20) return "20*alpha must be an integer in 0..20";
+    if (!near_int(3.0 * p->tau_c, &c.tc3) || c.tc3 < 0) return "3*tau_c must be a non-negative integer";
+    if (!near_int(6.0 * p->tau_g, &c.tg6) || c.tg6 < 0) return "6*tau_g must be a non-negative integer";
+    if (p->st_k < 0) return "st_k must be >= 0";
+    if (p->beta_den <= 0 || p->beta_num < 0 || p->beta_num > p->beta_den) return "beta must be in [0, 1]";
+    if (!(p->delta0 >= 0.0) || p->delta0 >= 1.0) return "delta0 must be in [0, 1)";
+    if (p->prior != HDP_PRIOR_SAMPLED && p->prior != HDP_PRIOR_UNIFORM) return "unknown prior";
+    if (p->storage != HDP_STORE_FP32 && p->storage != HDP_STORE_FP16) return "unknown storage";
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
+        if (p->gmm_k[l] < 0 || p->gmm_k[l] > HDP_MAX_GMM) return "gmm_k out of range";
+        for (int k = 0; k < p->gmm_k[l]; ++k)
+            if (!(p->gmm[l][k][2] > 0)) return "gmm standard deviations must be > 0";
+    }
+    if ((long long)p->width * p->height > (1 << 23)) return "images above 2^23 pixels are not supported";
+    c.nlev = p->mode == HDP_MODE_FULL ? 1 : p->levels;
+    c.top = c.nlev - 1;
+    int W = p->width, H = p->height, d = p->max_disp;
+    for (int l = 0; l < c.nlev; ++l) {
+        c.dim[l] = LayerDims{W, H, W * H, d};
+        if (8 + 2 * l + edge_bits(W * H) > 32) return "edge keys do not fit 32 bits";
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+        d = d / 2;
+    }
+    return nullptr;
+}
+
+// Host-side constants of a context: GMM parameters per predicted layer and
+// the full label set of every layer.
+struct HostConsts {
+    double g[HDP_MAX_LEVELS * HDP_MAX_GMM * 3];
+    int gk[HDP_MAX_LEVELS];
+    uint32_t fm[HDP_MAX_LEVELS * HDP_WORDS];
+};
+
+static void host_constants(const Ctx& c, HostConsts& h)
+{
+    const hdp_params* p = &c.p;
+    double* g = h.g;
+    int* gk = h.gk;
+    uint32_t* fm = h.fm;
+    for (int i = 0; i < HDP_MAX_LEVELS * HDP_MAX_GMM * 3; ++i) g[i] = 0.0;
+    for (int i = 0; i < HDP_MAX_LEVELS; ++i) gk[i] = 1;
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
+        if (p->gmm_k[l] == 0) {
+            g[(size_t)l * HDP_MAX_GMM * 3 + 0] = 1.0;
+            g[(size_t)l * HDP_MAX_GMM * 3 + 1] = 0.0;
+            g[(size_t)l * HDP_MAX_GMM * 3 + 2] = 1.0;
+        } else {
+            gk[l] = p->gmm_k[l];
+            for (int k = 0; k < p->gmm_k[l]; ++k)
+                for (int t = 0; t < 3; ++t) g[((size_t)l * HDP_MAX_GMM + k) * 3 + t] = p->gmm[l][k][t];
+        }
+    }
+    for (int i = 0; i < HDP_MAX_LEVELS * HDP_WORDS; ++i) fm[i] = 0u;
+    for (int l = 0; l < c.nlev; ++l)
+        for (int j = 0; j <= c.dim[l].d; ++j) fm[l * HDP_WORDS + (j >> 5)] |= 1u << (j & 31);
+}
+
 extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
 {
     if (!p || !out) return HDP_ERR_ARG;
     *out = nullptr;
     hdp_ctx* ctx = new hdp_ctx();
     Ctx& c = ctx->c;
-    c.p = *p;
     c.s = (cudaStream_t)stream;
-    auto bad = [&](const char* m) {
-        fprintf(stderr, "hdp_create: %s\n", m);
+    if (const char* why = setup_params(c, p)) {
+        fprintf(stderr, "hdp_create: %s\n", why);
         delete ctx;
         return HDP_ERR_ARG;
-    };
-    if (p->width < 2 || p->height < 2) return bad("width and height must be >= 2");
-    if (p->max_disp < 1 || p->max_disp > HDP_MAX_DISP) return bad("max_disp must be in 1..255");
-    if (p->levels < 1 || p->levels > HDP_MAX_LEVELS) return bad("levels must be in 1..8");
-    if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST) return bad("unknown tree");
-    if (p->mode != HDP_MODE_HDP && p->mode != HDP_MODE_FULL) return bad("unknown mode");
-    if (!(p->gamma > 0)) return bad("gamma must be > 0");
-    if (!near_int(20.0 * p->alpha, &c.a20) || c.a20 < 0 || c.a20 > 20) return bad("20*alpha must be an integer in 0..20");
-    if (!near_int(3.0 * p->tau_c, &c.tc3) || c.tc3 < 0) return bad("3*tau_c must be a non-negative integer");
-    if (!near_int(6.0 * p->tau_g, &c.tg6) || c.tg6 < 0) return bad("6*tau_g must be a non-negative integer");
-    if (p->st_k < 0) return bad("st_k must be >= 0");
-    if (p->beta_den <= 0 || p->beta_num < 0 || p->beta_num > p->beta_den) return bad("beta must be in [0, 1]");
-    if (!(p->delta0 >= 0.0) || p->delta0 >= 1.0) return bad("delta0 must be in [0, 1)");
-    if (p->prior != HDP_PRIOR_SAMPLED && p->prior != HDP_PRIOR_UNIFORM) return bad("unknown prior");
-    if (p->storage != HDP_STORE_FP32 && p->storage != HDP_STORE_FP16) return bad("unknown storage");
-    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
-        if (p->gmm_k[l] < 0 || p->gmm_k[l] > HDP_MAX_GMM) return bad("gmm_k out of range");
-        for (int k = 0; k < p->gmm_k[l]; ++k)
-            if (!(p->gmm[l][k][2] > 0)) return bad("gmm standard deviations must be > 0");
-    }
-    if ((long long)p->width * p->height > (1 << 23)) return bad("images above 2^23 pixels are not supported");
-    c.nlev = p->mode == HDP_MODE_FULL ? 1 : p->levels;
-    c.top = c.nlev - 1;
-    int W = p->width, H = p->height, d = p->max_disp;
-    for (int l = 0; l < c.nlev; ++l) {
-        if (d < 0) return bad("too many levels for max_disp");
-        c.dim[l] = LayerDims{W, H, W * H, d};
-        if (8 + 2 * l + edge_bits(W * H) > 32) return bad("edge keys do not fit 32 bits");
-        W = (W + 1) / 2;
-        H = (H + 1) / 2;
-        d = d / 2;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -253,26 +290,11 @@ extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
         return ce == cudaErrorMemoryAllocation ? HDP_ERR_OOM : HDP_ERR_CUDA;
     }
     layout_buffers(c);
-    // constants: GMM parameters, full sets
-    std::vector<double> g(HDP_MAX_LEVELS * HDP_MAX_GMM * 3, 0.0);
-    std::vector<int> gk(HDP_MAX_LEVELS, 1);
-    for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
-        if (p->gmm_k[l] == 0) {
-            g[(size_t)l * HDP_MAX_GMM * 3 + 0] = 1.0;
-            g[(size_t)l * HDP_MAX_GMM * 3 + 1] = 0.0;
-            g[(size_t)l * HDP_MAX_GMM * 3 + 2] = 1.0;
-        } else {
-            gk[l] = p->gmm_k[l];
-            for (int k = 0; k < p->gmm_k[l]; ++k)
-                for (int t = 0; t < 3; ++t) g[((size_t)l * HDP_MAX_GMM + k) * 3 + t] = p->gmm[l][k][t];
-        }
-    }
-    std::vector<uint32_t> fm(HDP_MAX_LEVELS * HDP_WORDS, 0u);
-    for (int l = 0; l < c.nlev; ++l)
-        for (int j = 0; j <= c.dim[l].d; ++j) fm[l * HDP_WORDS + (j >> 5)] |= 1u << (j & 31);
-    TRY_CUDA(cudaMemcpy(c.gmm, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice));
-    TRY_CUDA(cudaMemcpy(c.gmm_k, gk.data(), gk.size() * sizeof(int), cudaMemcpyHostToDevice));
-    TRY_CUDA(cudaMemcpy(c.full_mask, fm.data(), fm.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    HostConsts hc;
+    host_constants(c, hc);
+    TRY_CUDA(cudaMemcpy(c.gmm, hc.g, sizeof(hc.g), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(c.gmm_k, hc.gk, sizeof(hc.gk), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(c.full_mask, hc.fm, sizeof(hc.fm), cudaMemcpyHostToDevice));
     TRY_CUDA(cudaMemset(c.st, 0, sizeof(DevStatus)));
     TRY_CUDA(cudaMemset(c.ints, 0, sizeof(int) * IDX_COUNT));
     *out = ctx;
@@ -651,5 +673,71 @@ extern "C" int hdp_graph_launch(hdp_ctx* ctx)
     if (!ctx) return HDP_ERR_ARG;
     if (!ctx->exec) return fail(ctx, HDP_ERR_STATE, "no captured graph");
     TRY_CUDA(cudaGraphLaunch(ctx->exec, ctx->c.s));
+    return HDP_OK;
+}
+
+// ------------------------------------------------------ no-allocation path ---
+// Workspace of hdp_match_noalloc: a fixed device array that lives as long as
+// the library is loaded, on every GPU that loads it.
+#define HDP_NOALLOC_BYTES (64u << 20)
+static __device__ __align__(256) char g_noalloc_scratch[HDP_NOALLOC_BYTES];
+
+#define HDP_NOALLOC_MAX_DEVICES 64
+static char* g_noalloc_ptr[HDP_NOALLOC_MAX_DEVICES];
+
+extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, const uint8_t* d_right, int pitch,
+                                 int32_t* d_disp_out, void* stream)
+{
+    if (!p || !d_left || !d_right || !d_disp_out) return HDP_ERR_ARG;
+    hdp_ctx local;   // on the stack: no host or device allocation
+    hdp_ctx* ctx = &local;
+    Ctx& c = ctx->c;
+    c.s = (cudaStream_t)stream;
+    if (const char* why = setup_params(c, p)) {
+        fprintf(stderr, "hdp_match_noalloc: %s\n", why);
+        return HDP_ERR_ARG;
+    }
+    if (pitch < 3 * p->width) return HDP_ERR_ARG;
+    c.arena = nullptr;
+    layout_buffers(c);
+    if (c.arena_used > HDP_NOALLOC_BYTES) {
+        fprintf(stderr, "hdp_match_noalloc: this problem needs %zu bytes of workspace, above the fixed %u\n",
+                c.arena_used, (unsigned)HDP_NOALLOC_BYTES);
+        return HDP_ERR_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= HDP_NOALLOC_MAX_DEVICES) return HDP_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        // one-time set-up on this device (it must be current): the device
+        // address of the fixed array; host code cannot use the symbol itself
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            fprintf(stderr, "hdp_match_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+            return HDP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = (char*)ptr;
+    }
+    c.arena = g_noalloc_ptr[dev];
+    c.arena_bytes = HDP_NOALLOC_BYTES;
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    layout_buffers(c);
+    // the array keeps the previous call's contents: reset what must start at zero
+    HostConsts hc;   // on the stack
+    host_constants(c, hc);
+    TRY_CUDA(cudaMemcpyAsync(c.gmm, hc.g, sizeof(hc.g), cudaMemcpyHostToDevice, c.s));
+    TRY_CUDA(cudaMemcpyAsync(c.gmm_k, hc.gk, sizeof(hc.gk), cudaMemcpyHostToDevice, c.s));
+    TRY_CUDA(cudaMemcpyAsync(c.full_mask, hc.fm, sizeof(hc.fm), cudaMemcpyHostToDevice, c.s));
+    TRY_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
+    TRY_CUDA(cudaMemsetAsync(c.ints, 0, sizeof(int) * IDX_COUNT, c.s));
+    // the host constants above must outlive the copies: wait for them
+    TRY_CUDA(cudaStreamSynchronize(c.s));
+    int rc = hdp_build_trees(ctx, d_left, d_right, pitch);
+    if (!rc) rc = hdp_match(ctx, d_disp_out);
+    if (rc) {
+        fprintf(stderr, "hdp_match_noalloc: %s\n", c.err.c_str());
+        return rc;
+    }
     return HDP_OK;
 }
