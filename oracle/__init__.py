@@ -70,6 +70,8 @@ def _declare(L):
         "orc_gmm_density": (D, [I, P, D]),
         "orc_range_table": (I, [P, I, I, I, P, D, P, P]),
         "orc_pixel_intervals": (I, [I, I, P, I, P, P]),
+        "orc_aggregate_given": (I, [I64, I, P, P, P, P, P, P]),
+        "orc_aggregate_adjoint": (I, [I64, I, P, P, P, D, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -239,3 +241,60 @@ def set_from_labels(labels) -> np.ndarray:
 def labels_of(mask) -> list:
     m = np.asarray(mask, np.uint32)
     return [j for j in range(256) if (int(m[j >> 5]) >> (j & 31)) & 1]
+
+
+def aggregate_given(order, parent, s, E, want_up=False):
+    """Eq. C for a given volume E (N, X), all labels defined; s = per-node similarity to parent."""
+    E = _c(E, np.float64)
+    N, X = E.shape
+    C = np.empty_like(E)
+    U = np.empty_like(E) if want_up else None
+    rc = lib().orc_aggregate_given(N, X, _p(_c(order, np.int32)), _p(_c(parent, np.int32)), _p(_c(s, np.float64)),
+                                   _p(E), _p(C), _p(U))
+    if rc:
+        raise MemoryError("orc_aggregate_given")
+    return (C, U) if want_up else C
+
+
+def aggregate_adjoint(order, parent, w_node, gamma, E, g):
+    """(dL/dE, dL/dw per node, dL/dgamma) of L with dL/dC = g."""
+    E = _c(E, np.float64)
+    g = _c(g, np.float64)
+    N, X = E.shape
+    gE = np.empty_like(E)
+    gw = np.empty(N, np.float64)
+    gg = np.zeros(1, np.float64)
+    rc = lib().orc_aggregate_adjoint(N, X, _p(_c(order, np.int32)), _p(_c(parent, np.int32)),
+                                     _p(_c(w_node, np.float64)), float(gamma), _p(E), _p(g), _p(gE), _p(gw), _p(gg))
+    if rc:
+        raise MemoryError("orc_aggregate_adjoint")
+    return gE, gw, float(gg[0])
+
+
+def node_weights(W, H, parent, w_edges, level=0):
+    """Weight (real units) of the edge from each node to its parent; 0 for roots."""
+    N = W * H
+    out = np.zeros(N, np.float64)
+    for v in range(N):
+        p = parent[v]
+        if p < 0:
+            continue
+        if p == v - 1:
+            e = 2 * p
+        elif p == v + 1:
+            e = 2 * v
+        elif p == v - W:
+            e = 2 * p + 1
+        else:
+            e = 2 * v + 1
+        out[v] = w_edges[e] / float(4 ** level)
+    return out
+
+
+def soft_argmin(C, T=1.0):
+    """d(p) = sum_x x softmax(-C(p, .)/T)(x) per row of C (N, X), FP64."""
+    C = np.asarray(C, np.float64)
+    z = -(C - C.min(1, keepdims=True)) / T
+    e = np.exp(z)
+    pr = e / e.sum(1, keepdims=True)
+    return (pr * np.arange(C.shape[1])[None, :]).sum(1)

@@ -548,3 +548,67 @@ int orc_pixel_intervals(int W, int H, const int32_t* d_up_map, int W_up,
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. C for a given cost volume: C(p, x) = sum_q S(p, q) E(q, x) over the tree
+ * of p, S = exp(-W/gamma), with the two-pass recurrences, every label defined.
+ * s[v] = exp(-w(v, parent)/gamma) (0 for roots); E, C: [N][X].  Eup (optional)
+ * receives the leaf-to-root pass U.                                         */
+int orc_aggregate_given(int64_t N, int X, const int32_t* order, const int32_t* parent, const double* s,
+                        const double* E, double* C, double* Eup)
+{
+    double* U = (double*)malloc(sizeof(double) * (size_t)N * X);
+    if (!U) return -1;
+    memcpy(U, E, sizeof(double) * (size_t)N * X);
+    for (int64_t i = N - 1; i >= 0; --i) {
+        int32_t v = order[i], p = parent[v];
+        if (p < 0) continue;
+        for (int x = 0; x < X; ++x) U[(size_t)p * X + x] += s[v] * U[(size_t)v * X + x];
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t v = order[i], p = parent[v];
+        for (int x = 0; x < X; ++x)
+            C[(size_t)v * X + x] = p < 0 ? U[(size_t)v * X + x]
+                                         : s[v] * C[(size_t)p * X + x] + (1.0 - s[v] * s[v]) * U[(size_t)v * X + x];
+    }
+    if (Eup) memcpy(Eup, U, sizeof(double) * (size_t)N * X);
+    free(U);
+    return 0;
+}
+
+/* Adjoint of Eq. C with respect to the cost volume, the tree edge weights and
+ * gamma, for L with g = dL/dC.  A(p, q) = exp(-W(p, q)/gamma) is symmetric, so
+ * dL/dE = A g.  Tree edge e = (c, pi): the pairs whose path crosses e have one
+ * end in the subtree of c; with up-pass values E^, g^ and full aggregates C, G,
+ *   dL/dw_e = -(s_e/gamma) sum_x [ g^(c)(C(pi) - s_e E^(c)) + E^(c)(G(pi) - s_e g^(c)) ],
+ *   dL/dgamma = -(1/gamma) sum_e w_e dL/dw_e   (W is linear in the weights).
+ * w[v]: weight of the edge from v to its parent (real units; unused for roots).
+ * Outputs gE [N][X], gw[v] per node (0 for roots), *ggamma.                  */
+int orc_aggregate_adjoint(int64_t N, int X, const int32_t* order, const int32_t* parent, const double* w,
+                          double gamma, const double* E, const double* g, double* gE, double* gw, double* ggamma)
+{
+    double* s = (double*)malloc(sizeof(double) * N);
+    double* Eu = (double*)malloc(sizeof(double) * (size_t)N * X);
+    double* Cf = (double*)malloc(sizeof(double) * (size_t)N * X);
+    double* gu = (double*)malloc(sizeof(double) * (size_t)N * X);
+    if (!s || !Eu || !Cf || !gu) return -1;
+    for (int64_t v = 0; v < N; ++v) s[v] = parent[v] < 0 ? 0.0 : exp(-w[v] / gamma);
+    orc_aggregate_given(N, X, order, parent, s, E, Cf, Eu);
+    orc_aggregate_given(N, X, order, parent, s, g, gE, gu);
+    double acc = 0.0;
+    for (int64_t c = 0; c < N; ++c) {
+        int32_t p = parent[c];
+        gw[c] = 0.0;
+        if (p < 0) continue;
+        double t = 0.0;
+        for (int x = 0; x < X; ++x) {
+            size_t ic = (size_t)c * X + x, ip = (size_t)p * X + x;
+            t += gu[ic] * (Cf[ip] - s[c] * Eu[ic]) + Eu[ic] * (gE[ip] - s[c] * gu[ic]);
+        }
+        gw[c] = -(s[c] / gamma) * t;
+        acc += w[c] * gw[c];
+    }
+    *ggamma = -acc / gamma;
+    free(s); free(Eu); free(Cf); free(gu);
+    return 0;
+}

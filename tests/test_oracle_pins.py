@@ -529,3 +529,62 @@ def test_range_table_offset_sign():
     assert oracle.labels_of(masks[0]) == [0, 1]
     for i in range(1, d_up + 1):
         assert oracle.labels_of(masks[i]) == [2 * i - 2, 2 * i - 1]
+
+
+# ------------------------------------------- differentiable aggregation ---
+def _tree_case(rng, H=5, W=6):
+    img = rng.integers(0, 60, size=(H, W, 3)).astype(np.int32)
+    w, order, in_tree, _, _ = _forest(img)
+    bo, parent, _ = oracle.bfs(W, H, in_tree)
+    wn = oracle.node_weights(W, H, parent, w)
+    return img, w, in_tree, bo, parent, wn
+
+
+def test_aggregate_given_equals_brute_force():
+    rng = np.random.default_rng(20)
+    H, W, X, gamma = 4, 5, 6, 25.5
+    img, w, in_tree, bo, parent, wn = _tree_case(rng, H, W)
+    E = rng.uniform(0, 2.5, size=(W * H, X))
+    s = np.where(parent >= 0, np.exp(-wn / gamma), 0.0)
+    C = oracle.aggregate_given(bo, parent, s, E)
+    ref = brute.brute_aggregate(W, H, in_tree, w.astype(float), E, gamma)
+    assert np.allclose(C, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_adjoint_matches_central_differences():
+    # L = sum(g * C(E, w, gamma)); FP64 central differences with h = 1e-6
+    rng = np.random.default_rng(21)
+    H, W, X, gamma = 4, 5, 5, 7.0
+    img, w, in_tree, bo, parent, wn = _tree_case(rng, H, W)
+    E = rng.uniform(0, 2.5, size=(W * H, X))
+    g = rng.normal(size=(W * H, X))
+    gE, gw, gg = oracle.aggregate_adjoint(bo, parent, wn, gamma, E, g)
+
+    def L(E_, wn_, gamma_):
+        s = np.where(parent >= 0, np.exp(-wn_ / gamma_), 0.0)
+        return float((g * oracle.aggregate_given(bo, parent, s, E_)).sum())
+
+    h = 1e-6
+    for _ in range(6):
+        i, x = int(rng.integers(0, W * H)), int(rng.integers(0, X))
+        Ep, Em = E.copy(), E.copy()
+        Ep[i, x] += h
+        Em[i, x] -= h
+        assert gE[i, x] == pytest.approx((L(Ep, wn, gamma) - L(Em, wn, gamma)) / (2 * h), rel=1e-6, abs=1e-8)
+    for v in np.flatnonzero(parent >= 0)[:8]:
+        wp, wm = wn.copy(), wn.copy()
+        wp[v] += h
+        wm[v] -= h
+        assert gw[v] == pytest.approx((L(E, wp, gamma) - L(E, wm, gamma)) / (2 * h), rel=1e-6, abs=1e-8)
+    assert gg == pytest.approx((L(E, wn, gamma + h) - L(E, wn, gamma - h)) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+def test_soft_argmin_closed_forms():
+    X = 9
+    assert oracle.soft_argmin(np.zeros((1, X)))[0] == pytest.approx((X - 1) / 2)
+    C = np.full((1, X), 1000.0)
+    C[0, 6] = 0.0
+    assert oracle.soft_argmin(C)[0] == pytest.approx(6.0)
+    # two equal minima, far below the rest: the midpoint
+    C[0, 2] = 0.0
+    assert oracle.soft_argmin(C)[0] == pytest.approx(4.0)
