@@ -198,6 +198,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", default="hdp_st_fp32",
+                    choices=["hdp_st_fp32", "hdp_st_fp16", "full_st_fp32", "full_st_fp16", "hdp_mst_fp32"],
+                    help="configuration of the timed headline (profiling runs); the reported metric is hdp_st_fp32")
     args = ap.parse_args()
     rank, ws = dist_init()
 
@@ -240,9 +244,14 @@ def main():
     pair = workload_pair("full", index=rank)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     base = dict(width=W, height=H, max_disp=D, levels=LEVELS, tree="st")
-    head_p = hdp.HDPParams(**base)
+    specs = {"hdp_st_fp32": dict(base), "hdp_st_fp16": dict(base, storage="fp16"),
+             "full_st_fp32": dict(base, mode="full", levels=1),
+             "full_st_fp16": dict(base, mode="full", levels=1, storage="fp16"),
+             "hdp_mst_fp32": dict(base, tree="mst")}
+    head_p = hdp.HDPParams(**specs[args.variant])
     barrier(ws)
-    head = run_variant(hdp, torch, head_p, pair, args.steps, args.warmup, flush, dev, want_e2e=True, clocks=True)
+    head = run_variant(hdp, torch, head_p, pair, args.steps, args.warmup, flush, dev, want_e2e=not args.no_e2e,
+                       clocks=True)
     step_ms = float(np.sum(head["step_ms"]))
     step_ms = reduce_max(step_ms, ws) / args.steps
     Ktot = sum(head["K"])
@@ -250,17 +259,16 @@ def main():
     dims = hdp.Context(None, head_p).dims
     hbm, peak_kind = peaks()
     agg_ms = float(np.mean(head["agg_ms"]))
-    abytes = agg_bytes(head["K"], dims, 4)
+    abytes = agg_bytes(head["K"], dims, 2 if head_p.storage == "fp16" else 4)
     achieved = abytes / (agg_ms / 1000.0) / 1e9
     e2e = head["e2e"]
-    e2e_v = ws * Ktot / e2e["seconds"] / 1e6
+    e2e_v = ws * Ktot / e2e["seconds"] / 1e6 if e2e else None
 
     variants = {}
     if not args.no_variants:
-        specs = {"hdp_st_fp16": dict(base, storage="fp16"),
-                 "full_st_fp32": dict(base, mode="full", levels=1),
-                 "full_st_fp16": dict(base, mode="full", levels=1, storage="fp16")}
         for name, kw in specs.items():
+            if name == args.variant:
+                continue
             p = hdp.HDPParams(**kw)
             r = run_variant(hdp, torch, p, pair, max(3, args.steps // 2), args.warmup, flush, dev)
             ms = float(np.mean(r["step_ms"]))
@@ -273,7 +281,8 @@ def main():
                      "stage_ms": {hdp.STAGE_NAMES[k]: float(r["stage_ms"][:, k].sum()) for k in range(5)},
                      "disparity_agreement_with_headline": float((r["D"] == head["D"]).mean())}
             variants[name] = entry
-        variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
+        if "full_st_fp32" in variants and args.variant == "hdp_st_fp32":
+            variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -287,7 +296,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "ms_per_pair": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs_per_gpu": 1, "aggregated_entries_per_layer": head["K"],
+        "config": {"workload": WORKLOAD, "variant": args.variant, "pairs_per_gpu": 1, "aggregated_entries_per_layer": head["K"],
                    "l2": "flushed (512 MiB write) before every timed step", "graph": "one CUDA graph per step",
                    "parallelism": f"replicas x{ws}"},
         "stage_ms_per_layer": {hdp.STAGE_NAMES[k]: [float(x) for x in head["stage_ms"][:, k]] for k in range(5)},
@@ -295,8 +304,8 @@ def main():
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                "ms_per_pair": 1000 * e2e["seconds"]},
+        "e2e": ({"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                 "ms_per_pair": 1000 * e2e["seconds"]} if e2e else None),
         "gpu_launches": head["n_kernels"],
         "clocks": head["clocks"],
         "variants": variants,

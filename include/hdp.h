@@ -149,6 +149,29 @@ int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_righ
                       int* n_kernels);
 int hdp_graph_launch(hdp_ctx* ctx);
 
+/* Differentiable aggregation (Eq. C as a function of the cost volume, the
+ * edge weights and gamma) over the forest of the layer whose tree is loaded
+ * (after hdp_build_trees: the top layer; with HDP_MODE_FULL the whole-image
+ * MST or segment tree).  That layer must be full range and the storage FP32.
+ * Volumes are dense FP32 [height][width][X] device arrays, X = d_l + 1
+ * labels, pixel-major.  The tree itself is held fixed (it is piecewise
+ * constant in the weights).
+ *   hdp_aggregate_fwd: C = A E, A(p,q) = exp(-W(p,q)/gamma).
+ *   hdp_aggregate_bwd: with g = dL/dC: dL/dE = A g (A is symmetric),
+ *     dL/dw[e] for every grid edge id e (0 outside the forest; weights in
+ *     0..255 intensity units) and dL/dgamma, by the closed forms of the
+ *     adjoint; the forward passes are recomputed, not stored.
+ *   hdp_set_gamma: change gamma for the loaded tree.
+ *   hdp_soft_argmin_l1: d(p) = sum_x x softmax(-C(p,.)/T), the mean |d - gt|
+ *     over pixels with valid[p] != 0 (valid may be NULL), and dL/dC; d_disp,
+ *     d_loss (one float) and d_gC may each be NULL.
+ * The first call allocates four volume-sized buffers in the context. */
+int hdp_aggregate_fwd(hdp_ctx* ctx, const float* d_E, float* d_C);
+int hdp_aggregate_bwd(hdp_ctx* ctx, const float* d_E, const float* d_gC, float* d_gE, float* d_gw, float* d_ggamma);
+int hdp_set_gamma(hdp_ctx* ctx, float gamma);
+int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const uint8_t* d_valid, float T,
+                       float* d_disp, float* d_loss, float* d_gC);
+
 /* hdp_build_trees + hdp_match without any allocation, for callers that cannot
  * allocate device memory: code running where cudaMalloc is not allowed or
  * would break an allocator they do not control (inside a memory pool or

@@ -122,6 +122,10 @@ def load(path: str = LIB_PATH):
         "hdp_graph_capture": (I, [P, P, P, I, P, P]),
         "hdp_graph_launch": (I, [P]),
         "hdp_match_noalloc": (I, [P, P, P, I, P, P]),
+        "hdp_aggregate_fwd": (I, [P, P, P]),
+        "hdp_aggregate_bwd": (I, [P, P, P, P, P, P]),
+        "hdp_set_gamma": (I, [P, ctypes.c_float]),
+        "hdp_soft_argmin_l1": (I, [P, P, P, P, ctypes.c_float, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -281,9 +285,34 @@ def hdp_match_noalloc(params: HDPParams, left, right, out, stream=None):
         raise HDPError(f"hdp_match_noalloc failed ({rc})")
 
 
+def _optr(t):
+    return None if t is None else _ptr(t)
+
+
+def hdp_aggregate_fwd(ctx: Context, E, C):
+    """C = A E over the loaded full-range tree; E, C: float32 (H, W, X) CUDA tensors."""
+    _check(ctx, load().hdp_aggregate_fwd(ctx.handle, _ptr(E), _ptr(C)), "hdp_aggregate_fwd")
+
+
+def hdp_aggregate_bwd(ctx: Context, E, gC, gE, gw, ggamma):
+    """dL/dE (H, W, X), dL/dw per grid edge id (2*H*W,), dL/dgamma (1,) from dL/dC."""
+    _check(ctx, load().hdp_aggregate_bwd(ctx.handle, _ptr(E), _ptr(gC), _ptr(gE), _ptr(gw), _ptr(ggamma)),
+           "hdp_aggregate_bwd")
+
+
+def hdp_set_gamma(ctx: Context, gamma: float):
+    _check(ctx, load().hdp_set_gamma(ctx.handle, float(gamma)), "hdp_set_gamma")
+
+
+def hdp_soft_argmin_l1(ctx: Context, C, gt=None, valid=None, T=1.0, disp=None, loss=None, gC=None):
+    _check(ctx, load().hdp_soft_argmin_l1(ctx.handle, _ptr(C), _optr(gt), _optr(valid), float(T), _optr(disp),
+                                          _optr(loss), _optr(gC)), "hdp_soft_argmin_l1")
+
+
 def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
     return ["hdp_default_params", "hdp_create", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
-            "hdp_graph_launch", "hdp_match_noalloc"]
+            "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
+            "hdp_soft_argmin_l1"]

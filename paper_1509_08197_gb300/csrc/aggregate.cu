@@ -11,15 +11,23 @@
 // light level is an affine recurrence along rows:
 //   up   x_r = a_r + m_r x_{r+1},  a_r = E_r + sum_light s_c U_c,  m_r = s_{r+1}
 //   down x_r = b_r + m_r x_{r-1},  b_r = (1 - s_r^2) U_r (+ s_r C(parent) at a top)
-// with m = 0 across path boundaries.  A warp owns a unit of whole paths and
-// walks it in groups of rows, one row per lane group, combining rows with a
-// shuffle scan of affine maps and carrying the last row into the next group.
-// Light levels run one launch each (deepest first for the up pass).
+// with m = 0 across path boundaries.  The rows of a level are cut into tiles of
+// about TILE_FLOATS costs; a warp stages its tile in shared memory (all loads
+// of the tile in flight together), scans it (per-lane sequential chunks and a
+// shuffle scan of affine maps across chunks), and takes the carry from the
+// neighbouring tile of the same path with a decoupled look-back: a tile
+// publishes its affine aggregate (A, M), then its inclusive boundary value; the
+// carry is evaluated innermost-first, so the rounding does not depend on
+// timing.  Light levels run one launch each (deepest first for the up pass).
 #include "hdp_impl.cuh"
 
-#define AGG_THREADS 256
+#define AGG_WARPS 4
+#define AGG_THREADS (32 * AGG_WARPS)
+#define TILE_ROWS_MAX (TILE_FLOATS / 4)
 
 struct AggArgs {
+    const uint32_t* tstart;   // 1 at the first row of a tile
+    const uint32_t* tid;      // exclusive count of tile starts
     const int4* imL;
     const int4* imR;
     int W, N, full, dl;
@@ -33,15 +41,22 @@ struct AggArgs {
     const int* lcrow;
     const uint32_t* roff;
     const int* kp;
-    const int* ubeg;
-    const int* d_nunits;
+    const int* tbeg;
+    const int* d_ntiles;
     const int* lvl_first;
     const int* lvl_count;
-    float* vol;
+    float* vol;          // up-pass values U (and the down pass input)
+    float* vout;         // down-pass output C (== vol for in-place aggregation)
+    const float* Ein;    // optional dense cost volume [N][X] (all labels) instead of the matching cost
+    int X;
     __half* volh;
     float* nup;
     float* nd;
     int* tickets;
+    int* tflags;
+    float* aggA;
+    float* inclA;
+    float* aggM;
     int level;
     int32_t* disp;
     DevStatus* st;
@@ -52,20 +67,11 @@ __device__ __forceinline__ float4 fma4(float m, float4 x, float4 a)
 {
     return make_float4(fmaf(m, x.x, a.x), fmaf(m, x.y, a.y), fmaf(m, x.z, a.z), fmaf(m, x.w, a.w));
 }
-__device__ __forceinline__ float4 shfl_down4(float4 v, int d)
-{
-    return make_float4(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
-                       __shfl_down_sync(0xffffffffu, v.z, d), __shfl_down_sync(0xffffffffu, v.w, d));
-}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 __device__ __forceinline__ float4 shfl_up4(float4 v, int d)
 {
     return make_float4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
                        __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
-}
-__device__ __forceinline__ float4 shfl4(float4 v, int src)
-{
-    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
 // label of the n-th element (0-based) of a 256-bit set, -1 if absent
@@ -80,54 +86,39 @@ __device__ __forceinline__ int nth_label(const uint32_t* m, int n)
     return -1;
 }
 
-struct RowInfo {
-    int k;            // number of labels of the row's tree
-    int lab[8];       // labels of this lane's (up to 2 x 4) slots, -1 = padding
-};
-
-__device__ __forceinline__ void row_labels(const AggArgs& a, int r, int col0, int fpl, int q, RowInfo& ri)
+// labels of slots 4j .. 4j+3 of a row (-1 for padding slots)
+__device__ __forceinline__ void slot_labels(const AggArgs& a, int row, int j, int lab[4], int* kout)
 {
     if (a.full) {
-        ri.k = a.dl + 1;
+        const int k = a.dl + 1;
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                int slot = 4 * (col0 + 32 * f) + i;
-                ri.lab[4 * f + i] = (f < fpl && col0 + 32 * f < q && slot < ri.k) ? slot : -1;
-            }
+        for (int i = 0; i < 4; ++i) lab[i] = 4 * j + i < k ? 4 * j + i : -1;
+        if (kout) *kout = k;
         return;
     }
     uint32_t m[HDP_WORDS];
-    const uint32_t* src = a.T + (size_t)a.rdt[r] * HDP_WORDS;
+    const uint32_t* src = a.T + (size_t)a.rdt[row] * HDP_WORDS;
 #pragma unroll
     for (int w = 0; w < HDP_WORDS; ++w) m[w] = src[w];
     int k = 0;
 #pragma unroll
     for (int w = 0; w < HDP_WORDS; ++w) k += __popc(m[w]);
-    ri.k = k;
+    if (kout) *kout = k;
+    int l = 4 * j < k ? nth_label(m, 4 * j) : -1;
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-        int col = col0 + 32 * f;
-        bool ok = f < fpl && col < q;
-        int lab = ok && 4 * col < k ? nth_label(m, 4 * col) : -1;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ri.lab[4 * f + i] = lab;
-            if (lab >= 0 && 4 * col + i + 1 < k) {
-                // next set bit after lab
-                int w = lab >> 5, b = lab & 31;
-                int nxt = -1;
-                if (b < 31) {
-                    unsigned r2 = __fns(m[w], b + 1, 1);
-                    if (r2 != 0xffffffffu) nxt = 32 * w + (int)r2;
-                }
-                for (int ww = w + 1; nxt < 0 && ww < HDP_WORDS; ++ww)
-                    if (m[ww]) nxt = 32 * ww + __ffs(m[ww]) - 1;
-                lab = nxt;
-            } else {
-                lab = -1;
+    for (int i = 0; i < 4; ++i) {
+        lab[i] = l;
+        if (l >= 0 && 4 * j + i + 1 < k) {
+            int w = l >> 5, b = l & 31, nxt = -1;
+            if (b < 31) {
+                unsigned r = __fns(m[w], b + 1, 1);
+                if (r != 0xffffffffu) nxt = 32 * w + (int)r;
             }
+            for (int ww = w + 1; nxt < 0 && ww < HDP_WORDS; ++ww)
+                if (m[ww]) nxt = 32 * ww + __ffs(m[ww]) - 1;
+            l = nxt;
+        } else {
+            l = -1;
         }
     }
 }
@@ -143,11 +134,24 @@ template <bool FP16>
 __device__ __forceinline__ float4 load_row4(const AggArgs& a, size_t off)
 {
     if (FP16) {
-        const __half2* h = (const __half2*)(a.volh + off);
-        float2 x = __half22float2(h[0]), y = __half22float2(h[1]);
+        const uint2 raw = *(const uint2*)(a.volh + off);
+        float2 x = __half22float2(*(const __half2*)&raw.x), y = __half22float2(*(const __half2*)&raw.y);
         return make_float4(x.x, x.y, y.x, y.y);
     } else {
         return *(const float4*)(a.vol + off);
+    }
+}
+
+// rows written by other SMs during the same kernel: read through L2 only
+template <bool FP16>
+__device__ __forceinline__ float4 load_row4_cg(const AggArgs& a, size_t off)
+{
+    if (FP16) {
+        const uint2 raw = __ldcg((const uint2*)(a.volh + off));
+        float2 x = __half22float2(*(const __half2*)&raw.x), y = __half22float2(*(const __half2*)&raw.y);
+        return make_float4(x.x, x.y, y.x, y.y);
+    } else {
+        return __ldcg((const float4*)(a.vol + off));
     }
 }
 
@@ -155,217 +159,378 @@ template <bool FP16>
 __device__ __forceinline__ void store_row4(const AggArgs& a, size_t off, float4 v)
 {
     if (FP16) {
-        __half2* h = (__half2*)(a.volh + off);
-        h[0] = __floats2half2_rn(v.x, v.y);
-        h[1] = __floats2half2_rn(v.z, v.w);
+        __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+        uint2 raw;
+        raw.x = *(const unsigned*)&h0;
+        raw.y = *(const unsigned*)&h1;
+        *(uint2*)(a.volh + off) = raw;
     } else {
         *(float4*)(a.vol + off) = v;
     }
 }
 
-struct Shape {
-    int q, lpr, rpw, fpl, col0, rsub;
-};
-__device__ __forceinline__ Shape unit_shape(int kp)
+__device__ __forceinline__ int tile_of_row(const AggArgs& a, int r) { return (int)a.tid[r] + (int)a.tstart[r] - 1; }
+
+// the spin on a neighbouring tile's state is bounded; on timeout the carry is
+// taken as zero and the device status reports DEV_TIMEOUT
+__device__ __forceinline__ int wait_flag(const AggArgs& a, int* f)
 {
-    Shape s;
-    s.q = kp >> 2;
-    s.lpr = s.q <= 32 ? (1 << (32 - __clz(s.q - 1))) : 32;
-    if (s.q == 1) s.lpr = 1;
-    s.rpw = 32 / s.lpr;
-    s.fpl = (s.q + 31) >> 5;
-    int lane = threadIdx.x & 31;
-    s.col0 = lane % s.lpr;
-    s.rsub = lane / s.lpr;
-    return s;
+    unsigned it = 0;
+    int v;
+    while ((v = *(volatile int*)f) == 0) {
+        if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+            dev_fail(a.st, DEV_TIMEOUT, 50);
+            return -1;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return v;
 }
 
-template <bool FP16>
-__device__ void up_unit(const AggArgs& a, int u, int nunits)
+__device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 {
-    const int b = a.ubeg[u];
-    const int e = u + 1 < nunits ? a.ubeg[u + 1] : a.N;
-    const Shape sh = unit_shape(a.kp[b]);
+    unsigned it = 0;
+    while (*(volatile int*)f != 2) {
+        if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+            dev_fail(a.st, DEV_TIMEOUT, 52);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+template <bool FP16, bool UP>
+__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float4* CIN)
+{
+    const int lane = threadIdx.x & 31;
+    const int ntiles = *a.d_ntiles;
+    const int b = a.tbeg[u];
+    const int kp = a.kp[b];
+    const int q = kp >> 2;
+    const int qe = q + (FP16 ? 1 : 0);          // FP16: an extra column carries the support mass
+    int e = b + tile_rows_of(kp);
+    if (u + 1 < ntiles) e = min(e, a.tbeg[u + 1]);
+    e = min(e, a.N);
+    const int n = e - b;
     const size_t base = a.roff[b];
-    const int kp = sh.q * 4;
-    float4 carry[2] = {f4(0.f), f4(0.f)};
-    float ncarry = 0.f;
-    for (int gend = e; gend > b; gend -= sh.rpw) {
-        const int r = gend - sh.rpw + sh.rsub;
-        const bool act = r >= b;
-        float4 A[2] = {f4(0.f), f4(0.f)};
-        float m = 0.f, An = 0.f;
-        RowInfo ri;
-        if (act) {
-            if (r + 1 < e) {
-                float s1 = a.rs[r + 1];
+    int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
+
+    // ---- phase 1: the affine inputs of every (row, column) of the tile, all loads in flight
+#pragma unroll 4
+    for (int idx = lane; idx < n * qe; idx += 32) {
+        const int r = idx / qe, j = idx - r * qe, row = b + r;
+        float4 x;
+        if (UP) {
+            if (j < q) {
+                const int v = a.lay[row];
+                float t[4];
+                if (a.Ein) {
+                    const float* er = a.Ein + (size_t)v * a.X;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
+                } else {
+                    int lab[4];
+                    slot_labels(a, row, j, lab, nullptr);
+                    const int px = v % a.W, py = v / a.W;
+                    const int4 Lp = a.imL[v];
+                    const int4* Rrow = a.imR + (size_t)py * a.W;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
+                }
+                x = make_float4(t[0], t[1], t[2], t[3]);
+                const uint32_t l0 = a.lcoff[row], l1 = a.lcoff[row + 1];
+                for (uint32_t c = l0; c < l1; ++c) {
+                    const int cr = a.lcrow[c];
+                    const float sc = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
+                    x = fma4(sc, load_row4_cg<FP16>(a, a.roff[cr] + 4 * j), x);
+                }
+            } else {
+                float mass = 1.f;
+                const uint32_t l0 = a.lcoff[row], l1 = a.lcoff[row + 1];
+                for (uint32_t c = l0; c < l1; ++c) {
+                    const int cr = a.lcrow[c];
+                    mass = fmaf(fabsf(a.rs[cr]), __ldcg(a.nup + cr), mass);
+                }
+                x = make_float4(mass, 0.f, 0.f, 0.f);
+            }
+        } else {
+            const float s = a.rs[row];
+            const bool top = signbit(s);
+            const float sv = fabsf(s), w = 1.f - sv * sv;
+            const int pr = top ? a.prow[row] : -1;
+            if (j < q) {
+                float4 U = load_row4<FP16>(a, base + (size_t)r * kp + 4 * j);
+                if (FP16) {
+                    const float nu = a.nup[row];
+                    U = make_float4(U.x * nu, U.y * nu, U.z * nu, U.w * nu);
+                }
+                x = make_float4(w * U.x, w * U.y, w * U.z, w * U.w);
+                if (pr >= 0) {
+                    const float4 cp = FP16 ? load_row4_cg<FP16>(a, a.roff[pr] + 4 * j)
+                                           : __ldcg((const float4*)(a.vout + a.roff[pr] + 4 * j));
+                    x = fma4(sv * (FP16 ? __ldcg(a.nd + pr) : 1.f), cp, x);
+                }
+            } else {
+                float mass = w * a.nup[row];
+                if (pr >= 0) mass = fmaf(sv, __ldcg(a.nd + pr), mass);
+                x = make_float4(mass, 0.f, 0.f, 0.f);
+            }
+        }
+        X[idx] = x;
+    }
+    for (int r = lane; r < n; r += 32) {
+        const int row = b + r;
+        float m;
+        if (UP) {
+            m = 0.f;
+            if (row + 1 < a.N) {
+                const float s1 = a.rs[row + 1];
                 m = signbit(s1) ? 0.f : s1;
             }
-            row_labels(a, r, sh.col0, sh.fpl, sh.q, ri);
-            const int v = a.lay[r];
-            const int px = v % a.W, py = v / a.W;
-            const int4 Lp = a.imL[v];
-            const int4* Rrow = a.imR + (size_t)py * a.W;
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                float t[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    int x = ri.lab[4 * f + i];
-                    t[i] = x >= 0 ? cost_m(Lp, Rrow[max(px - x, 0)], a.ck) : 0.f;
-                }
-                A[f] = make_float4(t[0], t[1], t[2], t[3]);
-            }
-            An = 1.f;
-            const uint32_t l0 = a.lcoff[r], l1 = a.lcoff[r + 1];
-            for (uint32_t j = l0; j < l1; ++j) {
-                const int c = a.lcrow[j];
-                const float sc = fabsf(a.rs[c]);
-                const size_t co = a.roff[c];
-                const float nc = FP16 ? a.nup[c] : 1.f;
-#pragma unroll
-                for (int f = 0; f < 2; ++f) {
-                    int col = sh.col0 + 32 * f;
-                    if (f < sh.fpl && col < sh.q) A[f] = fma4(sc * nc, load_row4<FP16>(a, co + 4 * col), A[f]);
-                }
-                if (FP16) An = fmaf(sc, nc, An);
-            }
+        } else {
+            const float s = a.rs[row];
+            m = signbit(s) ? 0.f : s;
         }
-        // suffix scan of affine maps (A, m) across the rows of the group
-        for (int dlt = 1; dlt < sh.rpw; dlt <<= 1) {
-            const int src = dlt * sh.lpr;
-            float4 o0 = shfl_down4(A[0], src), o1 = shfl_down4(A[1], src);
-            float om = __shfl_down_sync(0xffffffffu, m, src);
-            float on = __shfl_down_sync(0xffffffffu, An, src);
-            if (sh.rsub + dlt < sh.rpw) {
-                A[0] = fma4(m, o0, A[0]);
-                A[1] = fma4(m, o1, A[1]);
-                if (FP16) An = fmaf(m, on, An);
-                m *= om;
-            }
-        }
-        float4 x0 = fma4(m, carry[0], A[0]);
-        float4 x1 = fma4(m, carry[1], A[1]);
-        float nx = FP16 ? fmaf(m, ncarry, An) : 1.f;
-        if (act) {
-            const size_t ro = base + (size_t)(r - b) * kp;
-            const float sc = FP16 ? 1.f / nx : 1.f;
-            if (sh.col0 < sh.q) store_row4<FP16>(a, ro + 4 * sh.col0, FP16 ? make_float4(x0.x * sc, x0.y * sc, x0.z * sc, x0.w * sc) : x0);
-            if (sh.fpl > 1 && sh.col0 + 32 < sh.q)
-                store_row4<FP16>(a, ro + 4 * (sh.col0 + 32), FP16 ? make_float4(x1.x * sc, x1.y * sc, x1.z * sc, x1.w * sc) : x1);
-            if (FP16 && sh.col0 == 0) a.nup[r] = nx;
-        }
-        carry[0] = shfl4(x0, sh.col0);
-        carry[1] = shfl4(x1, sh.col0);
-        if (FP16) ncarry = __shfl_sync(0xffffffffu, nx, 0);
+        M[r] = m;
     }
-}
+    __syncwarp();
 
-template <bool FP16>
-__device__ void down_unit(const AggArgs& a, int u, int nunits)
-{
-    const int b = a.ubeg[u];
-    const int e = u + 1 < nunits ? a.ubeg[u + 1] : a.N;
-    const Shape sh = unit_shape(a.kp[b]);
-    const size_t base = a.roff[b];
-    const int kp = sh.q * 4;
-    float4 carry[2] = {f4(0.f), f4(0.f)};
-    float ncarry = 0.f;
-    for (int gs = b; gs < e; gs += sh.rpw) {
-        const int r = gs + sh.rsub;
-        const bool act = r < e;
-        float4 B[2] = {f4(0.f), f4(0.f)};
-        float m = 0.f, Bn = 0.f, nu = 1.f;
-        if (act) {
-            const float s = a.rs[r];
-            const bool top = signbit(s);
-            const float sv = fabsf(s);
-            m = top ? 0.f : sv;
-            const float w = 1.f - sv * sv;
-            const size_t ro = base + (size_t)(r - b) * kp;
-            const int pr = top ? a.prow[r] : -1;
-            const size_t po = pr >= 0 ? a.roff[pr] : 0;
-            if (FP16) nu = a.nup[r];
-            const float np = FP16 && pr >= 0 ? a.nd[pr] : 1.f;
+    // ---- phase 2: scan in recurrence order t (row = n-1-t going up, t going down)
+    const int G = qe >= 32 ? 32 : (qe <= 1 ? 1 : 1 << (32 - __clz(qe - 1)));
+    const int C = 32 / G;
+    const int col = lane % G, chunk = lane / G;
+    const int len = (n + C - 1) / C;
+    const int t0 = min(n, chunk * len), t1 = min(n, t0 + len);
+    float4 acc[3] = {f4(0.f), f4(0.f), f4(0.f)};
+    float accM = 1.f;
+    for (int t = t0; t < t1; ++t) {
+        const int r = UP ? n - 1 - t : t;
+        const float m = M[r];
 #pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                int col = sh.col0 + 32 * f;
-                if (f < sh.fpl && col < sh.q) {
-                    float4 U = load_row4<FP16>(a, ro + 4 * col);
-                    if (FP16) U = make_float4(U.x * nu, U.y * nu, U.z * nu, U.w * nu);
-                    float4 bb = make_float4(w * U.x, w * U.y, w * U.z, w * U.w);
-                    if (pr >= 0) bb = fma4(sv * np, load_row4<FP16>(a, po + 4 * col), bb);
-                    B[f] = bb;
+        for (int k = 0; k < 3; ++k) {
+            const int j = col + G * k;
+            if (j < qe) {
+                acc[k] = fma4(m, acc[k], X[r * qe + j]);
+                X[r * qe + j] = acc[k];
+            }
+        }
+        accM *= m;
+        if (col == 0) P[r] = accM;
+    }
+    float4 inc[3] = {acc[0], acc[1], acc[2]};
+    float incM = accM;
+    for (int d = 1; d < C; d <<= 1) {
+        float4 o0 = shfl_up4(inc[0], d * G), o1 = shfl_up4(inc[1], d * G), o2 = shfl_up4(inc[2], d * G);
+        const float om = __shfl_up_sync(0xffffffffu, incM, d * G);
+        if (chunk >= d) {
+            inc[0] = fma4(incM, o0, inc[0]);
+            inc[1] = fma4(incM, o1, inc[1]);
+            inc[2] = fma4(incM, o2, inc[2]);
+            incM *= om;
+        }
+    }
+    float4 carry[3] = {shfl_up4(inc[0], G), shfl_up4(inc[1], G), shfl_up4(inc[2], G)};
+    float mprev = __shfl_up_sync(0xffffffffu, incM, G);
+    if (chunk == 0) {
+        carry[0] = carry[1] = carry[2] = f4(0.f);
+        mprev = 1.f;
+    }
+    __syncwarp();
+    for (int t = t0; t < t1; ++t) {
+        const int r = UP ? n - 1 - t : t;
+        const float p = P[r];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int j = col + G * k;
+            if (j < qe) X[r * qe + j] = fma4(p, carry[k], X[r * qe + j]);
+        }
+        if (col == 0) PT[r] = p * mprev;
+    }
+    __syncwarp();
+
+    // ---- phase 3: carry from the neighbouring tile of the same path.  Tiles of a
+    // path sit at consecutive indices; a tile that links to its neighbour
+    // publishes its aggregate (A, M), then looks back 32 tiles at a time for the
+    // nearest inclusive value and composes the aggregates in between from the
+    // inner end outwards (the same arithmetic whoever evaluates it).  With no
+    // inclusive value within reach it waits for one to appear.
+    const int rfirst = UP ? n - 1 : 0;   // first row in recurrence order
+    const int rlast = UP ? 0 : n - 1;    // boundary row handed to the next tile
+    const bool need = M[rfirst] != 0.f;
+    const int nf = 4 * qe;
+    if (need) {
+        float* dst = a.aggA + (size_t)u * SCR_STRIDE;
+        const float* xl = (const float*)(X + rlast * qe);
+        for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
+        if (lane == 0) a.aggM[u] = PT[rlast];
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicExch(flags + u, 1);
+        const int dir = UP ? 1 : -1;
+        int kI = -1;          // position (1..32) of the inclusive value, relative to u
+        unsigned it = 0;
+        for (;;) {
+            const int jt = u + dir * (lane + 1);
+            // a neighbour outside the tile range would be a chain start with value 0
+            int f = (jt >= 0 && jt < ntiles) ? *(volatile int*)(flags + jt) : 3;
+            const unsigned incl = __ballot_sync(0xffffffffu, f >= 2);
+            const unsigned none = __ballot_sync(0xffffffffu, f == 0);
+            if (incl) {
+                const int k = __ffs(incl);          // 1-based
+                const unsigned before = k == 1 ? 0u : (0xffffffffu >> (33 - k));
+                if (!(none & before)) { kI = k; break; }
+            }
+            if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+                dev_fail(a.st, DEV_TIMEOUT, 51);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+            // multiplier of the tile `lane + 1` steps back, shared by all columns
+        const int jm = u + dir * (lane + 1);
+        const float mk = (lane + 1 < kI && jm >= 0 && jm < ntiles) ? __ldcg(a.aggM + jm) : 0.f;
+        for (int f0 = 0; f0 < nf; f0 += 32) {      // warp-uniform trip count (shuffles inside)
+            const int f = f0 + lane;
+            const bool ok = f < nf;
+            float cval = 0.f;
+            if (kI > 0) {
+                const int jI = u + dir * kI;
+                cval = (ok && jI >= 0 && jI < ntiles) ? __ldcg(a.inclA + (size_t)jI * SCR_STRIDE + f) : 0.f;
+                float av[31];
+#pragma unroll
+                for (int k = 1; k < 32; ++k) {
+                    const int jj = u + dir * k;
+                    av[k - 1] = (ok && k < kI) ? __ldcg(a.aggA + (size_t)jj * SCR_STRIDE + f) : 0.f;
+                }
+#pragma unroll
+                for (int k = 31; k >= 1; --k) {
+                    const float m = __shfl_sync(0xffffffffu, mk, k - 1);
+                    if (k < kI) cval = fmaf(m, cval, av[k - 1]);
                 }
             }
-            if (FP16) Bn = fmaf(sv, pr >= 0 ? np : 0.f, w * nu);
+            if (ok) ((float*)CIN)[f] = cval;
         }
-        // prefix scan of affine maps across the rows of the group
-        for (int dlt = 1; dlt < sh.rpw; dlt <<= 1) {
-            const int src = dlt * sh.lpr;
-            float4 o0 = shfl_up4(B[0], src), o1 = shfl_up4(B[1], src);
-            float om = __shfl_up_sync(0xffffffffu, m, src);
-            float on = __shfl_up_sync(0xffffffffu, Bn, src);
-            if (sh.rsub >= dlt) {
-                B[0] = fma4(m, o0, B[0]);
-                B[1] = fma4(m, o1, B[1]);
-                if (FP16) Bn = fmaf(m, on, Bn);
-                m *= om;
-            }
-        }
-        float4 x0 = fma4(m, carry[0], B[0]);
-        float4 x1 = fma4(m, carry[1], B[1]);
-        float nx = FP16 ? fmaf(m, ncarry, Bn) : 1.f;
-        // WTA over this row's slots (lowest label on ties)
-        float bv = INFINITY;
-        int bl = INT_MAX;
-        if (act) {
-            RowInfo ri;
-            row_labels(a, r, sh.col0, sh.fpl, sh.q, ri);
-            float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                int lab = ri.lab[i];
-                if (lab >= 0 && (xs[i] < bv || (xs[i] == bv && lab < bl))) { bv = xs[i]; bl = lab; }
-            }
-            const size_t ro = base + (size_t)(r - b) * kp;
-            const float sc = FP16 ? 1.f / nx : 1.f;
-            if (sh.col0 < sh.q) store_row4<FP16>(a, ro + 4 * sh.col0, FP16 ? make_float4(x0.x * sc, x0.y * sc, x0.z * sc, x0.w * sc) : x0);
-            if (sh.fpl > 1 && sh.col0 + 32 < sh.q)
-                store_row4<FP16>(a, ro + 4 * (sh.col0 + 32), FP16 ? make_float4(x1.x * sc, x1.y * sc, x1.z * sc, x1.w * sc) : x1);
-            if (FP16 && sh.col0 == 0) a.nd[r] = nx;
-        }
-        for (int o = sh.lpr >> 1; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (ov < bv || (ov == bv && ol < bl)) { bv = ov; bl = ol; }
-        }
-        if (act && sh.col0 == 0) a.disp[a.lay[r]] = bl == INT_MAX ? -1 : bl;
-        const int last = (sh.rpw - 1) * sh.lpr + sh.col0;
-        carry[0] = shfl4(x0, last);
-        carry[1] = shfl4(x1, last);
-        if (FP16) ncarry = __shfl_sync(0xffffffffu, nx, (sh.rpw - 1) * sh.lpr);
+    } else {
+        for (int f = lane; f < nf; f += 32) ((float*)CIN)[f] = 0.f;
     }
+    __syncwarp();
+
+    // ---- phase 4: final values, stores, inclusive value for the next tile
+    for (int idx = lane; idx < n * qe; idx += 32) {
+        const int r = idx / qe, j = idx - r * qe;
+        X[idx] = fma4(PT[r], CIN[j], X[idx]);
+    }
+    __syncwarp();
+    for (int idx = lane; idx < n * q; idx += 32) {
+        const int r = idx / q, j = idx - r * q;
+        float4 x = X[r * qe + j];
+        if (FP16) {
+            const float inv = 1.f / X[r * qe + q].x;
+            x = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);
+        }
+        if (!FP16 && !UP) *(float4*)(a.vout + base + (size_t)r * kp + 4 * j) = x;
+        else store_row4<FP16>(a, base + (size_t)r * kp + 4 * j, x);
+    }
+    if (FP16)
+        for (int r = lane; r < n; r += 32) (UP ? a.nup : a.nd)[b + r] = X[r * qe + q].x;
+    {
+        float* dst = a.inclA + (size_t)u * SCR_STRIDE;
+        const float* xl = (const float*)(X + rlast * qe);
+        for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicExch(flags + u, 2);
+    }
+
+    // ---- phase 5 (down pass): WTA, lowest label on ties
+    if (!UP) {
+        if (q >= 8) {
+            for (int r = 0; r < n; ++r) {
+                const int row = b + r;
+                int k = 0;
+                int dummy[4];
+                slot_labels(a, row, 0, dummy, &k);
+                float bv = INFINITY;
+                int bs = INT_MAX;
+                for (int j = lane; j < q; j += 32) {
+                    const float4 x = X[r * qe + j];
+                    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int slot = 4 * j + i;
+                        if (slot < k && xs[i] < bv) { bv = xs[i]; bs = slot; }
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+                    if (ov < bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
+                }
+                if (lane == 0) {
+                    int lab[4];
+                    slot_labels(a, row, bs >> 2, lab, nullptr);
+                    a.disp[a.lay[row]] = lab[bs & 3];
+                }
+            }
+        } else {
+            for (int r = lane; r < n; r += 32) {
+                const int row = b + r;
+                int k = 0;
+                int dummy[4];
+                slot_labels(a, row, 0, dummy, &k);
+                float bv = INFINITY;
+                int bs = 0;
+                for (int j = 0; j < q; ++j) {
+                    const float4 x = X[r * qe + j];
+                    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int slot = 4 * j + i;
+                        if (slot < k && xs[i] < bv) { bv = xs[i]; bs = slot; }
+                    }
+                }
+                int lab[4];
+                slot_labels(a, row, bs >> 2, lab, nullptr);
+                a.disp[a.lay[row]] = lab[bs & 3];
+            }
+        }
+    }
+    __syncwarp();
 }
 
 template <bool FP16, bool UP>
 __global__ void __launch_bounds__(AGG_THREADS) k_agg(AggArgs a)
 {
+    extern __shared__ float4 smem[];
     const int cnt = a.lvl_count[a.level];
     if (cnt == 0) return;
     const int first = a.lvl_first[a.level];
-    const int nunits = *a.d_nunits;
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int xcap = FP16 ? 2 * TILE_ROWS_MAX : TILE_ROWS_MAX;   // float4 per warp
+    float4* X = smem + (size_t)warp * (xcap + 3 * TILE_ROWS_MAX / 4 + 80);
+    float* M = (float*)(X + xcap);
+    float* P = M + TILE_ROWS_MAX;
+    float* PT = P + TILE_ROWS_MAX;
+    float4* CIN = (float4*)(PT + TILE_ROWS_MAX);
     int* tk = a.tickets + (UP ? 0 : MAX_LIGHT_LEVELS) + a.level;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(tk, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= cnt) break;
-        const int u = first + t;
-        if (UP) up_unit<FP16>(a, u, nunits);
-        else down_unit<FP16>(a, u, nunits);
+        // up: bottom tiles first (carries flow upwards); down: top tiles first.
+        // A tile only waits on tiles with earlier tickets, so the waits end.
+        const int u = UP ? first + cnt - 1 - t : first + t;
+        tile_pass<FP16, UP>(a, u, X, M, P, PT, CIN);
     }
+}
+
+static size_t agg_smem(bool fp16)
+{
+    const size_t xcap = fp16 ? 2 * TILE_ROWS_MAX : TILE_ROWS_MAX;
+    return (size_t)AGG_WARPS * (xcap + 3 * TILE_ROWS_MAX / 4 + 80) * sizeof(float4);
 }
 
 CostK cost_consts(const Ctx& c, int l)
@@ -380,7 +545,19 @@ CostK cost_consts(const Ctx& c, int l)
     return k;
 }
 
-void launch_aggregate(Ctx& c, int l)
+template <bool FP16, bool UP>
+static void launch_level(const AggArgs& a, int blocks, cudaStream_t s)
+{
+    const size_t sm = agg_smem(FP16);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_agg<FP16, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        configured = true;
+    }
+    k_agg<FP16, UP><<<blocks, AGG_THREADS, sm, s>>>(a);
+}
+
+void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
 {
     const LayerDims& d = c.dim[l];
     const bool hdp = c.p.mode == HDP_MODE_HDP && l < c.top;
@@ -401,31 +578,44 @@ void launch_aggregate(Ctx& c, int l)
     a.lcrow = c.lcrow;
     a.roff = c.roff;
     a.kp = c.kp;
-    a.ubeg = c.ubeg;
-    a.d_nunits = c.ints + IDX_NUNITS;
+    a.tbeg = c.ubeg;
+    a.tstart = c.ustart_flag;
+    a.tid = c.uid;
+    a.d_ntiles = c.ints + IDX_NUNITS;
     a.lvl_first = c.lvl_first;
     a.lvl_count = c.lvl_count;
-    a.vol = c.vol;
+    a.vol = vol_up ? vol_up : c.vol;
+    a.vout = vol_down ? vol_down : a.vol;
+    a.Ein = Ein;
+    a.X = d.d + 1;
     a.volh = c.volh;
     a.nup = c.nup;
     a.nd = c.nfull;
     a.tickets = c.tickets;
+    a.tflags = c.tflags;
+    a.aggA = c.aggA;
+    a.inclA = c.inclA;
+    a.aggM = c.aggM;
     a.disp = c.disp[l];
     a.st = c.st;
+    // light depth is at most floor(log2 N): one launch per possible level
     int levels = 1;
     while ((1 << levels) <= d.N) ++levels;
     if (levels > MAX_LIGHT_LEVELS) levels = MAX_LIGHT_LEVELS;
     cudaMemsetAsync(c.tickets, 0, sizeof(int) * 2 * MAX_LIGHT_LEVELS, c.s);
-    const int blocks = c.num_sms * 8;
+    cudaMemsetAsync(c.tflags, 0, sizeof(int) * 2 * c.max_tiles, c.s);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
+    const int blocks = c.num_sms * 3;
     for (int lv = levels - 1; lv >= 0; --lv) {
         a.level = lv;
-        if (fp16) k_agg<true, true><<<blocks, AGG_THREADS, 0, c.s>>>(a);
-        else k_agg<false, true><<<blocks, AGG_THREADS, 0, c.s>>>(a);
+        if (fp16) launch_level<true, true>(a, blocks, c.s);
+        else launch_level<false, true>(a, blocks, c.s);
     }
     for (int lv = 0; lv < levels; ++lv) {
         a.level = lv;
-        if (fp16) k_agg<true, false><<<blocks, AGG_THREADS, 0, c.s>>>(a);
-        else k_agg<false, false><<<blocks, AGG_THREADS, 0, c.s>>>(a);
+        if (fp16) launch_level<true, false>(a, blocks, c.s);
+        else launch_level<false, false>(a, blocks, c.s);
     }
 }
+
+void launch_aggregate(Ctx& c, int l) { launch_aggregate_ex(c, l, nullptr, nullptr, nullptr); }

@@ -51,7 +51,7 @@ __device__ __forceinline__ bool grid_sync(DevStatus* st, unsigned nblocks)
                     dev_fail(st, DEV_TIMEOUT, 1);
                     break;
                 }
-                __nanosleep(100);
+                if (it > 2048) __nanosleep(100);   // spin tight first: most barriers complete within microseconds
             }
         }
         __threadfence();

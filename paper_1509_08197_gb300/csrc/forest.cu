@@ -20,7 +20,7 @@
 //    sequential algorithm would.
 #include "hdp_impl.cuh"
 
-#define FOREST_THREADS 256
+#define FOREST_THREADS 512
 
 int edge_bits(int N)
 {
@@ -41,6 +41,7 @@ struct ForestArgs {
     int* size;
     int* intw;
     int* best;
+    int* best2;          // second reservation array: Boruvka alternates between the two
     uint8_t* in_tree;
     int *listA, *listB, *raA, *rbA, *raB, *rbB, *hooked;
     int* ctr;
@@ -81,10 +82,14 @@ __device__ __forceinline__ void append(const ForestArgs& a, int which, int idx, 
     RB[pos] = rb;
 }
 
-// Boruvka rounds on the candidate list `cur` (best[] holds each root's
+__device__ __forceinline__ int* best_of(const ForestArgs& a, int par) { return par ? a.best2 : a.best; }
+
+// Boruvka rounds on the candidate list `cur` (best_of(par) holds each root's
 // smallest candidate index).  Every root hooks onto the other end of its
 // smallest edge; a pair that chose the same edge keeps the smaller root.
-__device__ bool boruvka_rounds(const ForestArgs& a, int& cur, bool record_hooks)
+// Two reservation arrays alternate, so clearing one overlaps the selection
+// into the other: two grid barriers per round.
+__device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool record_hooks, int wclass = 0)
 {
     const unsigned nb = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
@@ -94,39 +99,55 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, bool record_hooks)
         const int* L = cur ? a.listB : a.listA;
         const int* RA = cur ? a.raB : a.raA;
         const int* RB = cur ? a.rbB : a.rbA;
+        int* best = best_of(a, par);
+        int* bnext = best_of(a, par ^ 1);
+        int* hk = a.hooked + (par ? (size_t)a.N : 0);   // this round's hooked roots (two lists alternate)
+        const int nxt = cur ^ 1;
         for (int j = tid; j < m; j += nth) {
             int idx = L[j], ra = RA[j], rb = RB[j];
-            int ba = __ldcg(a.best + ra), bb = __ldcg(a.best + rb);
+            int ba = __ldcg(best + ra), bb = __ldcg(best + rb);
             if (ba == idx || bb == idx) a.in_tree[a.keys[idx] & ((1u << a.ebits) - 1u)] = 1;
             if (ba == idx && !(bb == idx && ra < rb)) {
                 __stcg(a.parent + ra, rb);
-                if (record_hooks) a.hooked[atomicAdd(a.ctr + 2, 1)] = ra;
+                if (record_hooks) hk[atomicAdd(a.ctr + 2 + par, 1)] = ra;
             }
             if (bb == idx && !(ba == idx && rb < ra)) {
                 __stcg(a.parent + rb, ra);
-                if (record_hooks) a.hooked[atomicAdd(a.ctr + 2, 1)] = rb;
+                if (record_hooks) hk[atomicAdd(a.ctr + 2 + par, 1)] = rb;
             }
         }
-        if (!grid_sync(a.st, nb)) return false;
-        const int nxt = cur ^ 1;
-        for (int j = tid; j < m; j += nth) {
-            __stcg(a.best + RA[j], INT_MAX);
-            __stcg(a.best + RB[j], INT_MAX);
+        if (tid == 0) {
+            a.ctr[nxt] = 0;
+            a.ctr[2 + (par ^ 1)] = 0;   // the other hooked list was consumed last round, before a barrier
         }
-        if (tid == 0) a.ctr[nxt] = 0;
         if (!grid_sync(a.st, nb)) return false;
+        if (record_hooks) {
+            // roots hooked in this round fold their (complete) sizes into the
+            // roots they now hang from; those are roots after every hook of the
+            // round and receive no hook themselves, so the sums are exact
+            const int nh = __ldcg(a.ctr + 2 + par);
+            for (int j = tid; j < nh; j += nth) {
+                const int r = hk[j];
+                const int R = uf_find(a.parent, r);
+                atomicAdd(a.size + R, __ldcg(a.size + r));
+                __stcg(a.intw + R, wclass);
+            }
+        }
         for (int j = tid; j < m; j += nth) {
+            __stcg(best + RA[j], INT_MAX);
+            __stcg(best + RB[j], INT_MAX);
             int idx = L[j], e, w, p, q;
             decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
             int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
             if (ra != rb) {
-                atomicMin(a.best + ra, idx);
-                atomicMin(a.best + rb, idx);
+                atomicMin(bnext + ra, idx);
+                atomicMin(bnext + rb, idx);
                 append(a, nxt, idx, ra, rb);
             }
         }
         if (!grid_sync(a.st, nb)) return false;
         cur = nxt;
+        par ^= 1;
     }
     dev_fail(a.st, DEV_TIMEOUT, 20);
     return false;
@@ -153,8 +174,8 @@ __global__ void k_boruvka(ForestArgs a)
         }
     }
     if (!grid_sync(a.st, gridDim.x)) return;
-    int cur = 0;
-    boruvka_rounds(a, cur, false);
+    int cur = 0, par = 0;
+    boruvka_rounds(a, cur, par, false);
 }
 
 // Segment-tree first pass, one weight class at a time (see file comment).
@@ -163,7 +184,7 @@ __global__ void k_fh(ForestArgs a)
     if (a.risky && __ldcg(a.risky)) return;
     const int n = *a.d_n, ncls = *a.d_ncls;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    int cur = 0;
+    int cur = 0, par = 0;
     for (int c = 0; c < ncls; ++c) {
         const int s = a.cls_start[c];
         const int e_end = c + 1 < ncls ? a.cls_start[c + 1] : n;
@@ -177,24 +198,15 @@ __global__ void k_fh(ForestArgs a)
             long long sa = __ldcg(a.size + ra), sb = __ldcg(a.size + rb);
             long long ia = __ldcg(a.intw + ra), ib = __ldcg(a.intw + rb);
             if ((w - ia) * sa > a.kq || (w - ib) * sb > a.kq) continue;
-            atomicMin(a.best + ra, idx);
-            atomicMin(a.best + rb, idx);
+            atomicMin(best_of(a, par) + ra, idx);
+            atomicMin(best_of(a, par) + rb, idx);
             append(a, cur, idx, ra, rb);
         }
         if (!grid_sync(a.st, gridDim.x)) return;
         if (__ldcg(a.ctr + cur) == 0) continue;
-        if (!boruvka_rounds(a, cur, true)) return;
-        // the class is done: fold the sizes of hooked roots into their final
-        // roots and set Int = w for every tree that merged in this class
-        const int nh = __ldcg(a.ctr + 2);
-        for (int j = tid; j < nh; j += nth) {
-            int r = a.hooked[j];
-            int R = uf_find(a.parent, r);
-            atomicAdd(a.size + R, __ldcg(a.size + r));
-            __stcg(a.intw + R, (int)w);
-        }
-        if (!grid_sync(a.st, gridDim.x)) return;
-        if (tid == 0) a.ctr[2] = 0;
+        // sizes and Int = w of the trees merged in this class are folded inside
+        // the rounds; a tree's criterion is only read at the start of a class
+        if (!boruvka_rounds(a, cur, par, true, (int)w)) return;
     }
 }
 
@@ -225,12 +237,37 @@ __device__ int block_excl_sum(int v, int* smem, int* total)
     return r;
 }
 
+// single block: plain (L1-cached) accesses; the block's own writes are visible
+// to it after __syncthreads.  Grid: through L2, which all SMs share.
+template <bool SINGLE> __device__ __forceinline__ int ldv(const int* p) { return SINGLE ? *p : __ldcg(p); }
+template <bool SINGLE> __device__ __forceinline__ uint32_t ldv(const uint32_t* p) { return SINGLE ? *p : __ldcg(p); }
+template <bool SINGLE> __device__ __forceinline__ void stv(int* p, int v) { if (SINGLE) *p = v; else __stcg(p, v); }
+template <bool SINGLE> __device__ __forceinline__ void stv(uint32_t* p, uint32_t v) { if (SINGLE) *p = v; else __stcg(p, v); }
+
+// union-find root for one block (plain loads: the block's own writes are
+// visible to it after __syncthreads)
+template <bool SINGLE>
+__device__ __forceinline__ int uf_find_t(int* parent, int v)
+{
+    if (!SINGLE) return uf_find(parent, v);
+    for (int it = 0; it < (1 << 26); ++it) {
+        int p = parent[v];
+        if (p == v) return v;
+        int gp = parent[p];
+        if (gp == p) return p;
+        parent[v] = gp;
+        v = gp;
+    }
+    return v;
+}
+
 // Deterministic reservations over windows of the sorted list.  ctr[3] = window
 // size, ctr[4] = next fresh list index.  best[] holds window positions.
+template <bool SINGLE>
 __global__ void k_dr(ForestArgs a, int only_if_risky)
 {
     __shared__ int smem[33];
-    if (only_if_risky && !__ldcg(a.risky)) return;
+    if (only_if_risky && !ldv<SINGLE>(a.risky)) return;
     const unsigned nb = gridDim.x;
     const int n = *a.d_n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
@@ -243,19 +280,19 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
         for (long long round = 0;; ++round) {
             if (round > (1LL << 30)) { dev_fail(a.st, DEV_TIMEOUT, 30); return; }
             if (blockIdx.x == 0) {
-                int k = __ldcg(a.ctr + 3), nx = __ldcg(a.ctr + 4);
+                int k = ldv<SINGLE>(a.ctr + 3), nx = ldv<SINGLE>(a.ctr + 4);
                 int add = min(a.WIN - k, n - nx);
                 for (int t = threadIdx.x; t < add; t += blockDim.x) a.win[k + t] = nx + t;
                 __syncthreads();
                 if (threadIdx.x == 0) { a.ctr[3] = k + add; a.ctr[4] = nx + add; }
             }
             if (!grid_sync(a.st, nb)) return;
-            const int wc = __ldcg(a.ctr + 3);
+            const int wc = ldv<SINGLE>(a.ctr + 3);
             if (wc == 0) break;
             for (int i = tid; i < wc; i += nth) {
-                int idx = __ldcg(a.win + i), e, w, p, q;
+                int idx = ldv<SINGLE>(a.win + i), e, w, p, q;
                 decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
-                int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
+                int ra = uf_find_t<SINGLE>(a.parent, p), rb = uf_find_t<SINGLE>(a.parent, q);
                 a.wra[i] = ra;
                 a.wrb[i] = rb;
                 if (ra != rb) {
@@ -265,41 +302,41 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
             }
             if (!grid_sync(a.st, nb)) return;
             for (int i = tid; i < wc; i += nth) {
-                int ra = __ldcg(a.wra + i), rb = __ldcg(a.wrb + i);
+                int ra = ldv<SINGLE>(a.wra + i), rb = ldv<SINGLE>(a.wrb + i);
                 int done = 1;
                 if (ra != rb) {
-                    if (__ldcg(a.best + ra) == i && __ldcg(a.best + rb) == i) {
-                        int idx = __ldcg(a.win + i), e, w, p, q;
+                    if (ldv<SINGLE>(a.best + ra) == i && ldv<SINGLE>(a.best + rb) == i) {
+                        int idx = ldv<SINGLE>(a.win + i), e, w, p, q;
                         decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
                         bool ok = true;
                         if (!full) {
                             int inter = 0, uni = 0;
 #pragma unroll
                             for (int k = 0; k < HDP_WORDS; ++k) {
-                                uint32_t ta = __ldcg(a.T + (size_t)ra * HDP_WORDS + k);
-                                uint32_t tb = __ldcg(a.T + (size_t)rb * HDP_WORDS + k);
+                                uint32_t ta = ldv<SINGLE>(a.T + (size_t)ra * HDP_WORDS + k);
+                                uint32_t tb = ldv<SINGLE>(a.T + (size_t)rb * HDP_WORDS + k);
                                 inter += __popc(ta & tb);
                                 uni += __popc(ta | tb);
                             }
                             ok = (long long)inter * a.bden >= (long long)a.bnum * uni;   // DT-Rule 2
                         }
-                        long long sa = __ldcg(a.size + ra), sb = __ldcg(a.size + rb);
+                        long long sa = ldv<SINGLE>(a.size + ra), sb = ldv<SINGLE>(a.size + rb);
                         if (ok && crit) {
-                            long long ia = __ldcg(a.intw + ra), ib = __ldcg(a.intw + rb);
+                            long long ia = ldv<SINGLE>(a.intw + ra), ib = ldv<SINGLE>(a.intw + rb);
                             ok = (long long)w * sa <= ia * sa + a.kq && (long long)w * sb <= ib * sb + a.kq;
                         }
                         if (ok) {
                             int big = ra, small = rb;
                             if (sa < sb) { big = rb; small = ra; }
-                            __stcg(a.parent + small, big);
-                            __stcg(a.size + big, (int)(sa + sb));
-                            __stcg(a.intw + big, w);
+                            stv<SINGLE>(a.parent + small, big);
+                            stv<SINGLE>(a.size + big, (int)(sa + sb));
+                            stv<SINGLE>(a.intw + big, w);
                             if (!full) {
 #pragma unroll
                                 for (int k = 0; k < HDP_WORDS; ++k) {
-                                    uint32_t u = __ldcg(a.T + (size_t)ra * HDP_WORDS + k) |
-                                                 __ldcg(a.T + (size_t)rb * HDP_WORDS + k);
-                                    __stcg(a.T + (size_t)big * HDP_WORDS + k, u);
+                                    uint32_t u = ldv<SINGLE>(a.T + (size_t)ra * HDP_WORDS + k) |
+                                                 ldv<SINGLE>(a.T + (size_t)rb * HDP_WORDS + k);
+                                    stv<SINGLE>(a.T + (size_t)big * HDP_WORDS + k, u);
                                 }
                             }
                             a.in_tree[e] = 1;
@@ -312,10 +349,10 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
             }
             if (!grid_sync(a.st, nb)) return;
             for (int i = tid; i < wc; i += nth) {
-                int ra = __ldcg(a.wra + i), rb = __ldcg(a.wrb + i);
+                int ra = ldv<SINGLE>(a.wra + i), rb = ldv<SINGLE>(a.wrb + i);
                 if (ra != rb) {
-                    __stcg(a.best + ra, INT_MAX);
-                    __stcg(a.best + rb, INT_MAX);
+                    stv<SINGLE>(a.best + ra, INT_MAX);
+                    stv<SINGLE>(a.best + rb, INT_MAX);
                 }
             }
             if (blockIdx.x == 0) {
@@ -323,11 +360,11 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
                 const int per = cdiv(wc, (int)blockDim.x);
                 const int b0 = threadIdx.x * per, b1 = min(wc, b0 + per);
                 int cnt = 0;
-                for (int i = b0; i < b1; ++i) cnt += __ldcg(a.wst + i) == 0;
+                for (int i = b0; i < b1; ++i) cnt += ldv<SINGLE>(a.wst + i) == 0;
                 int tot = 0;
                 int off = block_excl_sum(cnt, smem, &tot);
                 for (int i = b0; i < b1; ++i)
-                    if (__ldcg(a.wst + i) == 0) a.wtmp[off++] = __ldcg(a.win + i);
+                    if (ldv<SINGLE>(a.wst + i) == 0) a.wtmp[off++] = ldv<SINGLE>(a.win + i);
                 __syncthreads();
                 for (int i = threadIdx.x; i < tot; i += blockDim.x) a.win[i] = a.wtmp[i];
                 __syncthreads();
@@ -338,7 +375,7 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
     }
 }
 
-__global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int* minid, int N)
+__global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int* best2, int* minid, int N)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
@@ -346,6 +383,7 @@ __global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int*
     size[v] = 1;
     intw[v] = 0;
     best[v] = INT_MAX;
+    best2[v] = INT_MAX;
     minid[v] = INT_MAX;
 }
 
@@ -416,14 +454,15 @@ __global__ void k_adj(const uint8_t* in_tree, int W, int H, uint8_t* adj)
     adj[v] = m;
 }
 
-cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int max_blocks, int* used)
+// blocks_per_sm = 0: as many as fit; barrier-heavy kernels use 1 (fewer arrivals per barrier)
+cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    if (blocks_per_sm > 0 && per > blocks_per_sm) per = blocks_per_sm;
     int blocks = per * sms;
-    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     if (used) *used = blocks;
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
@@ -452,6 +491,7 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.size = c.csize;
     a.intw = c.intw;
     a.best = c.best;
+    a.best2 = c.best2;
     a.in_tree = c.in_tree;
     a.listA = c.listA; a.listB = c.listB;
     a.raA = c.raA; a.rbA = c.rbA; a.raB = c.raB; a.rbB = c.rbB;
@@ -468,7 +508,7 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.engine = c.ints + IDX_ENGINE;
     a.st = c.st;
 
-    k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.minid, N);
+    k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, N);
     cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
     cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
     cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);   // barrier state (keeps err)
@@ -484,15 +524,16 @@ void launch_forest(Ctx& c, int l, int hdp)
     void* args[] = {&a};
     int only_if_risky = 1;
     void* dr_args[] = {&a, &only_if_risky};
+    const void* dr_grid = (const void*)k_dr<false>;
     if (!st_tree) {
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 0, nullptr);
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
         a.passes = 1;
         a.crit_first = 0;
         a.WIN = small ? 4096 : 16384;
         if (hdp) {
             cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-            if (small) k_dr<<<1, 1024, 0, c.s>>>(a, 1);
-            else coop_launch((const void*)k_dr, FOREST_THREADS, dr_args, c.s, 0, nullptr);
+            if (small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
+            else coop_launch(dr_grid, FOREST_THREADS, dr_args, c.s, 1, nullptr);
         }
     } else if (!small) {
         // first pass by weight classes, then the linking pass by Boruvka
@@ -503,22 +544,22 @@ void launch_forest(Ctx& c, int l, int hdp)
         scan_u32(flags, pos, c.ints + IDX_NEDGES, 2 * N, true, c.tmp, total, c.s);
         k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, c.ints + IDX_NEDGES, c.cls_start, total,
                                                            c.ints + IDX_NCLS);
-        coop_launch((const void*)k_fh, FOREST_THREADS, args, c.s, 0, nullptr);
+        coop_launch((const void*)k_fh, FOREST_THREADS, args, c.s, 1, nullptr);
         cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 0, nullptr);
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 16384;
         if (hdp) {
             cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-            coop_launch((const void*)k_dr, FOREST_THREADS, dr_args, c.s, 0, nullptr);
+            coop_launch(dr_grid, FOREST_THREADS, dr_args, c.s, 1, nullptr);
         }
     } else {
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 4096;
-        k_dr<<<1, 1024, 0, c.s>>>(a, 0);
+        k_dr<true><<<1, 1024, 0, c.s>>>(a, 0);
     }
     k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
     k_finish_roots<<<cdiv(N, 256), 256, 0, c.s>>>(c.rootof, c.minid, c.dtroot, c.T, hdp ? c.pixset : nullptr,

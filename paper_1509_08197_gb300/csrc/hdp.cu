@@ -116,6 +116,7 @@ static void layout_buffers(Ctx& c)
     c.csize = carve<int>(c, N0);
     c.intw = carve<int>(c, N0);
     c.best = carve<int>(c, N0);
+    c.best2 = carve<int>(c, N0);
     c.rootof = carve<int>(c, N0);
     c.minid = carve<int>(c, N0);
     c.dtroot = carve<int>(c, N0);
@@ -127,7 +128,7 @@ static void layout_buffers(Ctx& c)
     c.rbA = carve<int>(c, E2);
     c.raB = carve<int>(c, E2);
     c.rbB = carve<int>(c, E2);
-    c.hooked = carve<int>(c, N0);
+    c.hooked = carve<int>(c, 2 * (size_t)N0);
     c.win = carve<int>(c, 16384);
     c.wtmp = carve<int>(c, 16384);
     c.wra = carve<int>(c, 16384);
@@ -167,7 +168,7 @@ static void layout_buffers(Ctx& c)
     c.rdt = carve<int>(c, N0);
     c.lcoff = carve<uint32_t>(c, N0 + 1);
     c.lcrow = carve<int>(c, N0);
-    c.nexttop = carve<int>(c, N0);
+    c.runstart = carve<int>(c, 2048);
     c.ustart_flag = carve<uint32_t>(c, N0);
     c.uid = carve<uint32_t>(c, N0);
     c.ubeg = carve<int>(c, N0);
@@ -186,6 +187,12 @@ static void layout_buffers(Ctx& c)
         K = std::max(K, (size_t)c.dim[l].N * kp);
     }
     c.vol_elems = K;
+    // every tile but the last of a run holds more than TILE_FLOATS - 256 costs
+    c.max_tiles = K / (TILE_FLOATS - 256) + 2 * 2048 + 16;
+    c.tflags = carve<int>(c, 2 * c.max_tiles);
+    c.aggA = carve<float>(c, c.max_tiles * SCR_STRIDE);
+    c.inclA = carve<float>(c, c.max_tiles * SCR_STRIDE);
+    c.aggM = carve<float>(c, c.max_tiles);
     if (c.p.storage == HDP_STORE_FP16) c.volh = carve<__half>(c, K + 8);
     else c.vol = carve<float>(c, K + 8);
 }
@@ -420,6 +427,9 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
     for (int l = 0; l < HDP_MAX_LEVELS; ++l)
         for (int k = 0; k < 6; ++k)
             if (ctx->ev[l][k]) cudaEventDestroy(ctx->ev[l][k]);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->c.gvol[i]) cudaFree(ctx->c.gvol[i]);
+    if (ctx->c.gacc) cudaFree(ctx->c.gacc);
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     delete ctx;
@@ -740,4 +750,57 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
         return rc;
     }
     return HDP_OK;
+}
+
+// ------------------------------------------------------ differentiable path ---
+static int grad_ready(hdp_ctx* ctx)
+{
+    Ctx& c = ctx->c;
+    if (!c.built || c.tree_level < 0) return fail(ctx, HDP_ERR_STATE, "no tree loaded (call hdp_build_trees)");
+    const bool full = c.p.mode == HDP_MODE_FULL || c.tree_level == c.top;
+    if (!full) return fail(ctx, HDP_ERR_STATE, "the loaded layer is not full range");
+    if (c.p.storage != HDP_STORE_FP32) return fail(ctx, HDP_ERR_ARG, "the differentiable path needs FP32 storage");
+    return HDP_OK;
+}
+
+extern "C" int hdp_aggregate_fwd(hdp_ctx* ctx, const float* d_E, float* d_C)
+{
+    if (!ctx || !d_E || !d_C) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    rc = grad_forward(ctx->c, d_E, d_C);
+    if (rc) return fail(ctx, rc, "workspace for the differentiable path");
+    return check_launch(ctx, "hdp_aggregate_fwd");
+}
+
+extern "C" int hdp_aggregate_bwd(hdp_ctx* ctx, const float* d_E, const float* d_gC, float* d_gE, float* d_gw,
+                                 float* d_ggamma)
+{
+    if (!ctx || !d_E || !d_gC || !d_gE || !d_gw || !d_ggamma) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    rc = grad_backward(ctx->c, d_E, d_gC, d_gE, d_gw, d_ggamma);
+    if (rc) return fail(ctx, rc, "workspace for the differentiable path");
+    return check_launch(ctx, "hdp_aggregate_bwd");
+}
+
+extern "C" int hdp_set_gamma(hdp_ctx* ctx, float gamma)
+{
+    if (!ctx || !(gamma > 0)) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    launch_set_gamma(ctx->c, gamma);
+    return check_launch(ctx, "hdp_set_gamma");
+}
+
+extern "C" int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const uint8_t* d_valid, float T,
+                                  float* d_disp, float* d_loss, float* d_gC)
+{
+    if (!ctx || !d_C || !(T > 0)) return HDP_ERR_ARG;
+    if ((d_loss || d_gC) && !d_gt) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    rc = launch_soft_argmin_l1(ctx->c, d_C, d_gt, d_valid, T, d_disp, d_loss, d_gC);
+    if (rc) return fail(ctx, rc, "workspace for the differentiable path");
+    return check_launch(ctx, "hdp_soft_argmin_l1");
 }

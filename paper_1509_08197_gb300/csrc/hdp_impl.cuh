@@ -10,6 +10,10 @@
 #include "prims.cuh"
 
 #define MAX_LIGHT_LEVELS 32
+// aggregation tiles: consecutive rows of one width holding about TILE_FLOATS costs
+#define TILE_FLOATS 2048
+#define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
+__host__ __device__ __forceinline__ int tile_rows_of(int kp) { return kp >= TILE_FLOATS ? 1 : TILE_FLOATS / kp; }
 
 struct LayerDims {
     int W, H, N, d;   // size and largest label of the layer
@@ -57,7 +61,7 @@ struct Ctx {
     uint32_t *keys0 = nullptr, *keys1 = nullptr;   // sorted (w << ebits | e)
     uint32_t* sorted = nullptr;      // points at keys0 or keys1
     int* cls_start = nullptr;        // weight-class starts in the sorted list
-    int *parent = nullptr, *csize = nullptr, *intw = nullptr, *best = nullptr;
+    int *parent = nullptr, *csize = nullptr, *intw = nullptr, *best = nullptr, *best2 = nullptr;
     int *rootof = nullptr, *minid = nullptr, *dtroot = nullptr;
     uint32_t* T = nullptr;           // [N][8] TreeIntv at union-find roots
     uint8_t* in_tree = nullptr;      // [2N]
@@ -88,11 +92,15 @@ struct Ctx {
     int* rdt = nullptr;              // union-find root of the row's tree (TreeIntv index)
     uint32_t* lcoff = nullptr;       // light-children offsets (N + 1)
     int* lcrow = nullptr;            // light-children rows
-    int* nexttop = nullptr;
     int* runstart = nullptr;         // per (level, width) key: first row
-    uint32_t* ustart_flag = nullptr;
-    uint32_t* uid = nullptr;
-    int *ubeg = nullptr;             // unit first row
+    uint32_t* ustart_flag = nullptr; // tile start flags
+    uint32_t* uid = nullptr;         // tile ids
+    int* ubeg = nullptr;             // tile first row
+    size_t max_tiles = 0;
+    int* tflags = nullptr;           // [2][max_tiles] look-back states (0 none, 1 aggregate, 2 inclusive)
+    float* aggA = nullptr;           // [max_tiles][SCR_STRIDE]
+    float* inclA = nullptr;          // [max_tiles][SCR_STRIDE]
+    float* aggM = nullptr;           // [max_tiles]
     int* lvl_first = nullptr;        // [MAX_LIGHT_LEVELS] first unit of the level
     int* lvl_count = nullptr;        // [MAX_LIGHT_LEVELS]
     int* tickets = nullptr;          // [2][MAX_LIGHT_LEVELS]
@@ -103,6 +111,8 @@ struct Ctx {
     __half* volh = nullptr;
     float *nup = nullptr, *nfull = nullptr;
     size_t vol_elems = 0;
+    float *gvol[4] = {nullptr, nullptr, nullptr, nullptr};   // differentiable path: U_E, C_E, U_g, G (lazy)
+    double* gacc = nullptr;
 
     // scalars on the device
     int* ints = nullptr;   // see IDX_* below
@@ -141,7 +151,15 @@ void launch_order(Ctx& c, int l);
 
 // aggregate.cu
 void launch_aggregate(Ctx& c, int l);
+void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down);
+
+// grad.cu
+int grad_forward(Ctx& c, const float* E, float* C);
+int grad_backward(Ctx& c, const float* E, const float* gC, float* gE, float* gw, float* ggamma);
+void launch_set_gamma(Ctx& c, float gamma);
+int launch_soft_argmin_l1(Ctx& c, const float* C, const float* gt, const uint8_t* valid, float T, float* disp,
+                          float* loss, float* gC);
 
 // helpers
 CostK cost_consts(const Ctx& c, int l);
-cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int max_blocks, int* used_blocks);
+cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used_blocks);

@@ -19,7 +19,6 @@
 // preorders and the light depth of every node.
 #include "hdp_impl.cuh"
 
-#define UNIT_ROWS 64
 
 __device__ __forceinline__ int nb_of(int v, int k, int W)
 {
@@ -270,34 +269,35 @@ __global__ void k_rows2(const int* lay, const int* rowof, const int* par, const 
     for (; m; m &= m - 1) lcrow[o++] = rowof[nb_of(v, __ffs(m) - 1, W)];
 }
 
-__global__ void k_top_idx(const float* rs, int N, int* out)
+// rows are sorted by key, so each (level, width) run starts where the key changes
+__global__ void k_runstart(const uint32_t* keys_sorted, int N, int* runstart)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) out[i] = signbit(rs[i]) ? i : INT_MAX;
+    if (i < N && (i == 0 || keys_sorted[i] != keys_sorted[i - 1])) runstart[keys_sorted[i]] = i;
 }
 
-// a unit starts at every (light level, width) run start and at the first path
-// top of every UNIT_ROWS-row bin; units never split a path
-__global__ void k_unit_flags(const uint32_t* keys_sorted, const int* nexttop, const float* rs, int N, uint32_t* flag)
+// a tile starts at every (light level, width) run start and every
+// tile_rows(width) rows after it; tiles may split heavy paths
+__global__ void k_tile_flags(const uint32_t* keys_sorted, const int* runstart, int N, uint32_t* flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    bool runstart = i == 0 || keys_sorted[i] != keys_sorted[i - 1];
-    bool top = signbit(rs[i]);
-    int bin = i - i % UNIT_ROWS;
-    flag[i] = runstart || (top && nexttop[bin] == i);
+    uint32_t key = keys_sorted[i];
+    int kp = 4 * (int)((key & 63u) + 1);
+    flag[i] = ((i - runstart[key]) % tile_rows_of(kp)) == 0;
 }
 
-__global__ void k_unit_fill(const uint32_t* flag, const uint32_t* uid, const uint32_t* keys_sorted, int N, int* ubeg,
-                            int* lvl_first, int* lvl_count)
+__global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uint32_t* keys_sorted, int N, int* tbeg,
+                            int* lvl_first, int* lvl_count, int max_tiles, DevStatus* st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N || !flag[i]) return;
-    int u = (int)uid[i];
-    ubeg[u] = i;
+    int t = (int)tid[i];
+    if (t >= max_tiles) { dev_fail(st, DEV_BAD_INPUT, 43); return; }
+    tbeg[t] = i;
     int lv = (int)(keys_sorted[i] >> 6);
     if (lv >= MAX_LIGHT_LEVELS) return;
-    atomicMin(lvl_first + lv, u);
+    atomicMin(lvl_first + lv, t);
     atomicAdd(lvl_count + lv, 1);
 }
 
@@ -368,12 +368,13 @@ void launch_order(Ctx& c, int l)
     k_rows2<<<g, 256, 0, s>>>(c.lay, c.rowof, c.par, c.pdir, c.hdir, c.adj, c.lcoff, N, d.W, c.prow, c.lcrow);
     scan_u32((const uint32_t*)c.kp, c.roff, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_K), s);
 
-    // units
-    k_top_idx<<<g, 256, 0, s>>>(c.rs, N, c.nexttop);
-    device_scan<int, OpMin>(c.nexttop, c.nexttop, dN, N, INT_MAX, OpMin(), false, true, (int*)c.tmp, nullptr, s);
-    k_unit_flags<<<g, 256, 0, s>>>(ksorted, c.nexttop, c.rs, N, c.ustart_flag);
+    // tiles
+    k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
+    k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
+    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.ustart_flag);
     scan_u32(c.ustart_flag, c.uid, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NUNITS), s);
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
-    k_unit_fill<<<g, 256, 0, s>>>(c.ustart_flag, c.uid, ksorted, N, c.ubeg, c.lvl_first, c.lvl_count);
+    k_tile_fill<<<g, 256, 0, s>>>(c.ustart_flag, c.uid, ksorted, N, c.ubeg, c.lvl_first, c.lvl_count, (int)c.max_tiles,
+                                  c.st);
 }
