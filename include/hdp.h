@@ -149,6 +149,20 @@ int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_righ
                       int* n_kernels);
 int hdp_graph_launch(hdp_ctx* ctx);
 
+/* Many independent pairs at once.  ctxs[i] (each created with its own
+ * stream; sizes, ranges and parameters may differ) matches d_left[i] /
+ * d_right[i] (row pitch pitch[i] bytes) into d_disp_out[i].  The work forks
+ * from the stream of ctxs[0], runs the pairs concurrently on their own
+ * streams and joins back, so the call can be captured in a CUDA graph.
+ * hdp_batch_graph_capture captures the whole batch once (the graph is kept in
+ * ctxs[0], *n_kernels receives its kernel count); hdp_batch_graph_launch
+ * replays it on the stream of ctxs[0]. */
+int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right, const int* pitch,
+                    int32_t* const* d_disp_out);
+int hdp_batch_graph_capture(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right,
+                            const int* pitch, int32_t* const* d_disp_out, int* n_kernels);
+int hdp_batch_graph_launch(hdp_ctx* ctx0);
+
 /* Differentiable aggregation (Eq. C as a function of the cost volume, the
  * edge weights and gamma) over the forest of the layer whose tree is loaded
  * (after hdp_build_trees: the top layer; with HDP_MODE_FULL the whole-image

@@ -126,6 +126,9 @@ def load(path: str = LIB_PATH):
         "hdp_aggregate_bwd": (I, [P, P, P, P, P, P]),
         "hdp_set_gamma": (I, [P, ctypes.c_float]),
         "hdp_soft_argmin_l1": (I, [P, P, P, P, ctypes.c_float, P, P, P]),
+        "hdp_match_batch": (I, [P, I, P, P, P, P]),
+        "hdp_batch_graph_capture": (I, [P, I, P, P, P, P, P]),
+        "hdp_batch_graph_launch": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -309,10 +312,37 @@ def hdp_soft_argmin_l1(ctx: Context, C, gt=None, valid=None, T=1.0, disp=None, l
                                           _optr(loss), _optr(gC)), "hdp_soft_argmin_l1")
 
 
+def _batch_arrays(ctxs, lefts, rights, outs):
+    n = len(ctxs)
+    H = (ctypes.c_void_p * n)(*[c.handle for c in ctxs])
+    L = (ctypes.c_void_p * n)(*[t.data_ptr() for t in lefts])
+    R = (ctypes.c_void_p * n)(*[t.data_ptr() for t in rights])
+    Pt = (ctypes.c_int * n)(*[3 * c.params.width for c in ctxs])
+    O = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    return n, H, L, R, Pt, O
+
+
+def hdp_match_batch(ctxs, lefts, rights, outs):
+    """Match len(ctxs) pairs concurrently (each context on its own stream)."""
+    n, H, L, R, Pt, O = _batch_arrays(ctxs, lefts, rights, outs)
+    _check(ctxs[0], load().hdp_match_batch(H, n, L, R, Pt, O), "hdp_match_batch")
+
+
+def hdp_batch_graph_capture(ctxs, lefts, rights, outs) -> int:
+    n, H, L, R, Pt, O = _batch_arrays(ctxs, lefts, rights, outs)
+    k = ctypes.c_int(0)
+    _check(ctxs[0], load().hdp_batch_graph_capture(H, n, L, R, Pt, O, ctypes.byref(k)), "hdp_batch_graph_capture")
+    return k.value
+
+
+def hdp_batch_graph_launch(ctx0):
+    _check(ctx0, load().hdp_batch_graph_launch(ctx0.handle), "hdp_batch_graph_launch")
+
+
 def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
     return ["hdp_default_params", "hdp_create", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
-            "hdp_soft_argmin_l1"]
+            "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch"]

@@ -169,6 +169,50 @@ __device__ __forceinline__ void store_row4(const AggArgs& a, size_t off, float4 
     }
 }
 
+// ---- TMA bulk copies (untiled cp.async.bulk): 16-byte aligned addresses and sizes
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+    return ok != 0;
+}
+// bounded wait for a bulk load; on timeout the error is recorded and the wait
+// continues (bounded again) so that no copy into this warp's buffer is left
+// in flight
+__device__ __forceinline__ void mbar_wait(const DevStatus* cst, uint64_t* bar, uint32_t phase)
+{
+    DevStatus* st = const_cast<DevStatus*>(cst);
+    for (int round = 0; round < 2; ++round) {
+        for (unsigned it = 0; it < HDP_SPIN_LIMIT; ++it)
+            if (mbar_test(bar, phase)) return;
+        dev_fail(st, DEV_TIMEOUT, 53);
+    }
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the shared-memory source of earlier bulk stores may be overwritten after this
+__device__ __forceinline__ void bulk_store_drain() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every earlier bulk store has completed (written to global memory)
+__device__ __forceinline__ void bulk_store_complete() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ int tile_of_row(const AggArgs& a, int r) { return (int)a.tid[r] + (int)a.tstart[r] - 1; }
 
 // the spin on a neighbouring tile's state is bounded; on timeout the carry is
@@ -201,7 +245,8 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 }
 
 template <bool FP16, bool UP>
-__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float4* CIN)
+__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float4* CIN,
+                          uint64_t* bar, uint32_t& bar_phase)
 {
     const int lane = threadIdx.x & 31;
     const int ntiles = *a.d_ntiles;
@@ -215,6 +260,16 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     const int n = e - b;
     const size_t base = a.roff[b];
     int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
+
+    // the previous tile's bulk store reads X: let it finish before X is rewritten
+    if (!FP16 && lane == 0) bulk_store_drain();
+    __syncwarp();
+    if (!FP16 && !UP) {
+        // the tile's U rows are one contiguous run: one TMA bulk copy into X
+        if (lane == 0) bulk_load(X, a.vol + base, (uint32_t)(n * kp * sizeof(float)), bar);
+        mbar_wait(a.st, bar, bar_phase);
+        bar_phase ^= 1u;
+    }
 
     // ---- phase 1: the affine inputs of every (row, column) of the tile, all loads in flight
 #pragma unroll 4
@@ -260,7 +315,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
             const float sv = fabsf(s), w = 1.f - sv * sv;
             const int pr = top ? a.prow[row] : -1;
             if (j < q) {
-                float4 U = load_row4<FP16>(a, base + (size_t)r * kp + 4 * j);
+                float4 U = FP16 ? load_row4<FP16>(a, base + (size_t)r * kp + 4 * j) : X[idx];
                 if (FP16) {
                     const float nu = a.nup[row];
                     U = make_float4(U.x * nu, U.y * nu, U.z * nu, U.w * nu);
@@ -423,15 +478,18 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         X[idx] = fma4(PT[r], CIN[j], X[idx]);
     }
     __syncwarp();
-    for (int idx = lane; idx < n * q; idx += 32) {
-        const int r = idx / q, j = idx - r * q;
-        float4 x = X[r * qe + j];
-        if (FP16) {
+    if (FP16) {
+        for (int idx = lane; idx < n * q; idx += 32) {
+            const int r = idx / q, j = idx - r * q;
+            float4 x = X[r * qe + j];
             const float inv = 1.f / X[r * qe + q].x;
             x = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);
+            store_row4<FP16>(a, base + (size_t)r * kp + 4 * j, x);
         }
-        if (!FP16 && !UP) *(float4*)(a.vout + base + (size_t)r * kp + 4 * j) = x;
-        else store_row4<FP16>(a, base + (size_t)r * kp + 4 * j, x);
+    } else {
+        // X holds the tile's rows exactly as laid out in HBM: one TMA bulk store
+        __syncwarp();
+        if (lane == 0) bulk_store((UP ? a.vol : a.vout) + base, X, (uint32_t)(n * kp * sizeof(float)));
     }
     if (FP16)
         for (int r = lane; r < n; r += 32) (UP ? a.nup : a.nd)[b + r] = X[r * qe + q].x;
@@ -514,6 +572,11 @@ __global__ void __launch_bounds__(AGG_THREADS) k_agg(AggArgs a)
     float* P = M + TILE_ROWS_MAX;
     float* PT = P + TILE_ROWS_MAX;
     float4* CIN = (float4*)(PT + TILE_ROWS_MAX);
+    __shared__ __align__(8) uint64_t bars[AGG_WARPS];
+    uint64_t* bar = bars + warp;
+    uint32_t bar_phase = 0;
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
     int* tk = a.tickets + (UP ? 0 : MAX_LIGHT_LEVELS) + a.level;
     for (;;) {
         int t = 0;
@@ -523,8 +586,9 @@ __global__ void __launch_bounds__(AGG_THREADS) k_agg(AggArgs a)
         // up: bottom tiles first (carries flow upwards); down: top tiles first.
         // A tile only waits on tiles with earlier tickets, so the waits end.
         const int u = UP ? first + cnt - 1 - t : first + t;
-        tile_pass<FP16, UP>(a, u, X, M, P, PT, CIN);
+        tile_pass<FP16, UP>(a, u, X, M, P, PT, CIN, bar, bar_phase);
     }
+    if (!FP16 && lane == 0) bulk_store_complete();
 }
 
 static size_t agg_smem(bool fp16)

@@ -11,6 +11,7 @@
 
 struct hdp_ctx {
     Ctx c;
+    cudaEvent_t fork = nullptr, join = nullptr;   // batch fork/join events (lazily created)
     int prior_injected[HDP_MAX_LEVELS] = {};
     int timing = 0;
     cudaEvent_t ev[HDP_MAX_LEVELS][6] = {};
@@ -430,6 +431,8 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
     for (int i = 0; i < 4; ++i)
         if (ctx->c.gvol[i]) cudaFree(ctx->c.gvol[i]);
     if (ctx->c.gacc) cudaFree(ctx->c.gacc);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     delete ctx;
@@ -804,3 +807,70 @@ extern "C" int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d
     if (rc) return fail(ctx, rc, "workspace for the differentiable path");
     return check_launch(ctx, "hdp_soft_argmin_l1");
 }
+
+// ------------------------------------------------------------------ batch ---
+extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right,
+                               const int* pitch, int32_t* const* d_out)
+{
+    if (!ctxs || n <= 0 || !d_left || !d_right || !pitch || !d_out) return HDP_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return HDP_ERR_ARG;
+    hdp_ctx* ctx = ctxs[0];
+    for (int i = 1; i < n; ++i)
+        if (ctxs[i]->c.s == ctx->c.s) return fail(ctx, HDP_ERR_ARG, "every context of a batch needs its own stream");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]->fork) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->fork, cudaEventDisableTiming));
+        if (!ctxs[i]->join) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->join, cudaEventDisableTiming));
+    }
+    TRY_CUDA(cudaEventRecord(ctx->fork, ctx->c.s));
+    for (int i = 1; i < n; ++i) TRY_CUDA(cudaStreamWaitEvent(ctxs[i]->c.s, ctx->fork, 0));
+    for (int i = 0; i < n; ++i) {
+        int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
+        if (!rc) rc = hdp_match(ctxs[i], d_out[i]);
+        if (rc) return rc;
+    }
+    for (int i = 1; i < n; ++i) {
+        TRY_CUDA(cudaEventRecord(ctxs[i]->join, ctxs[i]->c.s));
+        TRY_CUDA(cudaStreamWaitEvent(ctx->c.s, ctxs[i]->join, 0));
+    }
+    return HDP_OK;
+}
+
+extern "C" int hdp_batch_graph_capture(hdp_ctx** ctxs, int n, const uint8_t* const* d_left,
+                                       const uint8_t* const* d_right, const int* pitch, int32_t* const* d_out,
+                                       int* n_kernels)
+{
+    if (!ctxs || n <= 0 || !ctxs[0]) return HDP_ERR_ARG;
+    hdp_ctx* ctx = ctxs[0];
+    Ctx& c = ctx->c;
+    if (!c.s) return fail(ctx, HDP_ERR_ARG, "graph capture needs a non-default stream");
+    if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    // events are created before capture (creation is not a stream operation)
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return HDP_ERR_ARG;
+        if (!ctxs[i]->fork) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->fork, cudaEventDisableTiming));
+        if (!ctxs[i]->join) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->join, cudaEventDisableTiming));
+    }
+    TRY_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeGlobal));
+    int rc = hdp_match_batch(ctxs, n, d_left, d_right, pitch, d_out);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c.s, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, HDP_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    ctx->graph = g;
+    size_t nn = 0;
+    TRY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    TRY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    if (n_kernels) *n_kernels = k;
+    TRY_CUDA(cudaGraphInstantiate(&ctx->exec, g, 0));
+    return HDP_OK;
+}
+
+extern "C" int hdp_batch_graph_launch(hdp_ctx* ctx) { return hdp_graph_launch(ctx); }
