@@ -171,6 +171,52 @@ def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=Fa
         hdp.hdp_destroy(ctx)
 
 
+def run_batch(hdp, torch, dev, steps, warmup, flush, rank, per_size=16):
+    """64 seeded pairs of mixed sizes (320x240, 640x480, 1242x375, 1390x1110) with
+    disparity bounds drawn from 64..228, HDP + MST, 4 layers, FP16 storage, all
+    matched concurrently as one captured CUDA graph."""
+    from paper_1509_08197_gb300.scenes import make_pair
+    rng = np.random.default_rng(4000 + rank)
+    sizes = [(320, 240), (640, 480), (1242, 375), (1390, 1110)]
+    ctxs, L, R, outs, streams = [], [], [], [], []
+    n_pix_disp = 0
+    try:
+        for k, (w, h) in enumerate(sizes):
+            for i in range(per_size):
+                d = int(rng.integers(64, 229))
+                pr = make_pair(seed=4000 + 100 * k + i, width=w, height=h, max_disp=d, regions=40, octaves=3)
+                hp = hdp.HDPParams(width=w, height=h, max_disp=d, levels=4, tree="mst", storage="fp16")
+                ctxs.append(hdp.hdp_create_own_stream(hp))
+                streams.append(hdp.hdp_get_stream(ctxs[-1]))
+                L.append(torch.from_numpy(pr.left).to(dev).contiguous())
+                R.append(torch.from_numpy(pr.right).to(dev).contiguous())
+                outs.append(torch.empty((h, w), dtype=torch.int32, device=dev))
+                n_pix_disp += w * h * (d + 1)
+        s0 = streams[0]
+        with torch.cuda.stream(s0):
+            nk = hdp.hdp_batch_graph_capture(ctxs, L, R, outs)
+            for _ in range(warmup):
+                hdp.hdp_batch_graph_launch(ctxs[0])
+            s0.synchronize()
+            times = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s0)
+                hdp.hdp_batch_graph_launch(ctxs[0])
+                e1.record(s0)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        ms = float(np.mean(times))
+        return {"workload": "64 pairs: 16 each of 320x240, 640x480, 1242x375, 1390x1110; disparity bound 64-228; "
+                            "HDP+MST, 4 layers, FP16 storage; one CUDA graph",
+                "ms_per_batch": ms, "pairs_per_s": len(ctxs) / (ms / 1000.0), "gpu_launches": nk,
+                "full_range_equivalent_Mpix_disp_per_s": n_pix_disp / (ms / 1000.0) / 1e6}
+    finally:
+        for c in ctxs:
+            hdp.hdp_destroy(c)
+
+
 def agg_bytes(K, dims, b):
     """Algorithmic bytes of the two aggregation passes: 5 b per entry (U written once and
     read twice, C written once and read once) plus 16 B of node data per node and pass."""
@@ -284,6 +330,10 @@ def main():
         if "full_st_fp32" in variants and args.variant == "hdp_st_fp32":
             variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
 
+    batch = None
+    if not args.no_variants:
+        batch = run_batch(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush, rank)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         Kc, tc = cpu_baseline(pair, None)
@@ -309,6 +359,7 @@ def main():
         "gpu_launches": head["n_kernels"],
         "clocks": head["clocks"],
         "variants": variants,
+        "batch": batch,
     }
     print(json.dumps(line))
 

@@ -101,6 +101,18 @@ void hdp_default_params(hdp_params* p, int width, int height, int max_disp);
  * HDP_ERR_ARG on invalid parameters, HDP_ERR_OOM if the workspace does not fit. */
 int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out);
 
+/* As hdp_create, but the context creates its own non-blocking stream and
+ * destroys it in hdp_destroy.  For batches (hdp_match_batch) of more pairs
+ * than the caller has streams: every context of a batch needs its own.  No
+ * counterpart in the paper.  Returns HDP_ERR_CUDA if the stream cannot be
+ * created; otherwise as hdp_create. */
+int hdp_create_own_stream(const hdp_params* p, hdp_ctx** out);
+
+/* The stream the context enqueues its work on (NULL: the legacy default
+ * stream).  Owned by the caller unless the context was made by
+ * hdp_create_own_stream. */
+void* hdp_get_stream(const hdp_ctx* ctx);
+
 /* Bytes of device workspace held by the context. */
 size_t hdp_workspace_bytes(const hdp_ctx* ctx);
 

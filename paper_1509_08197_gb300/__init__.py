@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
     sigs = {
         "hdp_default_params": (None, [P, I, I, I]),
         "hdp_create": (I, [P, P, P]),
+        "hdp_create_own_stream": (I, [P, P]),
+        "hdp_get_stream": (P, [P]),
         "hdp_workspace_bytes": (SZ, [P]),
         "hdp_build_trees": (I, [P, P, P, I]),
         "hdp_match": (I, [P, P]),
@@ -182,6 +184,24 @@ def hdp_create(params: HDPParams, stream=None) -> Context:
     if rc != HDP_OK:
         raise HDPError(f"hdp_create failed ({rc})")
     return Context(h, params)
+
+
+def hdp_create_own_stream(params: HDPParams) -> Context:
+    """A context with its own non-blocking stream (destroyed with it)."""
+    L = load()
+    h = ctypes.c_void_p()
+    cp = params.to_c()
+    rc = L.hdp_create_own_stream(ctypes.byref(cp), ctypes.byref(h))
+    if rc != HDP_OK:
+        raise HDPError(f"hdp_create_own_stream failed ({rc})")
+    return Context(h, params)
+
+
+def hdp_get_stream(ctx: Context):
+    """The context's stream as a torch.cuda.ExternalStream (None: the default stream)."""
+    import torch
+    ptr = load().hdp_get_stream(ctx.handle)
+    return torch.cuda.ExternalStream(ptr) if ptr else None
 
 
 def hdp_workspace_bytes(ctx: Context) -> int:
@@ -341,7 +361,7 @@ def hdp_batch_graph_launch(ctx0):
 
 def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
-    return ["hdp_default_params", "hdp_create", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
+    return ["hdp_default_params", "hdp_create", "hdp_create_own_stream", "hdp_get_stream", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",

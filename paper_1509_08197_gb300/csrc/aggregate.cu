@@ -23,7 +23,7 @@
 
 #define AGG_WARPS 4
 #define AGG_THREADS (32 * AGG_WARPS)
-#define TILE_ROWS_MAX (TILE_FLOATS / 4)
+#define AGG_CHUNK 64   // light children staged per chunk
 
 struct AggArgs {
     const uint32_t* tstart;   // 1 at the first row of a tile
@@ -245,8 +245,8 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 }
 
 template <bool FP16, bool UP>
-__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float4* CIN,
-                          uint64_t* bar, uint32_t& bar_phase)
+__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float* Q, float4* CIN,
+                          int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
 {
     const int lane = threadIdx.x & 31;
     const int ntiles = *a.d_ntiles;
@@ -260,6 +260,10 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     const int n = e - b;
     const size_t base = a.roff[b];
     int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
+    int* Pi = (int*)P;
+    int* PTi = (int*)PT;
+    int* Qi = (int*)Q;
+    int* Ci = (int*)CIN;
 
     // the previous tile's bulk store reads X: let it finish before X is rewritten
     if (!FP16 && lane == 0) bulk_store_drain();
@@ -267,89 +271,116 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     if (!FP16 && !UP) {
         // the tile's U rows are one contiguous run: one TMA bulk copy into X
         if (lane == 0) bulk_load(X, a.vol + base, (uint32_t)(n * kp * sizeof(float)), bar);
-        mbar_wait(a.st, bar, bar_phase);
-        bar_phase ^= 1u;
     }
 
-    // ---- phase 1: the affine inputs of every (row, column) of the tile, all loads in flight
-#pragma unroll 4
-    for (int idx = lane; idx < n * qe; idx += 32) {
-        const int r = idx / qe, j = idx - r * qe, row = b + r;
-        float4 x;
-        if (UP) {
-            if (j < q) {
-                const int v = a.lay[row];
-                float t[4];
-                if (a.Ein) {
-                    const float* er = a.Ein + (size_t)v * a.X;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
-                } else {
-                    int lab[4];
-                    slot_labels(a, row, j, lab, nullptr);
-                    const int px = v % a.W, py = v / a.W;
-                    const int4 Lp = a.imL[v];
-                    const int4* Rrow = a.imR + (size_t)py * a.W;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
-                }
-                x = make_float4(t[0], t[1], t[2], t[3]);
-                const uint32_t l0 = a.lcoff[row], l1 = a.lcoff[row + 1];
-                for (uint32_t c = l0; c < l1; ++c) {
-                    const int cr = a.lcrow[c];
-                    const float sc = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
-                    x = fma4(sc, load_row4_cg<FP16>(a, a.roff[cr] + 4 * j), x);
-                }
-            } else {
-                float mass = 1.f;
-                const uint32_t l0 = a.lcoff[row], l1 = a.lcoff[row + 1];
-                for (uint32_t c = l0; c < l1; ++c) {
-                    const int cr = a.lcrow[c];
-                    mass = fmaf(fabsf(a.rs[cr]), __ldcg(a.nup + cr), mass);
-                }
-                x = make_float4(mass, 0.f, 0.f, 0.f);
-            }
-        } else {
-            const float s = a.rs[row];
-            const bool top = signbit(s);
-            const float sv = fabsf(s), w = 1.f - sv * sv;
-            const int pr = top ? a.prow[row] : -1;
-            if (j < q) {
-                float4 U = FP16 ? load_row4<FP16>(a, base + (size_t)r * kp + 4 * j) : X[idx];
-                if (FP16) {
-                    const float nu = a.nup[row];
-                    U = make_float4(U.x * nu, U.y * nu, U.z * nu, U.w * nu);
-                }
-                x = make_float4(w * U.x, w * U.y, w * U.z, w * U.w);
-                if (pr >= 0) {
-                    const float4 cp = FP16 ? load_row4_cg<FP16>(a, a.roff[pr] + 4 * j)
-                                           : __ldcg((const float4*)(a.vout + a.roff[pr] + 4 * j));
-                    x = fma4(sv * (FP16 ? __ldcg(a.nd + pr) : 1.f), cp, x);
-                }
-            } else {
-                float mass = w * a.nup[row];
-                if (pr >= 0) mass = fmaf(sv, __ldcg(a.nd + pr), mass);
-                x = make_float4(mass, 0.f, 0.f, 0.f);
-            }
-        }
-        X[idx] = x;
-    }
-    for (int r = lane; r < n; r += 32) {
-        const int row = b + r;
-        float m;
-        if (UP) {
-            m = 0.f;
+    // ---- phase 1a: per-row inputs, one lane per row (every load of a row in
+    // flight at once), kept in shared memory for the element loop
+    //   up:   Pi = node, Ci = its column, PTi/Qi = its run of light children, M
+    //   down: Pi = parent row offset (-1: none), PT = parent weight, Q = own weight, M
+    int c_base = 0, c_end = 0;
+    if (UP) {
+        c_base = (int)a.lcoff[b];
+        c_end = (int)a.lcoff[e];
+        for (int r = lane; r < n; r += 32) {
+            const int row = b + r;
+            const int v = a.lay[row];
+            Pi[r] = v;
+            Ci[r] = v % a.W;
+            PTi[r] = (int)a.lcoff[row];
+            Qi[r] = (int)a.lcoff[row + 1];
+            float m = 0.f;
             if (row + 1 < a.N) {
                 const float s1 = a.rs[row + 1];
                 m = signbit(s1) ? 0.f : s1;
             }
-        } else {
-            const float s = a.rs[row];
-            m = signbit(s) ? 0.f : s;
+            M[r] = m;
         }
-        M[r] = m;
+    } else {
+        for (int r = lane; r < n; r += 32) {
+            const int row = b + r;
+            const float s = a.rs[row];
+            const bool top = signbit(s);
+            const float sv = fabsf(s), w = 1.f - sv * sv;
+            const int pr = top ? a.prow[row] : -1;
+            Pi[r] = pr >= 0 ? (int)a.roff[pr] : -1;
+            PT[r] = pr >= 0 ? sv * (FP16 ? __ldcg(a.nd + pr) : 1.f) : 0.f;
+            Q[r] = FP16 ? w * a.nup[row] : w;
+            M[r] = top ? 0.f : s;
+        }
     }
     __syncwarp();
+    if (!FP16 && !UP) {
+        mbar_wait(a.st, bar, bar_phase);
+        bar_phase ^= 1u;
+    }
+
+    // ---- phase 1b: the affine inputs of every (row, column) of the tile.  Up:
+    // E plus the light children's U, in child order, the children taken in
+    // chunks of AGG_CHUNK whose row offsets and weights are staged first
+    for (int cc = c_base, first = 1; first || cc < c_end; cc += AGG_CHUNK, first = 0) {
+        const int cn = UP ? min(AGG_CHUNK, c_end - cc) : 0;
+        if (UP) {
+            for (int k = lane; k < cn; k += 32) {
+                const int cr = a.lcrow[cc + k];
+                CO[k] = (int)a.roff[cr];
+                CS[k] = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
+            }
+            __syncwarp();
+        }
+#pragma unroll 4
+        for (int idx = lane; idx < n * qe; idx += 32) {
+            const int r = idx / qe, j = idx - r * qe, row = b + r;
+            float4 x;
+            if (UP) {
+                const int lo = max(PTi[r], cc) - cc, hi = min(Qi[r], cc + cn) - cc;
+                if (j < q) {
+                    if (first) {
+                        const int v = Pi[r];
+                        float t[4];
+                        if (a.Ein) {
+                            const float* er = a.Ein + (size_t)v * a.X;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
+                        } else {
+                            int lab[4];
+                            slot_labels(a, row, j, lab, nullptr);
+                            const int px = Ci[r];
+                            const int4 Lp = a.imL[v];
+                            const int4* Rrow = a.imR + (size_t)(v - px);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
+                        }
+                        x = make_float4(t[0], t[1], t[2], t[3]);
+                    } else {
+                        x = X[idx];
+                    }
+                    for (int k = lo; k < hi; ++k) x = fma4(CS[k], load_row4_cg<FP16>(a, (size_t)CO[k] + 4 * j), x);
+                } else {
+                    float mass = first ? 1.f : X[idx].x;
+                    for (int k = lo; k < hi; ++k) mass += CS[k];
+                    x = make_float4(mass, 0.f, 0.f, 0.f);
+                }
+            } else {
+                const int po = Pi[r];
+                const float cw = Q[r];
+                if (j < q) {
+                    const float4 U = FP16 ? load_row4<FP16>(a, base + (size_t)r * kp + 4 * j) : X[idx];
+                    x = make_float4(cw * U.x, cw * U.y, cw * U.z, cw * U.w);
+                    if (po >= 0) {
+                        const float4 cp = FP16 ? load_row4_cg<FP16>(a, (size_t)po + 4 * j)
+                                               : __ldcg((const float4*)(a.vout + po + 4 * j));
+                        x = fma4(PT[r], cp, x);
+                    }
+                } else {
+                    x = make_float4(cw + PT[r], 0.f, 0.f, 0.f);
+                }
+            }
+            X[idx] = x;
+        }
+        __syncwarp();
+        if (!UP) break;
+    }
 
     // ---- phase 2: scan in recurrence order t (row = n-1-t going up, t going down)
     const int G = qe >= 32 ? 32 : (qe <= 1 ? 1 : 1 << (32 - __clz(qe - 1)));
@@ -406,14 +437,17 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
 
     // ---- phase 3: carry from the neighbouring tile of the same path.  Tiles of a
     // path sit at consecutive indices; a tile that links to its neighbour
-    // publishes its aggregate (A, M), then looks back 32 tiles at a time for the
-    // nearest inclusive value and composes the aggregates in between from the
-    // inner end outwards (the same arithmetic whoever evaluates it).  With no
-    // inclusive value within reach it waits for one to appear.
+    // publishes its aggregate (A, M), then walks back 32 tiles at a time over
+    // published aggregates to the nearest inclusive value (waiting only on a
+    // tile that has published nothing yet).  The carry is then applied tile by
+    // tile from that inclusive value outwards, so every tile's value is the
+    // same chain of fmas whichever inclusive value was found: the rounding does
+    // not depend on timing.
     const int rfirst = UP ? n - 1 : 0;   // first row in recurrence order
     const int rlast = UP ? 0 : n - 1;    // boundary row handed to the next tile
     const bool need = M[rfirst] != 0.f;
     const int nf = 4 * qe;
+    float* cin = (float*)CIN;
     if (need) {
         float* dst = a.aggA + (size_t)u * SCR_STRIDE;
         const float* xl = (const float*)(X + rlast * qe);
@@ -423,18 +457,21 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         __syncwarp();
         if (lane == 0) atomicExch(flags + u, 1);
         const int dir = UP ? 1 : -1;
-        int kI = -1;          // position (1..32) of the inclusive value, relative to u
+        int D = 0;            // distance of the inclusive value (0: wait failed)
         unsigned it = 0;
-        for (;;) {
-            const int jt = u + dir * (lane + 1);
+        for (int off = 0; D == 0;) {
+            const int jt = u + dir * (off + lane + 1);
             // a neighbour outside the tile range would be a chain start with value 0
-            int f = (jt >= 0 && jt < ntiles) ? *(volatile int*)(flags + jt) : 3;
+            const int f = (jt >= 0 && jt < ntiles) ? *(volatile int*)(flags + jt) : 3;
             const unsigned incl = __ballot_sync(0xffffffffu, f >= 2);
             const unsigned none = __ballot_sync(0xffffffffu, f == 0);
             if (incl) {
                 const int k = __ffs(incl);          // 1-based
                 const unsigned before = k == 1 ? 0u : (0xffffffffu >> (33 - k));
-                if (!(none & before)) { kI = k; break; }
+                if (!(none & before)) { D = off + k; break; }
+            } else if (!none) {
+                off += 32;                          // 32 aggregates: keep walking
+                continue;
             }
             if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
                 dev_fail(a.st, DEV_TIMEOUT, 51);
@@ -443,32 +480,41 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
             __nanosleep(64);
         }
         __threadfence();
-            // multiplier of the tile `lane + 1` steps back, shared by all columns
-        const int jm = u + dir * (lane + 1);
-        const float mk = (lane + 1 < kI && jm >= 0 && jm < ntiles) ? __ldcg(a.aggM + jm) : 0.f;
-        for (int f0 = 0; f0 < nf; f0 += 32) {      // warp-uniform trip count (shuffles inside)
-            const int f = f0 + lane;
-            const bool ok = f < nf;
-            float cval = 0.f;
-            if (kI > 0) {
-                const int jI = u + dir * kI;
-                cval = (ok && jI >= 0 && jI < ntiles) ? __ldcg(a.inclA + (size_t)jI * SCR_STRIDE + f) : 0.f;
-                float av[31];
+        if (D > 0) {
+            const int jI = u + dir * D;
+            for (int f = lane; f < nf; f += 32)
+                cin[f] = (jI >= 0 && jI < ntiles) ? __ldcg(a.inclA + (size_t)jI * SCR_STRIDE + f) : 0.f;
+        } else {
+            for (int f = lane; f < nf; f += 32) cin[f] = 0.f;
+        }
+        __syncwarp();
+        // distances D-1 .. 1, in chunks of 32 from the far end
+        for (int c0 = ((D - 2) >> 5) << 5; D > 1 && c0 >= 0; c0 -= 32) {
+            // multiplier of the tile at distance c0 + lane + 1, shared by all columns
+            const int dk = c0 + lane + 1;
+            const int jm = u + dir * dk;
+            const float mk = (dk < D && jm >= 0 && jm < ntiles) ? __ldcg(a.aggM + jm) : 0.f;
+            for (int f0 = 0; f0 < nf; f0 += 32) {      // warp-uniform trip count (shuffles inside)
+                const int f = f0 + lane;
+                const bool ok = f < nf;
+                float cval = ok ? cin[f] : 0.f;
+                float av[32];
 #pragma unroll
-                for (int k = 1; k < 32; ++k) {
-                    const int jj = u + dir * k;
-                    av[k - 1] = (ok && k < kI) ? __ldcg(a.aggA + (size_t)jj * SCR_STRIDE + f) : 0.f;
+                for (int k = 0; k < 32; ++k) {
+                    const int d = c0 + k + 1;
+                    av[k] = (ok && d < D) ? __ldcg(a.aggA + (size_t)(u + dir * d) * SCR_STRIDE + f) : 0.f;
                 }
 #pragma unroll
-                for (int k = 31; k >= 1; --k) {
-                    const float m = __shfl_sync(0xffffffffu, mk, k - 1);
-                    if (k < kI) cval = fmaf(m, cval, av[k - 1]);
+                for (int k = 31; k >= 0; --k) {
+                    const float m = __shfl_sync(0xffffffffu, mk, k);
+                    if (c0 + k + 1 < D) cval = fmaf(m, cval, av[k]);
                 }
+                if (ok) cin[f] = cval;
             }
-            if (ok) ((float*)CIN)[f] = cval;
+            __syncwarp();
         }
     } else {
-        for (int f = lane; f < nf; f += 32) ((float*)CIN)[f] = 0.f;
+        for (int f = lane; f < nf; f += 32) cin[f] = 0.f;
     }
     __syncwarp();
 
@@ -558,20 +604,28 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     __syncwarp();
 }
 
+template <bool FP16>
+__host__ __device__ constexpr int agg_xcap() { return TILE_FLOATS / 4 + (FP16 ? TILE_ROWS_MAX : 0); }   // float4 per warp
+// per warp: X | M, P, PT, Q (TILE_ROWS_MAX each) | CIN (80 float4) | CO, CS (AGG_CHUNK each)
+template <bool FP16>
+__host__ __device__ constexpr int agg_warp_f4() { return agg_xcap<FP16>() + TILE_ROWS_MAX + 80 + AGG_CHUNK / 2; }
+
 template <bool FP16, bool UP>
-__global__ void __launch_bounds__(AGG_THREADS) k_agg(AggArgs a)
+__global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
 {
     extern __shared__ float4 smem[];
     const int cnt = a.lvl_count[a.level];
     if (cnt == 0) return;
     const int first = a.lvl_first[a.level];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int xcap = FP16 ? 2 * TILE_ROWS_MAX : TILE_ROWS_MAX;   // float4 per warp
-    float4* X = smem + (size_t)warp * (xcap + 3 * TILE_ROWS_MAX / 4 + 80);
-    float* M = (float*)(X + xcap);
+    float4* X = smem + (size_t)warp * agg_warp_f4<FP16>();
+    float* M = (float*)(X + agg_xcap<FP16>());
     float* P = M + TILE_ROWS_MAX;
     float* PT = P + TILE_ROWS_MAX;
-    float4* CIN = (float4*)(PT + TILE_ROWS_MAX);
+    float* Q = PT + TILE_ROWS_MAX;
+    float4* CIN = (float4*)(Q + TILE_ROWS_MAX);
+    int* CO = (int*)(CIN + 80);
+    float* CS = (float*)(CO + AGG_CHUNK);
     __shared__ __align__(8) uint64_t bars[AGG_WARPS];
     uint64_t* bar = bars + warp;
     uint32_t bar_phase = 0;
@@ -586,15 +640,14 @@ __global__ void __launch_bounds__(AGG_THREADS) k_agg(AggArgs a)
         // up: bottom tiles first (carries flow upwards); down: top tiles first.
         // A tile only waits on tiles with earlier tickets, so the waits end.
         const int u = UP ? first + cnt - 1 - t : first + t;
-        tile_pass<FP16, UP>(a, u, X, M, P, PT, CIN, bar, bar_phase);
+        tile_pass<FP16, UP>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
     if (!FP16 && lane == 0) bulk_store_complete();
 }
 
 static size_t agg_smem(bool fp16)
 {
-    const size_t xcap = fp16 ? 2 * TILE_ROWS_MAX : TILE_ROWS_MAX;
-    return (size_t)AGG_WARPS * (xcap + 3 * TILE_ROWS_MAX / 4 + 80) * sizeof(float4);
+    return (size_t)AGG_WARPS * (fp16 ? agg_warp_f4<true>() : agg_warp_f4<false>()) * sizeof(float4);
 }
 
 CostK cost_consts(const Ctx& c, int l)
@@ -609,16 +662,18 @@ CostK cost_consts(const Ctx& c, int l)
     return k;
 }
 
+// one resident wave: SMs x the blocks that fit on one SM
 template <bool FP16, bool UP>
-static void launch_level(const AggArgs& a, int blocks, cudaStream_t s)
+static void launch_level(const AggArgs& a, int num_sms, cudaStream_t s)
 {
     const size_t sm = agg_smem(FP16);
-    static bool configured = false;
-    if (!configured) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
         cudaFuncSetAttribute(k_agg<FP16, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        configured = true;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg<FP16, UP>, AGG_THREADS, sm);
+        if (per_sm < 1) per_sm = 1;
     }
-    k_agg<FP16, UP><<<blocks, AGG_THREADS, sm, s>>>(a);
+    k_agg<FP16, UP><<<num_sms * per_sm, AGG_THREADS, sm, s>>>(a);
 }
 
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
@@ -669,16 +724,15 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     cudaMemsetAsync(c.tickets, 0, sizeof(int) * 2 * MAX_LIGHT_LEVELS, c.s);
     cudaMemsetAsync(c.tflags, 0, sizeof(int) * 2 * c.max_tiles, c.s);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
-    const int blocks = c.num_sms * 3;
     for (int lv = levels - 1; lv >= 0; --lv) {
         a.level = lv;
-        if (fp16) launch_level<true, true>(a, blocks, c.s);
-        else launch_level<false, true>(a, blocks, c.s);
+        if (fp16) launch_level<true, true>(a, c.num_sms, c.s);
+        else launch_level<false, true>(a, c.num_sms, c.s);
     }
     for (int lv = 0; lv < levels; ++lv) {
         a.level = lv;
-        if (fp16) launch_level<true, false>(a, blocks, c.s);
-        else launch_level<false, false>(a, blocks, c.s);
+        if (fp16) launch_level<true, false>(a, c.num_sms, c.s);
+        else launch_level<false, false>(a, c.num_sms, c.s);
     }
 }
 

@@ -2,22 +2,26 @@
 // (w, edge id) order with Rule 2, DT-Rule 2 (Eq. DTrules) and, for the
 // segment tree, the merge criterion w <= Int(C) + k/|C|.
 //
-// Three engines produce the sequential-Kruskal result exactly:
+// Four engines produce the sequential-Kruskal result exactly:
 //  * Boruvka over the sorted list (the list index is the strict order) when
-//    no state-dependent rule is active: plain MST, full-range layers, and HDP
-//    layers with no "risky" edge.  Without risky edges every tree keeps the
-//    set of its pixels (merges only join equal sets), so DT-Rule 2 reduces to
-//    "same PixelIntv" and the result is the minimum spanning forest of the
-//    same-set subgraph.
-//  * The segment-tree first pass one weight class at a time: inside a class
-//    every edge has the same w, and a tree's criterion cannot change before it
-//    merges (and a merge sets Int = w, which passes for the rest of the
-//    class), so the class reduces to a Boruvka by edge id among the edges
-//    whose two trees pass at the start of the class.
-//  * Deterministic reservations (general fallback): each round takes a window
-//    of the earliest unresolved edges; an edge that holds the reservation of
-//    both its trees is resolved on their current state, exactly as the
-//    sequential algorithm would.
+//    no state-dependent rule is active: plain MST, full-range layers, the
+//    segment tree's linking pass, and HDP layers with no "risky" edge.
+//    Without risky edges every tree keeps the set of its pixels (merges only
+//    join equal sets), so DT-Rule 2 reduces to "same PixelIntv" and the result
+//    is the minimum spanning forest of the same-set subgraph.
+//  * Windowed reservations in shared memory (segment-tree first pass, small
+//    layers): windows of consecutive edges whose trees are copied into shared
+//    memory and resolved there by deterministic reservations; a tree whose
+//    criterion fails at its earliest pending edge is frozen for good.
+//  * Hybrid first pass (big layers): a weight class with many edges is a
+//    Boruvka by edge id among the edges whose two trees pass at the start of
+//    the class (inside a class a tree's criterion cannot change before it
+//    merges, and a merge sets Int = w, which passes for the rest of the
+//    class); runs of small classes form windows resolved as above.
+//  * Deterministic reservations over the whole list (general fallback, risky
+//    HDP layers): each round takes a window of the earliest unresolved edges;
+//    an edge that holds the reservation of both its trees is resolved on their
+//    current state, exactly as the sequential algorithm would.
 #include "hdp_impl.cuh"
 
 #define FOREST_THREADS 512
@@ -161,7 +165,7 @@ __global__ void k_boruvka(ForestArgs a)
     if (a.risky && __ldcg(a.risky)) return;
     const int n = *a.d_n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    if (tid == 0) *a.engine = 1;
+    if (tid == 0 && *a.engine == 0) *a.engine = 1;
     for (int idx = tid; idx < n; idx += nth) {
         int e, w, p, q;
         decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
@@ -176,38 +180,6 @@ __global__ void k_boruvka(ForestArgs a)
     if (!grid_sync(a.st, gridDim.x)) return;
     int cur = 0, par = 0;
     boruvka_rounds(a, cur, par, false);
-}
-
-// Segment-tree first pass, one weight class at a time (see file comment).
-__global__ void k_fh(ForestArgs a)
-{
-    if (a.risky && __ldcg(a.risky)) return;
-    const int n = *a.d_n, ncls = *a.d_ncls;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    int cur = 0, par = 0;
-    for (int c = 0; c < ncls; ++c) {
-        const int s = a.cls_start[c];
-        const int e_end = c + 1 < ncls ? a.cls_start[c + 1] : n;
-        const long long w = (long long)(a.keys[s] >> a.ebits);
-        for (int idx = s + tid; idx < e_end; idx += nth) {
-            int e, ww, p, q;
-            decode(a.keys[idx], a.ebits, a.W, e, ww, p, q);
-            if (!same_set(a, p, q)) continue;
-            int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
-            if (ra == rb) continue;
-            long long sa = __ldcg(a.size + ra), sb = __ldcg(a.size + rb);
-            long long ia = __ldcg(a.intw + ra), ib = __ldcg(a.intw + rb);
-            if ((w - ia) * sa > a.kq || (w - ib) * sb > a.kq) continue;
-            atomicMin(best_of(a, par) + ra, idx);
-            atomicMin(best_of(a, par) + rb, idx);
-            append(a, cur, idx, ra, rb);
-        }
-        if (!grid_sync(a.st, gridDim.x)) return;
-        if (__ldcg(a.ctr + cur) == 0) continue;
-        // sizes and Int = w of the trees merged in this class are folded inside
-        // the rounds; a tree's criterion is only read at the start of a class
-        if (!boruvka_rounds(a, cur, par, true, (int)w)) return;
-    }
 }
 
 __device__ int block_excl_sum(int v, int* smem, int* total)
@@ -375,10 +347,274 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
     }
 }
 
-__global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int* best2, int* minid, int N)
+// ---- segment-tree first pass, windowed, for one CTA (layers up to
+// FH_LOCAL_MAX_NODES nodes, pure regime).  The sorted list is cut into windows
+// of LW_EDGES consecutive edges.  For a window, the current roots of every
+// live edge's end points are gathered from the union-find in global memory and
+// given local ids in shared memory, together with their size and Int.  The
+// window is then resolved entirely in shared memory by deterministic
+// reservations: each round, every unresolved edge reserves both of its local
+// roots with its window position (atomicMin of a round-stamped value, so no
+// reset pass is needed); an edge that holds both reservations is the earliest
+// unresolved edge on both trees, so it is decided on their current state
+// exactly as the sequential algorithm decides it.  At the end of the window
+// the merged local state is written back.
+#define LW_EDGES 4096
+#define LW_ROOTS (2 * LW_EDGES)
+#define LW_THREADS 1024
+#define LW_PER (LW_EDGES / LW_THREADS)
+
+struct LocalWin {
+    uint32_t key[LW_EDGES];
+    uint16_t la[LW_EDGES], lb[LW_EDGES];
+    uint32_t best[LW_ROOTS];
+    int parent[LW_ROOTS];
+    int size[LW_ROOTS];
+    int intw[LW_ROOTS];
+    int glob[LW_ROOTS];
+    uint16_t rep[2 * LW_EDGES];   // representative end point code -> local id
+    int nroots;
+};
+
+__device__ __forceinline__ int lw_find(int* parent, int x)
+{
+    for (int it = 0; it < LW_ROOTS; ++it) {
+        int p = parent[x];
+        if (p == x) return x;
+        int gp = parent[p];
+        if (gp != p) parent[x] = gp;
+        x = gp;
+        if (gp == p) return p;
+    }
+    return x;
+}
+
+// Union-find root in global memory.  L2 = false: plain loads (only this CTA
+// writes the union-find while the kernel runs); L2 = true: through L2 (other
+// SMs wrote it before the last grid barrier).
+template <bool L2>
+__device__ __forceinline__ int g_find(int* parent, int v)
+{
+    if (L2) return uf_find(parent, v);
+    for (int it = 0; it < (1 << 26); ++it) {
+        int p = parent[v];
+        if (p == v) return v;
+        int gp = parent[p];
+        if (gp == p) return p;
+        parent[v] = gp;
+        v = gp;
+    }
+    return v;
+}
+
+// One window [base, base + cnt) of the sorted list, resolved by the calling
+// CTA (all LW_THREADS threads).  loc[] is INT_MAX on entry and on exit.
+template <bool L2>
+__device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, int cnt)
+{
+    const int t = threadIdx.x;
+    if (t == 0) S.nroots = 0;
+    __syncthreads();
+    // gather: current global roots of both end points; one representative
+    // end point per distinct root (smallest code) allocates its local id
+    int ra[LW_PER], rb[LW_PER];
+    unsigned live = 0;
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        const int i = t + k * LW_THREADS;
+        ra[k] = rb[k] = -1;
+        if (i >= cnt) continue;
+        const uint32_t key = a.keys[base + i];
+        int e, w, p, q;
+        decode(key, a.ebits, a.W, e, w, p, q);
+        if (!same_set(a, p, q)) continue;
+        const int x = g_find<L2>(a.parent, p), y = g_find<L2>(a.parent, q);
+        if (x == y) continue;
+        ra[k] = x;
+        rb[k] = y;
+        S.key[i] = key;
+        atomicMin(loc + x, 2 * i);
+        atomicMin(loc + y, 2 * i + 1);
+        live |= 1u << k;
+    }
+    __syncthreads();
+    // a tree whose criterion already fails at the window's first weight can
+    // never merge again in this pass (every later edge is at least as heavy
+    // and its state cannot change without a merge): it starts frozen, which
+    // best == 0 marks (0 is below every reservation stamp)
+    const long long w0 = (long long)(a.keys[base] >> a.ebits);
+    int ca[LW_PER], cb[LW_PER];
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        ca[k] = cb[k] = 0;
+        if (!(live >> k & 1u)) continue;
+        const int i = t + k * LW_THREADS;
+        ca[k] = __ldcg(loc + ra[k]);
+        cb[k] = __ldcg(loc + rb[k]);
+        for (int side = 0; side < 2; ++side) {
+            const int code = side ? cb[k] : ca[k], r = side ? rb[k] : ra[k];
+            if (code == 2 * i + side) {
+                const int id = atomicAdd(&S.nroots, 1);
+                S.rep[code] = (uint16_t)id;
+                S.glob[id] = r;
+                S.parent[id] = id;
+                const int sz = L2 ? __ldcg(a.size + r) : a.size[r];
+                const int iw = L2 ? __ldcg(a.intw + r) : a.intw[r];
+                S.size[id] = sz;
+                S.intw[id] = iw;
+                S.best[id] = (w0 - iw) * sz > a.kq ? 0u : 0xffffffffu;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        if (!(live >> k & 1u)) continue;
+        const int i = t + k * LW_THREADS;
+        S.la[i] = S.rep[ca[k]];
+        S.lb[i] = S.rep[cb[k]];
+    }
+    __syncthreads();
+    // deterministic reservations in shared memory; the earliest unresolved
+    // edge always holds both of its reservations, so every round resolves at
+    // least one edge and the loop ends within LW_EDGES rounds
+    for (int round = 0; round <= LW_EDGES; ++round) {
+        const uint32_t stamp = (uint32_t)(0xffff - round) << 13;
+        int xa[LW_PER], xb[LW_PER];
+#pragma unroll
+        for (int k = 0; k < LW_PER; ++k) {
+            xa[k] = xb[k] = 0;
+            if (!(live >> k & 1u)) continue;
+            const int i = t + k * LW_THREADS;
+            xa[k] = lw_find(S.parent, S.la[i]);
+            xb[k] = lw_find(S.parent, S.lb[i]);
+            if (xa[k] == xb[k] || S.best[xa[k]] == 0u || S.best[xb[k]] == 0u) {
+                live &= ~(1u << k);   // a cycle, or a frozen tree: rejected
+            } else {
+                atomicMin(&S.best[xa[k]], stamp | (uint32_t)i);
+                atomicMin(&S.best[xb[k]], stamp | (uint32_t)i);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < LW_PER; ++k) {
+            if (!(live >> k & 1u)) continue;
+            const int i = t + k * LW_THREADS;
+            const uint32_t me = stamp | (uint32_t)i;
+            const bool ha = S.best[xa[k]] == me, hb = S.best[xb[k]] == me;
+            if (!ha && !hb) continue;
+            int e, w, p, q;
+            decode(S.key[i], a.ebits, a.W, e, w, p, q);
+            const long long sa = S.size[xa[k]], sb = S.size[xb[k]];
+            const long long ia = S.intw[xa[k]], ib = S.intw[xb[k]];
+            // the earliest unresolved edge of a tree sees its final state: if
+            // the criterion fails there, the tree is frozen and the edge rejected
+            const bool fa = ha && (w - ia) * sa > a.kq, fb = hb && (w - ib) * sb > a.kq;
+            if (fa || fb) {
+                if (fa) S.best[xa[k]] = 0u;
+                if (fb) S.best[xb[k]] = 0u;
+                live &= ~(1u << k);
+                continue;
+            }
+            if (!ha || !hb) continue;
+            live &= ~(1u << k);                                              // both pass: merge
+            int big = xa[k], small = xb[k];
+            if (sa < sb) { big = xb[k]; small = xa[k]; }
+            S.parent[small] = big;
+            S.size[big] = (int)(sa + sb);
+            S.intw[big] = w;
+            a.in_tree[e] = 1;
+        }
+        if (!__syncthreads_or(live != 0)) break;
+    }
+    if (live) dev_fail(a.st, DEV_TIMEOUT, 40);   // unreachable by the argument above
+    // write back: merged local roots hang from their new root's global id
+    const int nr = S.nroots;
+    for (int x = t; x < nr; x += LW_THREADS) {
+        const int r = S.glob[x];
+        const int rx = lw_find(S.parent, x);
+        if (rx != x) {
+            if (L2) __stcg(a.parent + r, S.glob[rx]);
+            else a.parent[r] = S.glob[rx];
+        } else if (L2) {
+            __stcg(a.size + r, S.size[x]);
+            __stcg(a.intw + r, S.intw[x]);
+        } else {
+            a.size[r] = S.size[x];
+            a.intw[r] = S.intw[x];
+        }
+        atomicExch(loc + r, INT_MAX);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(LW_THREADS, 1) k_fh_local(ForestArgs a, int* loc)
+{
+    extern __shared__ __align__(16) unsigned char lw_raw[];
+    LocalWin& S = *reinterpret_cast<LocalWin*>(lw_raw);
+    if (a.risky && __ldcg(a.risky)) return;
+    const int n = *a.d_n;
+    if (threadIdx.x == 0) *a.engine = 3;
+    for (int base = 0; base < n; base += LW_EDGES) lw_window<false>(a, loc, S, base, min(LW_EDGES, n - base));
+}
+
+// Segment-tree first pass for big layers (cooperative, one CTA per SM):
+// weight classes of at least LW_BIG_CLASS edges run as a grid Boruvka (see
+// the file comment); runs of consecutive smaller classes, up to LW_EDGES edges, form one
+// window that block 0 resolves in shared memory while the others wait at the
+// next grid barrier.
+#define LW_BIG_CLASS 2048
+
+__global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* loc)
+{
+    extern __shared__ __align__(16) unsigned char lw_raw[];
+    LocalWin& S = *reinterpret_cast<LocalWin*>(lw_raw);
+    if (a.risky && __ldcg(a.risky)) return;
+    const int n = *a.d_n, ncls = *a.d_ncls;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    if (tid == 0) *a.engine = 4;
+    int cur = 0, par = 0;
+    for (int c = 0; c < ncls;) {
+        const int s = a.cls_start[c];
+        const int e_end = c + 1 < ncls ? a.cls_start[c + 1] : n;
+        if (e_end - s >= LW_BIG_CLASS) {
+            const long long w = (long long)(a.keys[s] >> a.ebits);
+            for (int idx = s + tid; idx < e_end; idx += nth) {
+                int e, ww, p, q;
+                decode(a.keys[idx], a.ebits, a.W, e, ww, p, q);
+                if (!same_set(a, p, q)) continue;
+                int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
+                if (ra == rb) continue;
+                long long sa = __ldcg(a.size + ra), sb = __ldcg(a.size + rb);
+                long long ia = __ldcg(a.intw + ra), ib = __ldcg(a.intw + rb);
+                if ((w - ia) * sa > a.kq || (w - ib) * sb > a.kq) continue;
+                atomicMin(best_of(a, par) + ra, idx);
+                atomicMin(best_of(a, par) + rb, idx);
+                append(a, cur, idx, ra, rb);
+            }
+            if (!grid_sync(a.st, gridDim.x)) return;
+            if (__ldcg(a.ctr + cur) != 0 && !boruvka_rounds(a, cur, par, true, (int)w)) return;
+            ++c;
+        } else {
+            int c2 = c + 1;
+            while (c2 < ncls) {
+                const int e2 = c2 + 1 < ncls ? a.cls_start[c2 + 1] : n;
+                if (e2 - a.cls_start[c2] >= LW_BIG_CLASS || e2 - s > LW_EDGES) break;
+                ++c2;
+            }
+            const int wend = c2 < ncls ? a.cls_start[c2] : n;
+            if (blockIdx.x == 0) lw_window<true>(a, loc, S, s, wend - s);
+            if (!grid_sync(a.st, gridDim.x)) return;
+            c = c2;
+        }
+    }
+}
+
+__global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int* best2, int* minid, int* loc, int N)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
+    loc[v] = INT_MAX;
     parent[v] = v;
     size[v] = 1;
     intw[v] = 0;
@@ -455,22 +691,22 @@ __global__ void k_adj(const uint8_t* in_tree, int W, int H, uint8_t* adj)
 }
 
 // blocks_per_sm = 0: as many as fit; barrier-heavy kernels use 1 (fewer arrivals per barrier)
-cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used)
+cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used,
+                        size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
     if (blocks_per_sm > 0 && per > blocks_per_sm) per = blocks_per_sm;
     int blocks = per * sms;
     if (blocks < 1) blocks = 1;
     if (used) *used = blocks;
-    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, s);
 }
 
-// layers below this size run the segment-tree passes with the reservation
-// engine in a single block (many weight classes, few edges per class)
-#define FH_MIN_NODES 131072
+// layers below this size run the segment-tree first pass in one CTA (windowed
+// reservations in shared memory) and the risky fallback in a single block
 #define DR_SINGLE_BLOCK_NODES 131072
 
 void launch_forest(Ctx& c, int l, int hdp)
@@ -508,7 +744,7 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.engine = c.ints + IDX_ENGINE;
     a.st = c.st;
 
-    k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, N);
+    k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
     cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
     cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
     cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);   // barrier state (keeps err)
@@ -518,7 +754,7 @@ void launch_forest(Ctx& c, int l, int hdp)
     const bool small = N < DR_SINGLE_BLOCK_NODES;
     if (hdp) {
         // the reservation engine needs every TreeIntv when it may run
-        int always = st_tree && small;
+        int always = 0;
         k_T_init<<<cdiv(N * HDP_WORDS, 256), 256, 0, c.s>>>(c.T, c.pixset, c.table[l], N, c.ints + IDX_RISKY, always);
     }
     void* args[] = {&a};
@@ -544,7 +780,13 @@ void launch_forest(Ctx& c, int l, int hdp)
         scan_u32(flags, pos, c.ints + IDX_NEDGES, 2 * N, true, c.tmp, total, c.s);
         k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, c.ints + IDX_NEDGES, c.cls_start, total,
                                                            c.ints + IDX_NCLS);
-        coop_launch((const void*)k_fh, FOREST_THREADS, args, c.s, 1, nullptr);
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(k_fh_hybrid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalWin));
+            configured = true;
+        }
+        void* hy_args[] = {&a, &c.rootof};
+        coop_launch((const void*)k_fh_hybrid, LW_THREADS, hy_args, c.s, 1, nullptr, sizeof(LocalWin));
         cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
@@ -556,10 +798,25 @@ void launch_forest(Ctx& c, int l, int hdp)
             coop_launch(dr_grid, FOREST_THREADS, dr_args, c.s, 1, nullptr);
         }
     } else {
+        // pure regime: the windowed first pass in shared memory, then the
+        // linking pass by Boruvka.  With risky edges both return at once and
+        // the reservation engine runs both passes in one block.
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(k_fh_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalWin));
+            configured = true;
+        }
+        k_fh_local<<<1, LW_THREADS, sizeof(LocalWin), c.s>>>(a, c.rootof);
+        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
+        cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 4096;
-        k_dr<true><<<1, 1024, 0, c.s>>>(a, 0);
+        if (hdp) {
+            cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
+            k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
+        }
     }
     k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
     k_finish_roots<<<cdiv(N, 256), 256, 0, c.s>>>(c.rootof, c.minid, c.dtroot, c.T, hdp ? c.pixset : nullptr,

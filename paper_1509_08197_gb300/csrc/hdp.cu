@@ -18,6 +18,7 @@ struct hdp_ctx {
     int ev_used[HDP_MAX_LEVELS][6] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool own_stream = false;   // created by hdp_create_own_stream, destroyed with the context
 };
 
 static void mark(hdp_ctx* ctx, int l, int k)
@@ -182,14 +183,19 @@ static void layout_buffers(Ctx& c)
     c.st = carve<DevStatus>(c, 1);
     c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
     c.tmp = carve<uint32_t>(c, c.tmp_words);
-    size_t K = 0;
+    size_t K = 0, tiles = 0;
     for (int l = 0; l < c.nlev; ++l) {
         size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
         K = std::max(K, (size_t)c.dim[l].N * kp);
+        // every tile but the last of a run is full: with one label set per
+        // layer (full range, top layer) it holds tile_rows_of(kp) rows,
+        // otherwise at least 4 * TILE_ROWS_MAX costs (the narrowest rows)
+        const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.nlev - 1;
+        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp) : (size_t)c.dim[l].N * kp / (4 * TILE_ROWS_MAX);
+        tiles = std::max(tiles, t);
     }
     c.vol_elems = K;
-    // every tile but the last of a run holds more than TILE_FLOATS - 256 costs
-    c.max_tiles = K / (TILE_FLOATS - 256) + 2 * 2048 + 16;
+    c.max_tiles = tiles + 2 * 2048 + 16;   // + one partial tile per (light level, width) run
     c.tflags = carve<int>(c, 2 * c.max_tiles);
     c.aggA = carve<float>(c, c.max_tiles * SCR_STRIDE);
     c.inclA = carve<float>(c, c.max_tiles * SCR_STRIDE);
@@ -435,9 +441,31 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
     if (ctx->join) cudaEventDestroy(ctx->join);
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->own_stream && ctx->c.s) cudaStreamDestroy(ctx->c.s);
     delete ctx;
     return rc;
 }
+
+extern "C" int hdp_create_own_stream(const hdp_params* p, hdp_ctx** out)
+{
+    if (!p || !out) return HDP_ERR_ARG;
+    *out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+        fprintf(stderr, "hdp_create_own_stream: %s\n", cudaGetErrorString(ce));
+        return HDP_ERR_CUDA;
+    }
+    int rc = hdp_create(p, s, out);
+    if (rc != HDP_OK) {
+        cudaStreamDestroy(s);
+        return rc;
+    }
+    (*out)->own_stream = true;
+    return HDP_OK;
+}
+
+extern "C" void* hdp_get_stream(const hdp_ctx* ctx) { return ctx ? (void*)ctx->c.s : nullptr; }
 
 extern "C" const char* hdp_last_error(const hdp_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
 

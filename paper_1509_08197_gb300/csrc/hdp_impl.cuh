@@ -13,7 +13,12 @@
 // aggregation tiles: consecutive rows of one width holding about TILE_FLOATS costs
 #define TILE_FLOATS 2048
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
-__host__ __device__ __forceinline__ int tile_rows_of(int kp) { return kp >= TILE_FLOATS ? 1 : TILE_FLOATS / kp; }
+#define TILE_ROWS_MAX 256   // rows per tile at most (the narrowest rows, kp = 4, fill 1024 floats)
+__host__ __device__ __forceinline__ int tile_rows_of(int kp)
+{
+    const int r = kp >= TILE_FLOATS ? 1 : TILE_FLOATS / kp;
+    return r < TILE_ROWS_MAX ? r : TILE_ROWS_MAX;
+}
 
 struct LayerDims {
     int W, H, N, d;   // size and largest label of the layer
@@ -162,4 +167,5 @@ int launch_soft_argmin_l1(Ctx& c, const float* C, const float* gt, const uint8_t
 
 // helpers
 CostK cost_consts(const Ctx& c, int l);
-cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used_blocks);
+cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used_blocks,
+                        size_t smem = 0);

@@ -22,8 +22,10 @@ def test_batch_equals_one_at_a_time():
         H, W, _ = p.left.shape
         params.append(hdp.HDPParams(width=W, height=H, max_disp=p.max_disp, levels=3 if W < 200 else 4,
                                     tree="mst" if i % 2 == 0 else "st", storage="fp16" if i == 3 else "fp32"))
-    streams = [torch.cuda.Stream(device=dev) for _ in specs]
-    ctxs = [hdp.hdp_create(hp, st) for hp, st in zip(params, streams)]
+    # two contexts on caller streams, two that own theirs
+    ctxs = [hdp.hdp_create(hp, torch.cuda.Stream(device=dev)) if i < 2 else hdp.hdp_create_own_stream(hp)
+            for i, hp in enumerate(params)]
+    assert hdp.hdp_get_stream(ctxs[3]) is not None
     try:
         L = [torch.from_numpy(p.left).to(dev).contiguous() for p in pairs]
         R = [torch.from_numpy(p.right).to(dev).contiguous() for p in pairs]
