@@ -41,6 +41,33 @@ UNIT = "Mpix*disp/s"
 W, H, D, LEVELS = 1390, 1110, 255, 5
 
 
+AGG_SOURCES = ("paper_1509_08197_gb300/csrc/aggregate.cu", "paper_1509_08197_gb300/csrc/hdp_impl.cuh",
+               "paper_1509_08197_gb300/csrc/common.cuh")
+TRAFFIC_FILE = "profiles/k_agg_hdp_st_1390x1110_dram.json"
+
+
+def agg_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in AGG_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def agg_traffic(workload):
+    """DRAM bytes (read + write) of one step's aggregation launches from the committed ncu capture, or None
+    when the aggregation sources changed since the capture or it was taken on another workload."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_FILE)) as f:
+            t = json.load(f)
+        if t["source_sha256"] != agg_source_hash() or t["workload"] != workload:
+            return None
+        return float(t["dram_bytes_per_step"])
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -217,6 +244,63 @@ def run_batch(hdp, torch, dev, steps, warmup, flush, rank, per_size=16):
             hdp.hdp_destroy(c)
 
 
+def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
+    """Differentiable aggregation: B seeded 256x256 pairs, disparity 0-63, one full-range MST per pair, a
+    seeded FP32 cost volume E; a step is, for every pair, the forward Eq. C, the soft-argmin (T = 1) with
+    the L1 loss against the synthetic ground truth, and the backward (dL/dE, dL/dw, dL/dgamma) with the
+    forward recomputed."""
+    from paper_1509_08197_gb300.scenes import workload_pair
+    st = torch.cuda.Stream(device=dev)
+    ctxs, bufs = [], []
+    try:
+        with torch.cuda.stream(st):
+            for i in range(B):
+                pr = workload_pair("grad", index=i)
+                H, W, _ = pr.left.shape
+                X = pr.max_disp + 1
+                hp = hdp.HDPParams(width=W, height=H, max_disp=pr.max_disp, levels=1, mode="full", tree="mst")
+                ctx = hdp.hdp_create(hp, st)
+                ctxs.append(ctx)
+                hdp.hdp_build_trees(ctx, torch.from_numpy(pr.left).to(dev), torch.from_numpy(pr.right).to(dev))
+                g = torch.Generator().manual_seed(5000 + i)
+                E = (torch.rand((H, W, X), generator=g) * 2.5).to(dev)
+                bufs.append(dict(E=E, C=torch.empty_like(E), gC=torch.empty_like(E), gE=torch.empty_like(E),
+                                 gw=torch.empty(2 * H * W, device=dev), gg=torch.empty(1, device=dev),
+                                 d=torch.empty((H, W), device=dev), loss=torch.zeros(1, device=dev),
+                                 gt=torch.from_numpy(pr.gt.astype(np.float32)).to(dev),
+                                 valid=torch.from_numpy((~pr.occluded).astype(np.uint8)).to(dev)))
+
+            def step():
+                for ctx, b in zip(ctxs, bufs):
+                    b["loss"].zero_()
+                    hdp.hdp_aggregate_fwd(ctx, b["E"], b["C"])
+                    hdp.hdp_soft_argmin_l1(ctx, b["C"], b["gt"], b["valid"], 1.0, b["d"], b["loss"], b["gC"])
+                    hdp.hdp_aggregate_bwd(ctx, b["E"], b["gC"], b["gE"], b["gw"], b["gg"])
+
+            for _ in range(warmup):
+                step()
+            st.synchronize()
+            times = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                step()
+                e1.record(st)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            loss = float(sum(float(b["loss"]) for b in bufs) / B)
+        ms = float(np.mean(times))
+        n = sum(b["E"].numel() for b in bufs)
+        return {"workload": f"{B} pairs of 256x256, disparity 0-63, full-range MST, FP32 volume; forward + "
+                            "soft-argmin (T=1) + L1 + backward (dE, dw, dgamma), forward recomputed",
+                "ms_per_step": ms, "pairs_per_s": B / (ms / 1000.0),
+                "Mpix_disp_per_s": n / (ms / 1000.0) / 1e6, "mean_l1_loss": loss}
+    finally:
+        for c in ctxs:
+            hdp.hdp_destroy(c)
+
+
 def agg_bytes(K, dims, b):
     """Algorithmic bytes of the two aggregation passes: 5 b per entry (U written once and
     read twice, C written once and read once) plus 16 B of node data per node and pass."""
@@ -330,9 +414,10 @@ def main():
         if "full_st_fp32" in variants and args.variant == "hdp_st_fp32":
             variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
 
-    batch = None
+    batch = grad = None
     if not args.no_variants:
         batch = run_batch(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush, rank)
+        grad = run_grad(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -352,7 +437,8 @@ def main():
         "stage_ms_per_layer": {hdp.STAGE_NAMES[k]: [float(x) for x in head["stage_ms"][:, k]] for k in range(5)},
         "roofline": {"bound": "hbm", "kernel": "k_agg (up + down passes with WTA)", "achieved": achieved,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
+                     "traffic": agg_traffic(WORKLOAD) if args.variant == "hdp_st_fp32" else None,
+                     "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
         "cpu_baseline": cpu,
         "e2e": ({"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                  "ms_per_pair": 1000 * e2e["seconds"]} if e2e else None),
@@ -360,6 +446,7 @@ def main():
         "clocks": head["clocks"],
         "variants": variants,
         "batch": batch,
+        "differentiable": grad,
     }
     print(json.dumps(line))
 

@@ -90,6 +90,35 @@ typedef struct {
     int storage;
 } hdp_params;
 
+/*
+ * Launch-shape knobs (no counterpart in the paper).  Every setting gives the
+ * same results bit for bit (the forest engines are exact, and the carries of
+ * the aggregation are evaluated in a fixed order); only the speed changes.
+ * Defaults in brackets; hdp_set_tuning rejects values outside the ranges.
+ *   agg_ctas_per_sm        aggregation CTAs per SM, 1..4 [4]
+ *   region_ctas_per_sm     first-pass CTAs per SM on HDP layers, 1..4 [4]
+ *   big_class_edges        first pass of big full-range layers: a weight class
+ *                          with at least this many edges runs as a grid
+ *                          Boruvka, smaller ones in shared-memory windows,
+ *                          64..4096 [2048]
+ *   one_cta_nodes          layers with fewer nodes run the first pass in one
+ *                          CTA and the risky fallback in one block,
+ *                          1024..1<<24 [131072]
+ *   boruvka_edges_per_cta  cooperative grids get one CTA per this many edges
+ *                          (at most one wave), 512..1<<20 [4096]
+ *   region_max_nodes       HDP layers with fewer nodes run the first pass
+ *                          region by region (bigger ones by weight class),
+ *                          0..1<<30 [1<<20]
+ */
+typedef struct {
+    int agg_ctas_per_sm;
+    int region_ctas_per_sm;
+    int big_class_edges;
+    int one_cta_nodes;
+    int boruvka_edges_per_cta;
+    int region_max_nodes;
+} hdp_tuning;
+
 /* Fill p with the paper's settings (Sec. 4.1) for a width x height image:
  * S = 2, L = 3 (levels = 4), gamma = 25.5, alpha = 0.9, tau_c = 7, tau_g = 2,
  * delta0/beta = 0.004/0.95 for images wider than 640 pixels, else 0.064/0.6;
@@ -112,6 +141,19 @@ int hdp_create_own_stream(const hdp_params* p, hdp_ctx** out);
  * stream).  Owned by the caller unless the context was made by
  * hdp_create_own_stream. */
 void* hdp_get_stream(const hdp_ctx* ctx);
+
+/* Read or replace the context's launch-shape knobs (see hdp_tuning). */
+int hdp_get_tuning(const hdp_ctx* ctx, hdp_tuning* out);
+int hdp_set_tuning(hdp_ctx* ctx, const hdp_tuning* t);
+
+/* Autotuner: coordinate descent over the hdp_tuning knobs on the caller's
+ * pair (device images as for hdp_build_trees).  Each candidate runs
+ * hdp_build_trees + hdp_match `reps` times (1..16) on the context's stream,
+ * timed with CUDA events (fastest run counts); the best setting of each knob
+ * is kept before the next knob is tried.  The result is stored in the context
+ * and copied to *out (optional).  Synchronises; do not call during stream
+ * capture.  Leaves the context as after hdp_match on that pair. */
+int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch, int reps, hdp_tuning* out);
 
 /* Bytes of device workspace held by the context. */
 size_t hdp_workspace_bytes(const hdp_ctx* ctx);

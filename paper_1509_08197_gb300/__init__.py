@@ -109,6 +109,9 @@ def load(path: str = LIB_PATH):
         "hdp_create_own_stream": (I, [P, P]),
         "hdp_get_stream": (P, [P]),
         "hdp_workspace_bytes": (SZ, [P]),
+        "hdp_get_tuning": (I, [P, P]),
+        "hdp_set_tuning": (I, [P, P]),
+        "hdp_autotune": (I, [P, P, P, I, I, P]),
         "hdp_build_trees": (I, [P, P, P, I]),
         "hdp_match": (I, [P, P]),
         "hdp_match_host": (I, [P, P, P, P]),
@@ -138,6 +141,16 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = L
     return L
+
+
+class Tuning(ctypes.Structure):
+    """hdp_tuning: launch-shape knobs; every setting gives identical results."""
+    _fields_ = [("agg_ctas_per_sm", ctypes.c_int), ("region_ctas_per_sm", ctypes.c_int),
+                ("big_class_edges", ctypes.c_int), ("one_cta_nodes", ctypes.c_int),
+                ("boruvka_edges_per_cta", ctypes.c_int), ("region_max_nodes", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class HDPError(RuntimeError):
@@ -202,6 +215,25 @@ def hdp_get_stream(ctx: Context):
     import torch
     ptr = load().hdp_get_stream(ctx.handle)
     return torch.cuda.ExternalStream(ptr) if ptr else None
+
+
+def hdp_get_tuning(ctx: Context) -> Tuning:
+    t = Tuning()
+    _check(ctx, load().hdp_get_tuning(ctx.handle, ctypes.byref(t)), "hdp_get_tuning")
+    return t
+
+
+def hdp_set_tuning(ctx: Context, t: Tuning):
+    _check(ctx, load().hdp_set_tuning(ctx.handle, ctypes.byref(t)), "hdp_set_tuning")
+
+
+def hdp_autotune(ctx: Context, left, right, reps: int = 2) -> Tuning:
+    """Coordinate descent over the launch-shape knobs on this pair (device images)."""
+    t = Tuning()
+    W = ctx.params.width
+    _check(ctx, load().hdp_autotune(ctx.handle, _ptr(left), _ptr(right), 3 * W, int(reps), ctypes.byref(t)),
+           "hdp_autotune")
+    return t
 
 
 def hdp_workspace_bytes(ctx: Context) -> int:
@@ -361,7 +393,8 @@ def hdp_batch_graph_launch(ctx0):
 
 def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
-    return ["hdp_default_params", "hdp_create", "hdp_create_own_stream", "hdp_get_stream", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
+    return ["hdp_default_params", "hdp_create", "hdp_create_own_stream", "hdp_get_stream", "hdp_get_tuning",
+            "hdp_set_tuning", "hdp_autotune", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",

@@ -45,6 +45,11 @@ struct AggArgs {
     const int* d_ntiles;
     const int* lvl_first;
     const int* lvl_count;
+    const int* cstart;
+    const int* cend;
+    const int* wbeg;
+    const int* lvl_wfirst;
+    const int* lvl_wcount;
     float* vol;          // up-pass values U (and the down pass input)
     float* vout;         // down-pass output C (== vol for in-place aggregation)
     const float* Ein;    // optional dense cost volume [N][X] (all labels) instead of the matching cost
@@ -245,8 +250,8 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 }
 
 template <bool FP16, bool UP>
-__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float* Q, float4* CIN,
-                          int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
+__device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, float* M, float* P, float* PT, float* Q,
+                          float4* CIN, int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
 {
     const int lane = threadIdx.x & 31;
     const int ntiles = *a.d_ntiles;
@@ -263,7 +268,6 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     int* Pi = (int*)P;
     int* PTi = (int*)PT;
     int* Qi = (int*)Q;
-    int* Ci = (int*)CIN;
 
     // the previous tile's bulk store reads X: let it finish before X is rewritten
     if (!FP16 && lane == 0) bulk_store_drain();
@@ -275,7 +279,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
 
     // ---- phase 1a: per-row inputs, one lane per row (every load of a row in
     // flight at once), kept in shared memory for the element loop
-    //   up:   Pi = node, Ci = its column, PTi/Qi = its run of light children, M
+    //   up:   Pi = node, PTi = its first light child, Qi = its column | child count << 28, M
     //   down: Pi = parent row offset (-1: none), PT = parent weight, Q = own weight, M
     int c_base = 0, c_end = 0;
     if (UP) {
@@ -284,10 +288,10 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         for (int r = lane; r < n; r += 32) {
             const int row = b + r;
             const int v = a.lay[row];
+            const int c0 = (int)a.lcoff[row];
             Pi[r] = v;
-            Ci[r] = v % a.W;
-            PTi[r] = (int)a.lcoff[row];
-            Qi[r] = (int)a.lcoff[row + 1];
+            PTi[r] = c0;
+            Qi[r] = (v % a.W) | (((int)a.lcoff[row + 1] - c0) << 28);
             float m = 0.f;
             if (row + 1 < a.N) {
                 const float s1 = a.rs[row + 1];
@@ -332,7 +336,8 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
             const int r = idx / qe, j = idx - r * qe, row = b + r;
             float4 x;
             if (UP) {
-                const int lo = max(PTi[r], cc) - cc, hi = min(Qi[r], cc + cn) - cc;
+                const int cb = PTi[r], ce = cb + (int)((unsigned)Qi[r] >> 28);
+                const int lo = max(cb, cc) - cc, hi = min(ce, cc + cn) - cc;
                 if (j < q) {
                     if (first) {
                         const int v = Pi[r];
@@ -344,7 +349,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
                         } else {
                             int lab[4];
                             slot_labels(a, row, j, lab, nullptr);
-                            const int px = Ci[r];
+                            const int px = Qi[r] & 0x0fffffff;
                             const int4 Lp = a.imL[v];
                             const int4* Rrow = a.imR + (size_t)(v - px);
 #pragma unroll
@@ -448,16 +453,25 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     const bool need = M[rfirst] != 0.f;
     const int nf = 4 * qe;
     float* cin = (float*)CIN;
-    if (need) {
-        float* dst = a.aggA + (size_t)u * SCR_STRIDE;
-        const float* xl = (const float*)(X + rlast * qe);
-        for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
-        if (lane == 0) a.aggM[u] = PT[rlast];
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicExch(flags + u, 1);
+    if (need && !chained) {
         const int dir = UP ? 1 : -1;
         int D = 0;            // distance of the inclusive value (0: wait failed)
+        // the neighbour's inclusive value is often out already: then this
+        // tile's aggregate is never needed (later tiles wait for its own
+        // inclusive value instead) and is not published
+        const int j1 = u + dir;
+        const int f1 = (j1 >= 0 && j1 < ntiles) ? *(volatile int*)(flags + j1) : 3;
+        if (__shfl_sync(0xffffffffu, f1, 0) >= 2) {
+            D = 1;
+        } else {
+            float* dst = a.aggA + (size_t)u * SCR_STRIDE;
+            const float* xl = (const float*)(X + rlast * qe);
+            for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
+            if (lane == 0) a.aggM[u] = PT[rlast];
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicExch(flags + u, 1);
+        }
         unsigned it = 0;
         for (int off = 0; D == 0;) {
             const int jt = u + dir * (off + lane + 1);
@@ -490,32 +504,37 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         __syncwarp();
         // distances D-1 .. 1, in chunks of 32 from the far end
         for (int c0 = ((D - 2) >> 5) << 5; D > 1 && c0 >= 0; c0 -= 32) {
+            const int nk = min(32, D - 1 - c0);     // tiles of this chunk: distances c0 + 1 .. c0 + nk
             // multiplier of the tile at distance c0 + lane + 1, shared by all columns
             const int dk = c0 + lane + 1;
             const int jm = u + dir * dk;
-            const float mk = (dk < D && jm >= 0 && jm < ntiles) ? __ldcg(a.aggM + jm) : 0.f;
-            for (int f0 = 0; f0 < nf; f0 += 32) {      // warp-uniform trip count (shuffles inside)
+            const float mk = (lane < nk && jm >= 0 && jm < ntiles) ? __ldcg(a.aggM + jm) : 0.f;
+            for (int f0 = 0; f0 < nf; f0 += 32) {      // warp-uniform trip counts (shuffles inside)
                 const int f = f0 + lane;
                 const bool ok = f < nf;
                 float cval = ok ? cin[f] : 0.f;
-                float av[32];
+                for (int k1 = nk - 1; k1 >= 0; k1 -= 8) {   // 8 loads in flight, then the fma chain
+                    float av[8];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const int d = c0 + k + 1;
-                    av[k] = (ok && d < D) ? __ldcg(a.aggA + (size_t)(u + dir * d) * SCR_STRIDE + f) : 0.f;
-                }
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k1 - i;
+                        av[i] = (ok && k >= 0) ? __ldcg(a.aggA + (size_t)(u + dir * (c0 + k + 1)) * SCR_STRIDE + f) : 0.f;
+                    }
 #pragma unroll
-                for (int k = 31; k >= 0; --k) {
-                    const float m = __shfl_sync(0xffffffffu, mk, k);
-                    if (c0 + k + 1 < D) cval = fmaf(m, cval, av[k]);
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k1 - i;
+                        const float m = __shfl_sync(0xffffffffu, mk, k >= 0 ? k : 0);
+                        if (k >= 0) cval = fmaf(m, cval, av[i]);
+                    }
                 }
                 if (ok) cin[f] = cval;
             }
             __syncwarp();
         }
-    } else {
+    } else if (!need) {
         for (int f = lane; f < nf; f += 32) cin[f] = 0.f;
     }
+    // (chained and linked: CIN already holds the previous tile's boundary row)
     __syncwarp();
 
     // ---- phase 4: final values, stores, inclusive value for the next tile
@@ -539,7 +558,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     }
     if (FP16)
         for (int r = lane; r < n; r += 32) (UP ? a.nup : a.nd)[b + r] = X[r * qe + q].x;
-    {
+    if (!chained) {
         float* dst = a.inclA + (size_t)u * SCR_STRIDE;
         const float* xl = (const float*)(X + rlast * qe);
         for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
@@ -602,6 +621,12 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         }
     }
     __syncwarp();
+    if (chained) {
+        // the boundary row is the carry of the next tile of the chain
+        const float* xl = (const float*)(X + rlast * qe);
+        for (int f = lane; f < nf; f += 32) cin[f] = xl[f];
+        __syncwarp();
+    }
 }
 
 template <bool FP16>
@@ -614,9 +639,9 @@ template <bool FP16, bool UP>
 __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
 {
     extern __shared__ float4 smem[];
-    const int cnt = a.lvl_count[a.level];
+    const int cnt = a.lvl_wcount[a.level];
     if (cnt == 0) return;
-    const int first = a.lvl_first[a.level];
+    const int first = a.lvl_wfirst[a.level];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* X = smem + (size_t)warp * agg_warp_f4<FP16>();
     float* M = (float*)(X + agg_xcap<FP16>());
@@ -637,10 +662,17 @@ __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
         if (lane == 0) t = atomicAdd(tk, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= cnt) break;
-        // up: bottom tiles first (carries flow upwards); down: top tiles first.
+        // up: bottom units first (carries flow upwards); down: top units first.
         // A tile only waits on tiles with earlier tickets, so the waits end.
-        const int u = UP ? first + cnt - 1 - t : first + t;
-        tile_pass<FP16, UP>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
+        const int k = UP ? first + cnt - 1 - t : first + t;
+        const int s = a.wbeg[k], e = a.wbeg[k + 1];
+        // a short chain runs on this warp alone, in recurrence order, each tile
+        // handing its boundary row to the next in shared memory
+        const bool chained = a.cend[s] - a.cstart[s] + 1 <= CHAIN_MAX;
+        if (UP)
+            for (int u = e - 1; u >= s; --u) tile_pass<FP16, UP>(a, u, chained, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
+        else
+            for (int u = s; u < e; ++u) tile_pass<FP16, UP>(a, u, chained, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
     if (!FP16 && lane == 0) bulk_store_complete();
 }
@@ -664,7 +696,7 @@ CostK cost_consts(const Ctx& c, int l)
 
 // one resident wave: SMs x the blocks that fit on one SM
 template <bool FP16, bool UP>
-static void launch_level(const AggArgs& a, int num_sms, cudaStream_t s)
+static void launch_level(const AggArgs& a, int num_sms, int max_per_sm, cudaStream_t s)
 {
     const size_t sm = agg_smem(FP16);
     static int per_sm = 0;
@@ -673,7 +705,7 @@ static void launch_level(const AggArgs& a, int num_sms, cudaStream_t s)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg<FP16, UP>, AGG_THREADS, sm);
         if (per_sm < 1) per_sm = 1;
     }
-    k_agg<FP16, UP><<<num_sms * per_sm, AGG_THREADS, sm, s>>>(a);
+    k_agg<FP16, UP><<<num_sms * min(per_sm, max_per_sm), AGG_THREADS, sm, s>>>(a);
 }
 
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
@@ -703,6 +735,11 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.d_ntiles = c.ints + IDX_NUNITS;
     a.lvl_first = c.lvl_first;
     a.lvl_count = c.lvl_count;
+    a.cstart = c.cstart;
+    a.cend = c.cend;
+    a.wbeg = c.wbeg;
+    a.lvl_wfirst = c.lvl_wfirst;
+    a.lvl_wcount = c.lvl_wcount;
     a.vol = vol_up ? vol_up : c.vol;
     a.vout = vol_down ? vol_down : a.vol;
     a.Ein = Ein;
@@ -726,13 +763,13 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
     for (int lv = levels - 1; lv >= 0; --lv) {
         a.level = lv;
-        if (fp16) launch_level<true, true>(a, c.num_sms, c.s);
-        else launch_level<false, true>(a, c.num_sms, c.s);
+        if (fp16) launch_level<true, true>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
+        else launch_level<false, true>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
     }
     for (int lv = 0; lv < levels; ++lv) {
         a.level = lv;
-        if (fp16) launch_level<true, false>(a, c.num_sms, c.s);
-        else launch_level<false, false>(a, c.num_sms, c.s);
+        if (fp16) launch_level<true, false>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
+        else launch_level<false, false>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
     }
 }
 

@@ -58,6 +58,9 @@ struct ForestArgs {
     int *win, *wtmp, *wra, *wrb, *wst;
     int WIN;
     int passes, crit_first;
+    int dr_if_risky;     // k_boruvka: run the reservation engine itself when the layer is risky
+    int big_class;       // k_fh_hybrid: weight classes with at least this many edges run as a grid Boruvka
+    int* stats;          // [2]: reservation rounds and windows of the windowed engines (reported per layer)
     int* engine;
     DevStatus* st;
 };
@@ -157,12 +160,18 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool rec
     return false;
 }
 
+template <bool SINGLE>
+__device__ void dr_run(const ForestArgs& a);
+
 // Minimum spanning forest of the eligible edges (MST, or the linking pass of
 // the segment tree on top of the first pass).  Runs only when no risky edge
 // exists.
 __global__ void k_boruvka(ForestArgs a)
 {
-    if (a.risky && __ldcg(a.risky)) return;
+    if (a.risky && __ldcg(a.risky)) {
+        if (a.dr_if_risky) dr_run<false>(a);   // the general fallback, on the same grid
+        return;
+    }
     const int n = *a.d_n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     if (tid == 0 && *a.engine == 0) *a.engine = 1;
@@ -236,10 +245,9 @@ __device__ __forceinline__ int uf_find_t(int* parent, int v)
 // Deterministic reservations over windows of the sorted list.  ctr[3] = window
 // size, ctr[4] = next fresh list index.  best[] holds window positions.
 template <bool SINGLE>
-__global__ void k_dr(ForestArgs a, int only_if_risky)
+__device__ void dr_run(const ForestArgs& a)
 {
     __shared__ int smem[33];
-    if (only_if_risky && !ldv<SINGLE>(a.risky)) return;
     const unsigned nb = gridDim.x;
     const int n = *a.d_n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
@@ -347,6 +355,13 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
     }
 }
 
+template <bool SINGLE>
+__global__ void k_dr(ForestArgs a, int only_if_risky)
+{
+    if (only_if_risky && !ldv<SINGLE>(a.risky)) return;
+    dr_run<SINGLE>(a);
+}
+
 // ---- segment-tree first pass, windowed, for one CTA (layers up to
 // FH_LOCAL_MAX_NODES nodes, pure regime).  The sorted list is cut into windows
 // of LW_EDGES consecutive edges.  For a window, the current roots of every
@@ -360,25 +375,25 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
 // exactly as the sequential algorithm decides it.  At the end of the window
 // the merged local state is written back.
 #define LW_EDGES 4096
-#define LW_ROOTS (2 * LW_EDGES)
 #define LW_THREADS 1024
-#define LW_PER (LW_EDGES / LW_THREADS)
 
-struct LocalWin {
-    uint32_t key[LW_EDGES];
-    uint16_t la[LW_EDGES], lb[LW_EDGES];
-    uint32_t best[LW_ROOTS];
-    int parent[LW_ROOTS];
-    int size[LW_ROOTS];
-    int intw[LW_ROOTS];
-    int glob[LW_ROOTS];
-    uint16_t rep[2 * LW_EDGES];   // representative end point code -> local id
+template <int NE>
+struct LocalWinT {
+    uint32_t key[NE];
+    uint16_t la[NE], lb[NE];
+    uint32_t best[2 * NE];
+    int parent[2 * NE];
+    int size[2 * NE];
+    int intw[2 * NE];
+    int glob[2 * NE];
+    uint16_t rep[2 * NE];   // representative end point code -> local id
     int nroots;
 };
+typedef LocalWinT<LW_EDGES> LocalWin;
 
 __device__ __forceinline__ int lw_find(int* parent, int x)
 {
-    for (int it = 0; it < LW_ROOTS; ++it) {
+    for (int it = 0; it < 2 * LW_EDGES; ++it) {
         int p = parent[x];
         if (p == x) return x;
         int gp = parent[p];
@@ -407,11 +422,13 @@ __device__ __forceinline__ int g_find(int* parent, int v)
     return v;
 }
 
-// One window [base, base + cnt) of the sorted list, resolved by the calling
-// CTA (all LW_THREADS threads).  loc[] is INT_MAX on entry and on exit.
-template <bool L2>
-__device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, int cnt)
+// One window [base, base + cnt) of the list `keys` (a run of the strict
+// order), resolved by the calling CTA of NT threads.  loc[] is INT_MAX on
+// entry and on exit.
+template <bool L2, int NT, int NE>
+__device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, LocalWinT<NE>& S, int base, int cnt)
 {
+    constexpr int LW_PER = NE / NT;
     const int t = threadIdx.x;
     if (t == 0) S.nroots = 0;
     __syncthreads();
@@ -421,10 +438,10 @@ __device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, 
     unsigned live = 0;
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
-        const int i = t + k * LW_THREADS;
+        const int i = t + k * NT;
         ra[k] = rb[k] = -1;
         if (i >= cnt) continue;
-        const uint32_t key = a.keys[base + i];
+        const uint32_t key = keys[base + i];
         int e, w, p, q;
         decode(key, a.ebits, a.W, e, w, p, q);
         if (!same_set(a, p, q)) continue;
@@ -442,13 +459,13 @@ __device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, 
     // never merge again in this pass (every later edge is at least as heavy
     // and its state cannot change without a merge): it starts frozen, which
     // best == 0 marks (0 is below every reservation stamp)
-    const long long w0 = (long long)(a.keys[base] >> a.ebits);
+    const long long w0 = (long long)(keys[base] >> a.ebits);
     int ca[LW_PER], cb[LW_PER];
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         ca[k] = cb[k] = 0;
         if (!(live >> k & 1u)) continue;
-        const int i = t + k * LW_THREADS;
+        const int i = t + k * NT;
         ca[k] = __ldcg(loc + ra[k]);
         cb[k] = __ldcg(loc + rb[k]);
         for (int side = 0; side < 2; ++side) {
@@ -470,22 +487,22 @@ __device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, 
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         if (!(live >> k & 1u)) continue;
-        const int i = t + k * LW_THREADS;
+        const int i = t + k * NT;
         S.la[i] = S.rep[ca[k]];
         S.lb[i] = S.rep[cb[k]];
     }
     __syncthreads();
     // deterministic reservations in shared memory; the earliest unresolved
     // edge always holds both of its reservations, so every round resolves at
-    // least one edge and the loop ends within LW_EDGES rounds
-    for (int round = 0; round <= LW_EDGES; ++round) {
+    // least one edge and the loop ends within NE rounds
+    for (int round = 0; round <= NE; ++round) {
         const uint32_t stamp = (uint32_t)(0xffff - round) << 13;
         int xa[LW_PER], xb[LW_PER];
 #pragma unroll
         for (int k = 0; k < LW_PER; ++k) {
             xa[k] = xb[k] = 0;
             if (!(live >> k & 1u)) continue;
-            const int i = t + k * LW_THREADS;
+            const int i = t + k * NT;
             xa[k] = lw_find(S.parent, S.la[i]);
             xb[k] = lw_find(S.parent, S.lb[i]);
             if (xa[k] == xb[k] || S.best[xa[k]] == 0u || S.best[xb[k]] == 0u) {
@@ -499,7 +516,7 @@ __device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, 
 #pragma unroll
         for (int k = 0; k < LW_PER; ++k) {
             if (!(live >> k & 1u)) continue;
-            const int i = t + k * LW_THREADS;
+            const int i = t + k * NT;
             const uint32_t me = stamp | (uint32_t)i;
             const bool ha = S.best[xa[k]] == me, hb = S.best[xb[k]] == me;
             if (!ha && !hb) continue;
@@ -525,12 +542,18 @@ __device__ void lw_window(const ForestArgs& a, int* loc, LocalWin& S, int base, 
             S.intw[big] = w;
             a.in_tree[e] = 1;
         }
-        if (!__syncthreads_or(live != 0)) break;
+        if (!__syncthreads_or(live != 0)) {
+            if (t == 0 && a.stats) {
+                atomicAdd(a.stats, round + 1);   // reservation rounds
+                atomicAdd(a.stats + 1, 1);       // windows
+            }
+            break;
+        }
     }
     if (live) dev_fail(a.st, DEV_TIMEOUT, 40);   // unreachable by the argument above
     // write back: merged local roots hang from their new root's global id
     const int nr = S.nroots;
-    for (int x = t; x < nr; x += LW_THREADS) {
+    for (int x = t; x < nr; x += NT) {
         const int r = S.glob[x];
         const int rx = lw_find(S.parent, x);
         if (rx != x) {
@@ -555,15 +578,15 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_local(ForestArgs a, int* l
     if (a.risky && __ldcg(a.risky)) return;
     const int n = *a.d_n;
     if (threadIdx.x == 0) *a.engine = 3;
-    for (int base = 0; base < n; base += LW_EDGES) lw_window<false>(a, loc, S, base, min(LW_EDGES, n - base));
+    for (int base = 0; base < n; base += LW_EDGES)
+        lw_window<false, LW_THREADS, LW_EDGES>(a, a.keys, loc, S, base, min(LW_EDGES, n - base));
 }
 
 // Segment-tree first pass for big layers (cooperative, one CTA per SM):
-// weight classes of at least LW_BIG_CLASS edges run as a grid Boruvka (see
-// the file comment); runs of consecutive smaller classes, up to LW_EDGES edges, form one
-// window that block 0 resolves in shared memory while the others wait at the
-// next grid barrier.
-#define LW_BIG_CLASS 2048
+// weight classes of at least a.big_class (<= LW_EDGES) edges run as a grid
+// Boruvka (see the file comment); runs of consecutive smaller classes, up to
+// LW_EDGES edges, form one window that block 0 resolves in shared memory while
+// the others wait at the next grid barrier.
 
 __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* loc)
 {
@@ -577,7 +600,7 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
     for (int c = 0; c < ncls;) {
         const int s = a.cls_start[c];
         const int e_end = c + 1 < ncls ? a.cls_start[c + 1] : n;
-        if (e_end - s >= LW_BIG_CLASS) {
+        if (e_end - s >= a.big_class) {
             const long long w = (long long)(a.keys[s] >> a.ebits);
             for (int idx = s + tid; idx < e_end; idx += nth) {
                 int e, ww, p, q;
@@ -599,14 +622,64 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
             int c2 = c + 1;
             while (c2 < ncls) {
                 const int e2 = c2 + 1 < ncls ? a.cls_start[c2 + 1] : n;
-                if (e2 - a.cls_start[c2] >= LW_BIG_CLASS || e2 - s > LW_EDGES) break;
+                if (e2 - a.cls_start[c2] >= a.big_class || e2 - s > LW_EDGES) break;
                 ++c2;
             }
             const int wend = c2 < ncls ? a.cls_start[c2] : n;
-            if (blockIdx.x == 0) lw_window<true>(a, loc, S, s, wend - s);
+            if (blockIdx.x == 0) lw_window<true, LW_THREADS, LW_EDGES>(a, a.keys, loc, S, s, wend - s);
             if (!grid_sync(a.st, gridDim.x)) return;
             c = c2;
         }
+    }
+}
+
+// ---- segment-tree first pass by regions (HDP layers, pure regime).  Without
+// a risky edge no accepted edge joins different PixelIntv sets, so the
+// connected same-set regions are independent: the sequential result inside a
+// region depends only on the region's own edges, in the strict order.  The
+// edges are stably sorted by region (keeping the strict order inside each);
+// persistent CTAs take whole regions and resolve them window by window.
+#define RG_THREADS 512
+#define RG_EDGES 2048
+typedef LocalWinT<RG_EDGES> RegionWin;
+
+// region label of every same-set edge (its first end point's region root);
+// other edges get label N and sort last
+__global__ void k_region_keys(ForestArgs a, const int* label, uint32_t* rk, uint32_t* rv, int* nvalid)
+{
+    if (a.risky && __ldcg(a.risky)) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (idx < *a.d_n) {
+        const uint32_t key = a.keys[idx];
+        int e, w, p, q;
+        decode(key, a.ebits, a.W, e, w, p, q);
+        valid = same_set(a, p, q);
+        rk[idx] = valid ? (uint32_t)label[p] : (uint32_t)a.N;
+        rv[idx] = key;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, valid);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(nvalid, __popc(m));
+}
+
+__global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
+                                                           int* loc, int* ticket)
+{
+    extern __shared__ __align__(16) unsigned char rg_raw[];
+    RegionWin& S = *reinterpret_cast<RegionWin*>(rg_raw);
+    __shared__ int s_r;
+    if (a.risky && __ldcg(a.risky)) return;
+    const int nreg = *a.d_ncls, nv = *d_nvalid;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.engine = 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_r = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int r = s_r;
+        __syncthreads();
+        if (r >= nreg) break;
+        const int s = a.cls_start[r], e = r + 1 < nreg ? a.cls_start[r + 1] : nv;
+        for (int base = s; base < e; base += RG_EDGES)
+            lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
     }
 }
 
@@ -692,7 +765,7 @@ __global__ void k_adj(const uint8_t* in_tree, int W, int H, uint8_t* adj)
 
 // blocks_per_sm = 0: as many as fit; barrier-heavy kernels use 1 (fewer arrivals per barrier)
 cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s, int blocks_per_sm, int* used,
-                        size_t smem)
+                        size_t smem, int max_blocks)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -700,14 +773,12 @@ cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
     if (blocks_per_sm > 0 && per > blocks_per_sm) per = blocks_per_sm;
     int blocks = per * sms;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     if (used) *used = blocks;
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, s);
 }
 
-// layers below this size run the segment-tree first pass in one CTA (windowed
-// reservations in shared memory) and the risky fallback in a single block
-#define DR_SINGLE_BLOCK_NODES 131072
 
 void launch_forest(Ctx& c, int l, int hdp)
 {
@@ -743,36 +814,82 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.win = c.win; a.wtmp = c.wtmp; a.wra = c.wra; a.wrb = c.wrb; a.wst = c.wst;
     a.engine = c.ints + IDX_ENGINE;
     a.st = c.st;
+    a.stats = c.ints + IDX_DRROUNDS;
 
     k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
     cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
     cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
     cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);   // barrier state (keeps err)
     cudaMemsetAsync(c.ints + IDX_ENGINE, 0, sizeof(int), c.s);
+    cudaMemsetAsync(c.ints + IDX_DRROUNDS, 0, 2 * sizeof(int), c.s);   // and IDX_DRWINDOWS
 
     const bool st_tree = c.p.tree == HDP_TREE_ST;
-    const bool small = N < DR_SINGLE_BLOCK_NODES;
+    // layers below tune.one_cta_nodes run the first pass in one CTA (windowed
+    // reservations in shared memory) and the risky fallback in a single block
+    const bool small = N < c.tune.one_cta_nodes;
+    a.big_class = min(c.tune.big_class_edges, LW_EDGES);
     if (hdp) {
         // the reservation engine needs every TreeIntv when it may run
         int always = 0;
         k_T_init<<<cdiv(N * HDP_WORDS, 256), 256, 0, c.s>>>(c.T, c.pixset, c.table[l], N, c.ints + IDX_RISKY, always);
     }
     void* args[] = {&a};
-    int only_if_risky = 1;
-    void* dr_args[] = {&a, &only_if_risky};
-    const void* dr_grid = (const void*)k_dr<false>;
+    // grids sized by the layer (one block per 4K edges at most, one wave at
+    // most): small layers get cheap barriers and batched pairs share the GPU
+    const int bor_blocks = cdiv(2 * N, c.tune.boruvka_edges_per_cta);
+    a.dr_if_risky = hdp && !small;
     if (!st_tree) {
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
         a.passes = 1;
         a.crit_first = 0;
         a.WIN = small ? 4096 : 16384;
-        if (hdp) {
-            cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-            if (small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
-            else coop_launch(dr_grid, FOREST_THREADS, dr_args, c.s, 1, nullptr);
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        if (hdp && small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
+    } else if (hdp && N < c.tune.region_max_nodes) {
+        // HDP layer: regions.  Label the connected same-set regions (the
+        // minimum spanning forest of the same-set edges), sort the edges by
+        // region, resolve the first pass region by region, then link by
+        // Boruvka.  With risky edges every step but the last returns at once
+        // and the reservation engine runs both passes.
+        a.dr_if_risky = 0;
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
+        int* nvalid = c.ints + IDX_TMP3;
+        cudaMemsetAsync(nvalid, 0, sizeof(int), c.s);
+        k_region_keys<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, (uint32_t*)c.listA, (uint32_t*)c.listB, nvalid);
+        int rbits = 1;
+        while ((1 << rbits) <= N) ++rbits;
+        const int where = radix_sort((uint32_t*)c.listA, (uint32_t*)c.listB, (uint32_t*)c.raA, (uint32_t*)c.raB,
+                                     c.ints + IDX_NEDGES, 2 * N, rbits, c.tmp, c.s);
+        const uint32_t* rk = (const uint32_t*)(where ? c.raA : c.listA);
+        const uint32_t* rv = (const uint32_t*)(where ? c.raB : c.listB);
+        uint32_t* flags = (uint32_t*)c.rbA;
+        uint32_t* pos = (uint32_t*)c.rbB;
+        uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
+        k_class_flags<<<cdiv(2 * N, 256), 256, 0, c.s>>>(rk, nvalid, 0, flags);
+        scan_u32(flags, pos, nvalid, 2 * N, true, c.tmp, total, c.s);
+        k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, nvalid, c.cls_start, total, c.ints + IDX_NCLS);
+        k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
+        cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
+        int* ticket = c.ints + IDX_TMP2;
+        cudaMemsetAsync(ticket, 0, sizeof(int), c.s);
+        static int rg_per_sm = 0;
+        if (rg_per_sm == 0) {
+            cudaFuncSetAttribute(k_fh_regions, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RegionWin));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rg_per_sm, k_fh_regions, RG_THREADS, sizeof(RegionWin));
+            if (rg_per_sm < 1) rg_per_sm = 1;
         }
+        const int rg = min(rg_per_sm, c.tune.region_ctas_per_sm);
+        k_fh_regions<<<c.num_sms * rg, RG_THREADS, sizeof(RegionWin), c.s>>>(a, rv, nvalid, c.rootof, ticket);
+        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
+        cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
+        a.passes = 2;
+        a.crit_first = 1;
+        a.WIN = small ? 4096 : 16384;
+        a.dr_if_risky = !small;
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        if (small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
     } else if (!small) {
-        // first pass by weight classes, then the linking pass by Boruvka
+        // first pass by weight classes and windows, then the linking pass by Boruvka
         uint32_t* flags = c.sorted == c.keys0 ? c.keys1 : c.keys0;
         uint32_t* pos = (uint32_t*)c.listA;
         uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
@@ -786,21 +903,18 @@ void launch_forest(Ctx& c, int l, int hdp)
             configured = true;
         }
         void* hy_args[] = {&a, &c.rootof};
-        coop_launch((const void*)k_fh_hybrid, LW_THREADS, hy_args, c.s, 1, nullptr, sizeof(LocalWin));
+        coop_launch((const void*)k_fh_hybrid, LW_THREADS, hy_args, c.s, 1, nullptr, sizeof(LocalWin),
+                    cdiv(2 * N, 2 * c.tune.boruvka_edges_per_cta));
         cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 16384;
-        if (hdp) {
-            cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-            coop_launch(dr_grid, FOREST_THREADS, dr_args, c.s, 1, nullptr);
-        }
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
     } else {
-        // pure regime: the windowed first pass in shared memory, then the
-        // linking pass by Boruvka.  With risky edges both return at once and
-        // the reservation engine runs both passes in one block.
+        // small layer: the windowed first pass in shared memory, then the
+        // linking pass by Boruvka; with risky edges both return at once and
+        // the reservation engine runs both passes in one block
         static bool configured = false;
         if (!configured) {
             cudaFuncSetAttribute(k_fh_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalWin));
@@ -809,14 +923,11 @@ void launch_forest(Ctx& c, int l, int hdp)
         k_fh_local<<<1, LW_THREADS, sizeof(LocalWin), c.s>>>(a, c.rootof);
         cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr);
+        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 4096;
-        if (hdp) {
-            cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
-            k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
-        }
+        if (hdp) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);   // risky: both passes in one block
     }
     k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
     k_finish_roots<<<cdiv(N, 256), 256, 0, c.s>>>(c.rootof, c.minid, c.dtroot, c.T, hdp ? c.pixset : nullptr,

@@ -176,6 +176,13 @@ static void layout_buffers(Ctx& c)
     c.ubeg = carve<int>(c, N0);
     c.lvl_first = carve<int>(c, MAX_LIGHT_LEVELS);
     c.lvl_count = carve<int>(c, MAX_LIGHT_LEVELS);
+    c.cstart = carve<int>(c, N0);
+    c.cend = carve<int>(c, N0);
+    c.wflag = carve<uint32_t>(c, N0);
+    c.wid = carve<uint32_t>(c, N0);
+    c.wbeg = carve<int>(c, N0 + 1);
+    c.lvl_wfirst = carve<int>(c, MAX_LIGHT_LEVELS);
+    c.lvl_wcount = carve<int>(c, MAX_LIGHT_LEVELS);
     c.tickets = carve<int>(c, 2 * MAX_LIGHT_LEVELS);
     c.nup = carve<float>(c, N0);
     c.nfull = carve<float>(c, N0);
@@ -402,6 +409,104 @@ extern "C" int hdp_sync(hdp_ctx* ctx)
     return HDP_OK;
 }
 
+// ------------------------------------------------------------ tuning ---
+static const char* tuning_error(const hdp_tuning& t)
+{
+    if (t.agg_ctas_per_sm < 1 || t.agg_ctas_per_sm > 4) return "agg_ctas_per_sm out of 1..4";
+    if (t.region_ctas_per_sm < 1 || t.region_ctas_per_sm > 4) return "region_ctas_per_sm out of 1..4";
+    if (t.big_class_edges < 64 || t.big_class_edges > 4096) return "big_class_edges out of 64..4096";
+    if (t.one_cta_nodes < 1024 || t.one_cta_nodes > (1 << 24)) return "one_cta_nodes out of 1024..1<<24";
+    if (t.boruvka_edges_per_cta < 512 || t.boruvka_edges_per_cta > (1 << 20)) return "boruvka_edges_per_cta out of 512..1<<20";
+    if (t.region_max_nodes < 0 || t.region_max_nodes > (1 << 30)) return "region_max_nodes out of 0..1<<30";
+    return nullptr;
+}
+
+extern "C" int hdp_get_tuning(const hdp_ctx* ctx, hdp_tuning* out)
+{
+    if (!ctx || !out) return HDP_ERR_ARG;
+    *out = ctx->c.tune;
+    return HDP_OK;
+}
+
+extern "C" int hdp_set_tuning(hdp_ctx* ctx, const hdp_tuning* t)
+{
+    if (!ctx || !t) return HDP_ERR_ARG;
+    if (const char* why = tuning_error(*t)) return fail(ctx, HDP_ERR_ARG, why);
+    ctx->c.tune = *t;
+    return HDP_OK;
+}
+
+// fastest of `reps` timed runs of hdp_build_trees + hdp_match with the current knobs
+static int tune_time(hdp_ctx* ctx, const uint8_t* L, const uint8_t* R, int pitch, int reps, float* ms)
+{
+    Ctx& c = ctx->c;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TRY_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, HDP_ERR_CUDA, "cudaEventCreate");
+    }
+    float best = 1e30f;
+    int rc = HDP_OK;
+    for (int r = 0; r < reps && rc == HDP_OK; ++r) {
+        cudaEventRecord(e0, c.s);
+        rc = hdp_build_trees(ctx, L, R, pitch);
+        if (rc == HDP_OK) rc = hdp_match(ctx, c.disp_host_stage);
+        cudaEventRecord(e1, c.s);
+        if (rc == HDP_OK) rc = hdp_sync(ctx);
+        float t = 0.f;
+        if (rc == HDP_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && t < best) best = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return rc;
+}
+
+extern "C" int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch, int reps,
+                            hdp_tuning* out)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    if (reps < 1 || reps > 16) return fail(ctx, HDP_ERR_ARG, "reps out of 1..16");
+    Ctx& c = ctx->c;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c.s && cudaStreamIsCapturing(c.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(ctx, HDP_ERR_STATE, "hdp_autotune during stream capture");
+    const int timing = ctx->timing;
+    ctx->timing = 0;
+    float best = 0.f;
+    int rc = tune_time(ctx, d_left, d_right, pitch, reps, &best);   // also warms up
+    if (rc == HDP_OK) rc = tune_time(ctx, d_left, d_right, pitch, reps, &best);
+    static const int cand[6][5] = {{2048, 4096, 8192, 16384, 0},
+                                   {512, 1024, 2048, 4096, 0},
+                                   {32768, 131072, 524288, 0, 0},
+                                   {262144, 1 << 20, 1 << 24, 0, 0},
+                                   {1, 2, 4, 0, 0},
+                                   {2, 3, 4, 0, 0}};
+    for (int k = 0; k < 6 && rc == HDP_OK; ++k) {
+        hdp_tuning keep = c.tune;
+        for (int j = 0; j < 5 && cand[k][j] && rc == HDP_OK; ++j) {
+            hdp_tuning t = keep;
+            int* f = k == 0 ? &t.boruvka_edges_per_cta : k == 1 ? &t.big_class_edges : k == 2 ? &t.one_cta_nodes
+                   : k == 3 ? &t.region_max_nodes : k == 4 ? &t.region_ctas_per_sm : &t.agg_ctas_per_sm;
+            if (*f == cand[k][j]) continue;
+            *f = cand[k][j];
+            c.tune = t;
+            float ms = 0.f;
+            rc = tune_time(ctx, d_left, d_right, pitch, reps, &ms);
+            if (rc == HDP_OK && ms < best) {
+                best = ms;
+                keep = t;
+            }
+        }
+        c.tune = keep;
+    }
+    ctx->timing = timing;
+    if (rc != HDP_OK) return rc;
+    if (out) *out = c.tune;
+    return HDP_OK;
+}
+
 extern "C" int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, int32_t* h_disp_out)
 {
     if (!ctx || !h_left || !h_right || !h_disp_out) return HDP_ERR_ARG;
@@ -616,6 +721,8 @@ extern "C" int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, siz
         o[6] = v[IDX_NARCS];
         o[7] = v[IDX_NCLS];
         o[8] = v[IDX_NLC];
+        o[9] = v[IDX_DRROUNDS];      // windowed forest engines: reservation rounds
+        o[10] = v[IDX_DRWINDOWS];    // and windows
         break;
     }
     default: return HDP_ERR_ARG;

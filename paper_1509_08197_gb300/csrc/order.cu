@@ -301,6 +301,39 @@ __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uin
     atomicAdd(lvl_count + lv, 1);
 }
 
+// chains of tiles: tile u links to u + 1 when the first row of u + 1 is not
+// the top of a heavy path (the boundary cuts a path; never across runs, whose
+// first row is always a top)
+__global__ void k_chain_marks(const int* tbeg, const int* d_ntiles, const float* rs, int* st_in, int* en_in)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, nt = *d_ntiles;
+    if (u >= nt) return;
+    st_in[u] = (u == 0 || signbit(rs[tbeg[u]])) ? u : -1;
+    en_in[u] = (u + 1 == nt || signbit(rs[tbeg[u + 1]])) ? u : INT_MAX;
+}
+
+__global__ void k_work_flags(const int* cstart, const int* cend, const int* d_ntiles, uint32_t* wflag)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= *d_ntiles) return;
+    wflag[u] = u == cstart[u] || cend[u] - cstart[u] + 1 > CHAIN_MAX;
+}
+
+__global__ void k_work_fill(const uint32_t* wflag, const uint32_t* wid, const int* tbeg, const uint32_t* keys_sorted,
+                            const int* d_ntiles, int* wbeg, int* lvl_wfirst, int* lvl_wcount)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, nt = *d_ntiles;
+    if (u >= nt) return;
+    if (u + 1 == nt) wbeg[wid[u] + wflag[u]] = nt;
+    if (!wflag[u]) return;
+    const int k = (int)wid[u];
+    wbeg[k] = u;
+    const int lv = (int)(keys_sorted[tbeg[u]] >> 6);
+    if (lv >= MAX_LIGHT_LEVELS) return;
+    atomicMin(lvl_wfirst + lv, k);
+    atomicAdd(lvl_wcount + lv, 1);
+}
+
 __global__ void k_fill_int(int* p, int n, int v)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,7 +362,8 @@ void launch_order(Ctx& c, int l)
         int* ctr = c.ints + IDX_CTR0;
         DevStatus* st = c.st;
         void* args[] = {&a0, &a1, &a2, &a3, &nar, &ctr, &st};
-        coop_launch((const void*)k_rank, 256, args, s, 0, nullptr);
+        // about four arcs per thread per round, at most one wave
+        coop_launch((const void*)k_rank, 256, args, s, 0, nullptr, 0, cdiv(2 * N, 256 * 4));
     }
     k_orient<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, c.val, N, d.W, c.par, c.pdir, c.sub, c.tpos_down,
                                c.tpos_up, c.ka, c.kb);
@@ -377,4 +411,17 @@ void launch_order(Ctx& c, int l)
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
     k_tile_fill<<<g, 256, 0, s>>>(c.ustart_flag, c.uid, ksorted, N, c.ubeg, c.lvl_first, c.lvl_count, (int)c.max_tiles,
                                   c.st);
+
+    // chains of linked tiles and the work units over them
+    const int* dT = c.ints + IDX_NUNITS;
+    int* st_in = (int*)c.va;   // the sort's value buffers are free again (the order was copied to lay)
+    int* en_in = (int*)c.vb;
+    k_chain_marks<<<g, 256, 0, s>>>(c.ubeg, dT, c.rs, st_in, en_in);
+    device_scan<int, OpMax>(st_in, c.cstart, dT, N, -1, OpMax(), false, false, (int*)c.tmp, nullptr, s);
+    device_scan<int, OpMin>(en_in, c.cend, dT, N, INT_MAX, OpMin(), false, true, (int*)c.tmp, nullptr, s);
+    k_work_flags<<<g, 256, 0, s>>>(c.cstart, c.cend, dT, c.wflag);
+    scan_u32(c.wflag, c.wid, dT, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NWORK), s);
+    k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_wfirst, MAX_LIGHT_LEVELS, INT_MAX);
+    cudaMemsetAsync(c.lvl_wcount, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
+    k_work_fill<<<g, 256, 0, s>>>(c.wflag, c.wid, c.ubeg, ksorted, dT, c.wbeg, c.lvl_wfirst, c.lvl_wcount);
 }

@@ -19,6 +19,9 @@ struct OpSum {
 struct OpMin {
     template <typename T> __device__ __forceinline__ T operator()(T a, T b) const { return b < a ? b : a; }
 };
+struct OpMax {
+    template <typename T> __device__ __forceinline__ T operator()(T a, T b) const { return b > a ? b : a; }
+};
 
 __device__ __forceinline__ int shfl_up(int v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ unsigned shfl_up(unsigned v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }

@@ -107,6 +107,41 @@ def test_third_size_hdp(tree):
         _assert_layer(l, g, o, hp, None)
 
 
+@pytest.mark.parametrize("tree", ["mst", "st"])
+def test_risky_layers_take_the_reservation_engine(tree):
+    # beta = 1/5: DT-Rule 2 joins many different sets, so the lower layers are
+    # "risky" and only the reservation engine is exact there (grid form at the
+    # 463x370 layer, single block below 131072 nodes)
+    pair = workload_pair("third")
+    hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=3, tree=tree, beta=(1, 5))
+    res = _run_layers(hp, pair)
+    risky = {l: int(g["info"][5]) for l, (g, o) in res.items()}
+    engine = {l: int(g["info"][3]) for l, (g, o) in res.items()}
+    assert risky[0] == 1 and risky[1] == 1, risky
+    assert all(engine[l] == 2 for l in risky if risky[l]), engine
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
+def test_engines_of_the_segment_tree():
+    # first pass by regions on the HDP layers, windowed on the (small) top layer
+    pair = workload_pair("third")
+    # beta = 99/100: no two different PixelIntv sets of this scene qualify
+    hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=3, tree="st", beta=(99, 100))
+    res = _run_layers(hp, pair, check_costs=False)
+    engine = {l: int(g["info"][3]) for l, (g, o) in res.items()}
+    risky = {l: int(g["info"][5]) for l, (g, o) in res.items()}
+    assert not any(risky.values()), risky
+    assert engine[0] == 5 and engine[1] == 5 and engine[2] == 3, engine
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+    # hybrid first pass on a full-range layer of >= 131072 nodes
+    hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=1, mode="full", tree="st")
+    res = _run_layers(hp, pair, check_costs=False)
+    assert int(res[0][0]["info"][3]) == 4
+    _assert_layer(0, res[0][0], res[0][1], hp, None)
+
+
 def test_ragged_sizes_and_uniform_prior():
     # odd sizes (partial pyramid squares, ragged tiles), uniform prior, beta 0.95
     pair = workload_pair("tiny", width=77, height=41, max_disp=31)

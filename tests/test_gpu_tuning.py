@@ -1,0 +1,53 @@
+"""Launch-shape knobs change only the speed: every setting, and the
+autotuner's pick, gives bit-identical forests, costs and disparity maps."""
+import numpy as np
+import pytest
+
+import paper_1509_08197_gb300 as hdp
+from paper_1509_08197_gb300.scenes import workload_pair
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _match(ctx, L, R, H, W):
+    out = torch.empty((H, W), dtype=torch.int32, device=L.device)
+    hdp.hdp_build_trees(ctx, L, R)
+    hdp.hdp_match(ctx, out)
+    hdp.hdp_sync(ctx)
+    return out.cpu().numpy(), hdp.hdp_get_stage(ctx, 0, "in_tree"), hdp.hdp_get_stage(ctx, 0, "costs")
+
+
+@pytest.mark.parametrize("tree", ["mst", "st"])
+def test_knobs_do_not_change_results(tree):
+    pair = workload_pair("third")
+    H, W, _ = pair.left.shape
+    dev = torch.device("cuda:0")
+    L = torch.from_numpy(pair.left).to(dev).contiguous()
+    R = torch.from_numpy(pair.right).to(dev).contiguous()
+    ctx = hdp.hdp_create(hdp.HDPParams(width=W, height=H, max_disp=79, levels=3, tree=tree))
+    try:
+        t0 = hdp.hdp_get_tuning(ctx)
+        assert t0.as_dict() == dict(agg_ctas_per_sm=4, region_ctas_per_sm=4, big_class_edges=2048,
+                                    one_cta_nodes=131072, boruvka_edges_per_cta=4096, region_max_nodes=1 << 20)
+        ref = _match(ctx, L, R, H, W)
+        for kw in (dict(agg_ctas_per_sm=1, region_ctas_per_sm=1, big_class_edges=64, one_cta_nodes=1024,
+                        boruvka_edges_per_cta=512, region_max_nodes=0),
+                   dict(agg_ctas_per_sm=2, region_ctas_per_sm=3, big_class_edges=4096, one_cta_nodes=1 << 24,
+                        boruvka_edges_per_cta=1 << 20, region_max_nodes=1 << 30),
+                   dict(agg_ctas_per_sm=3, region_ctas_per_sm=2, big_class_edges=256, one_cta_nodes=1 << 24,
+                        boruvka_edges_per_cta=2048, region_max_nodes=0)):
+            hdp.hdp_set_tuning(ctx, hdp.Tuning(**kw))
+            got = _match(ctx, L, R, H, W)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b)
+        hdp.hdp_set_tuning(ctx, t0)
+        best = hdp.hdp_autotune(ctx, L, R, reps=1)
+        assert best.as_dict() == hdp.hdp_get_tuning(ctx).as_dict()
+        for a, b in zip(ref, _match(ctx, L, R, H, W)):
+            assert np.array_equal(a, b)
+        with pytest.raises(hdp.HDPError):
+            hdp.hdp_set_tuning(ctx, hdp.Tuning(agg_ctas_per_sm=0, region_ctas_per_sm=1, big_class_edges=2048,
+                                               one_cta_nodes=131072, boruvka_edges_per_cta=4096, region_max_nodes=1 << 20))
+    finally:
+        hdp.hdp_destroy(ctx)
