@@ -153,7 +153,7 @@ def aggregated_entries(hdp, ctx, left, right):
     return list(reversed(K))   # index = layer
 
 
-def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=False, clocks=False):
+def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=False, clocks=False, top_costs=False):
     stream = torch.cuda.Stream(device=dev)
     ctx = hdp.hdp_create(params, stream)
     try:
@@ -192,7 +192,16 @@ def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=Fa
             e2e_s = (time.perf_counter() - t0) / steps
             assert np.array_equal(D_host, D_dev)
             e2e = dict(seconds=e2e_s, h2d=pair.left.nbytes + pair.right.nbytes, d2h=D_host.nbytes)
+        costs = None
+        if top_costs:
+            # the top layer's aggregated costs (the same full-range tree in every storage mode)
+            with torch.cuda.stream(stream):
+                ctx_top = hdp.Context(None, params).top
+                hdp.hdp_build_trees(ctx, left, right)
+                hdp.hdp_run_level(ctx, ctx_top)
+                costs = hdp.hdp_get_stage(ctx, ctx_top, "costs")
         return dict(K=K, step_ms=step_ms, agg_ms=agg_ms, stage_ms=np.mean(stage_ms, 0), n_kernels=n_kernels,
+                    costs=costs,
                     e2e=e2e, clocks=clk, D=D_dev)
     finally:
         hdp.hdp_destroy(ctx)
@@ -301,6 +310,20 @@ def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
             hdp.hdp_destroy(c)
 
 
+def bad_pixels(D, pair, thr=1.0):
+    """Fraction of non-occluded pixels whose disparity is off the synthetic ground truth by more than thr."""
+    ok = ~pair.occluded
+    return float((np.abs(D.astype(np.float64) - pair.gt) > thr)[ok].mean())
+
+
+def max_rel_err(g, o):
+    """max |g - o| / max(|o|, 1e-6 mean|o|) over the entries (the parity tests' relative error)."""
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    den = np.maximum(np.abs(o), 1e-6 * np.abs(o).mean())
+    return float((np.abs(g - o) / den).max())
+
+
 def agg_bytes(K, dims, b):
     """Algorithmic bytes of the two aggregation passes: 5 b per entry (U written once and
     read twice, C written once and read once) plus 16 B of node data per node and pass."""
@@ -395,12 +418,15 @@ def main():
     e2e_v = ws * Ktot / e2e["seconds"] / 1e6 if e2e else None
 
     variants = {}
+    runs = {}
     if not args.no_variants:
         for name, kw in specs.items():
             if name == args.variant:
                 continue
             p = hdp.HDPParams(**kw)
-            r = run_variant(hdp, torch, p, pair, max(3, args.steps // 2), args.warmup, flush, dev)
+            r = run_variant(hdp, torch, p, pair, max(3, args.steps // 2), args.warmup, flush, dev,
+                            top_costs=name in ("hdp_st_fp16", "full_st_fp32", "full_st_fp16"))
+            runs[name] = r
             ms = float(np.mean(r["step_ms"]))
             b = 2 if kw.get("storage") == "fp16" else 4
             vd = hdp.Context(None, p).dims
@@ -409,10 +435,21 @@ def main():
                      "aggregated_entries": sum(r["K"]), "aggregation_ms": ag,
                      "aggregation_hbm_frac": agg_bytes(r["K"], vd, b) / (ag / 1000.0) / 1e9 / hbm,
                      "stage_ms": {hdp.STAGE_NAMES[k]: float(r["stage_ms"][:, k].sum()) for k in range(5)},
-                     "disparity_agreement_with_headline": float((r["D"] == head["D"]).mean())}
+                     "disparity_agreement_with_headline": float((r["D"] == head["D"]).mean()),
+                     "bad_pixel_rate": bad_pixels(r["D"], pair)}
             variants[name] = entry
         if "full_st_fp32" in variants and args.variant == "hdp_st_fp32":
             variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
+        if args.variant == "hdp_st_fp32" and "hdp_st_fp16" in runs:
+            # FP16 storage against FP32: the top layer (same full-range tree) for the costs, the final maps for
+            # the WTA flips (layers below the top see different trees once an upper disparity flips)
+            hc = run_variant(hdp, torch, head_p, pair, 1, 1, flush, dev, top_costs=True)["costs"]
+            variants["hdp_st_fp16"].update(
+                top_layer_max_rel_err_vs_fp32=max_rel_err(runs["hdp_st_fp16"]["costs"], hc),
+                wta_flip_rate_vs_fp32=float((runs["hdp_st_fp16"]["D"] != head["D"]).mean()))
+            variants["full_st_fp16"].update(
+                max_rel_err_vs_fp32=max_rel_err(runs["full_st_fp16"]["costs"], runs["full_st_fp32"]["costs"]),
+                wta_flip_rate_vs_fp32=float((runs["full_st_fp16"]["D"] != runs["full_st_fp32"]["D"]).mean()))
 
     batch = grad = None
     if not args.no_variants:
@@ -442,6 +479,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": ({"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                  "ms_per_pair": 1000 * e2e["seconds"]} if e2e else None),
+        "bad_pixel_rate": bad_pixels(head["D"], pair),
         "gpu_launches": head["n_kernels"],
         "clocks": head["clocks"],
         "variants": variants,

@@ -264,6 +264,11 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
     e = min(e, a.N);
     const int n = e - b;
     const size_t base = a.roff[b];
+    // idx / qe and idx / q by a multiply-high with m = ceil(2^32 / d): exact for
+    // idx < 2^14 and 2 <= d < 2^8 (here idx < n * qe <= 768, qe <= 65); d = 1,
+    // whose m does not fit in 32 bits, is taken apart
+    const uint32_t mqe = qe > 1 ? (uint32_t)((0x100000000ull + qe - 1) / qe) : 0u;
+    const uint32_t mq = q > 1 ? (uint32_t)((0x100000000ull + q - 1) / q) : 0u;
     int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
     int* Pi = (int*)P;
     int* PTi = (int*)PT;
@@ -331,9 +336,12 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
             }
             __syncwarp();
         }
-#pragma unroll 4
+        // no unrolling: the kernel is bound by instruction fetch and latency,
+        // not by the loop overhead (1390x1110 full range: 6.9 ms unrolled 4
+        // times, 6.0 ms not unrolled)
+#pragma unroll 1
         for (int idx = lane; idx < n * qe; idx += 32) {
-            const int r = idx / qe, j = idx - r * qe, row = b + r;
+            const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe, row = b + r;
             float4 x;
             if (UP) {
                 const int cb = PTi[r], ce = cb + (int)((unsigned)Qi[r] >> 28);
@@ -539,13 +547,13 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
 
     // ---- phase 4: final values, stores, inclusive value for the next tile
     for (int idx = lane; idx < n * qe; idx += 32) {
-        const int r = idx / qe, j = idx - r * qe;
+        const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe;
         X[idx] = fma4(PT[r], CIN[j], X[idx]);
     }
     __syncwarp();
     if (FP16) {
         for (int idx = lane; idx < n * q; idx += 32) {
-            const int r = idx / q, j = idx - r * q;
+            const int r = q > 1 ? (int)__umulhi((uint32_t)idx, mq) : idx, j = idx - r * q;
             float4 x = X[r * qe + j];
             const float inv = 1.f / X[r * qe + q].x;
             x = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);

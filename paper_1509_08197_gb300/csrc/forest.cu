@@ -388,6 +388,7 @@ struct LocalWinT {
     int glob[2 * NE];
     uint16_t rep[2 * NE];   // representative end point code -> local id
     int nroots;
+    int wmin;               // smallest weight in the window
 };
 typedef LocalWinT<LW_EDGES> LocalWin;
 
@@ -430,12 +431,16 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
 {
     constexpr int LW_PER = NE / NT;
     const int t = threadIdx.x;
-    if (t == 0) S.nroots = 0;
+    if (t == 0) {
+        S.nroots = 0;
+        S.wmin = INT_MAX;
+    }
     __syncthreads();
     // gather: current global roots of both end points; one representative
     // end point per distinct root (smallest code) allocates its local id
     int ra[LW_PER], rb[LW_PER];
     unsigned live = 0;
+    int wl = INT_MAX;
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         const int i = t + k * NT;
@@ -444,6 +449,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         const uint32_t key = keys[base + i];
         int e, w, p, q;
         decode(key, a.ebits, a.W, e, w, p, q);
+        wl = min(wl, w);
         if (!same_set(a, p, q)) continue;
         const int x = g_find<L2>(a.parent, p), y = g_find<L2>(a.parent, q);
         if (x == y) continue;
@@ -454,12 +460,15 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         atomicMin(loc + y, 2 * i + 1);
         live |= 1u << k;
     }
+    if (wl != INT_MAX) atomicMin(&S.wmin, wl);
     __syncthreads();
-    // a tree whose criterion already fails at the window's first weight can
-    // never merge again in this pass (every later edge is at least as heavy
-    // and its state cannot change without a merge): it starts frozen, which
-    // best == 0 marks (0 is below every reservation stamp)
-    const long long w0 = (long long)(keys[base] >> a.ebits);
+    // a tree whose criterion already fails at the window's smallest weight
+    // can never merge again in this pass (every later edge of its region is
+    // at least as heavy and its state cannot change without a merge): it
+    // starts frozen, which best == 0 marks (0 is below every reservation
+    // stamp).  (A window may hold several whole regions, each in the strict
+    // order; the smallest weight over all of them keeps the test exact.)
+    const long long w0 = S.wmin;
     int ca[LW_PER], cb[LW_PER];
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
@@ -641,46 +650,141 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
 // persistent CTAs take whole regions and resolve them window by window.
 #define RG_THREADS 512
 #define RG_EDGES 2048
+#define RG_SMALL (RG_EDGES / 2)   // regions of at most this many edges share windows
 typedef LocalWinT<RG_EDGES> RegionWin;
 
-// region label of every same-set edge (its first end point's region root);
-// other edges get label N and sort last
-__global__ void k_region_keys(ForestArgs a, const int* label, uint32_t* rk, uint32_t* rv, int* nvalid)
+// Connected same-set regions: lock-free union-find over the same-set edges,
+// the larger root hooked under the smaller (so a region's root is its
+// smallest pixel); parent pointers only decrease, so shortcuts are safe.
+__device__ __forceinline__ int cc_find(int* par, int v)
+{
+    for (int it = 0; it < (1 << 26); ++it) {
+        const int p = __ldcg(par + v);
+        if (p == v) return v;
+        const int gp = __ldcg(par + p);
+        if (gp == p) return p;
+        __stcg(par + v, gp);   // v is not a root: only shortcuts ever write it
+        v = gp;
+    }
+    return v;
+}
+
+__global__ void k_cc_hook(ForestArgs a, int* par)
 {
     if (a.risky && __ldcg(a.risky)) return;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false;
+    if (idx >= *a.d_n) return;
+    int e, w, p, q;
+    decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
+    if (!same_set(a, p, q)) return;
+    int u = p, v = q;
+    for (int it = 0; it < (1 << 20); ++it) {
+        u = cc_find(par, u);
+        v = cc_find(par, v);
+        if (u == v) return;
+        if (u < v) { const int t = u; u = v; v = t; }
+        if (atomicCAS(par + u, u, v) == u) return;   // else u was hooked meanwhile: retry
+    }
+    dev_fail(a.st, DEV_TIMEOUT, 41);
+}
+
+// edges per region (same-set edges, by their first end point's region root)
+__global__ void k_region_count(ForestArgs a, const int* label, int* rcnt)
+{
+    if (a.risky && __ldcg(a.risky)) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= *a.d_n) return;
+    int e, w, p, q;
+    decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
+    if (same_set(a, p, q)) atomicAdd(rcnt + label[p], 1);
+}
+
+// sort key of every same-set edge: its region label, with bit rbits set for
+// regions of more than RG_SMALL edges (small regions come first); other
+// edges get 2^(rbits+1) - 1 and sort last.  nsmall counts the edges of the
+// small regions.
+__global__ void k_region_keys(ForestArgs a, const int* label, const int* rcnt, int rbits, uint32_t* rk, uint32_t* rv,
+                              int* nvalid, int* nsmall)
+{
+    if (a.risky && __ldcg(a.risky)) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false, small = false;
     if (idx < *a.d_n) {
         const uint32_t key = a.keys[idx];
         int e, w, p, q;
         decode(key, a.ebits, a.W, e, w, p, q);
         valid = same_set(a, p, q);
-        rk[idx] = valid ? (uint32_t)label[p] : (uint32_t)a.N;
+        uint32_t k = (2u << rbits) - 1u;
+        if (valid) {
+            const int r = label[p];
+            small = rcnt[r] <= RG_SMALL;
+            k = (uint32_t)r | (small ? 0u : 1u << rbits);
+        }
+        rk[idx] = k;
         rv[idx] = key;
     }
     const unsigned m = __ballot_sync(0xffffffffu, valid);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(nvalid, __popc(m));
+    const unsigned ms = __ballot_sync(0xffffffffu, small);
+    if ((threadIdx.x & 31) == 0) {
+        if (m) atomicAdd(nvalid, __popc(m));
+        if (ms) atomicAdd(nsmall, __popc(ms));
+    }
 }
 
+// windows over the small regions: all small regions starting in the same
+// RG_SMALL-edge bucket of the sorted list share one window (whole regions,
+// under 2 * RG_SMALL edges)
+__global__ void k_region_buckets(ForestArgs a, const int* d_nvalid, const int* d_nsmall, int* wb_lo, int* wb_hi,
+                                 int* nsmall_regions)
+{
+    if (a.risky && __ldcg(a.risky)) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x, nreg = *a.d_ncls;
+    if (r >= nreg) return;
+    const int s = a.cls_start[r];
+    if (s >= *d_nsmall) return;
+    const int e = r + 1 < nreg ? a.cls_start[r + 1] : *d_nvalid;
+    const int b = s / RG_SMALL;
+    atomicMin(wb_lo + b, s);
+    atomicMax(wb_hi + b, e);
+    atomicAdd(nsmall_regions, 1);
+}
+
+// Work items: every big region (its windows in order, on one CTA), then one
+// window per bucket of small regions.
 __global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
-                                                           int* loc, int* ticket)
+                                                           const int* d_nsmall, const int* d_nsmall_regions,
+                                                           const int* wb_lo, const int* wb_hi, int* loc, int* ticket)
 {
     extern __shared__ __align__(16) unsigned char rg_raw[];
     RegionWin& S = *reinterpret_cast<RegionWin*>(rg_raw);
     __shared__ int s_r;
     if (a.risky && __ldcg(a.risky)) return;
-    const int nreg = *a.d_ncls, nv = *d_nvalid;
+    const int nreg = *a.d_ncls, nv = *d_nvalid, nsr = *d_nsmall_regions;
+    const int nbig = nreg - nsr, nbuckets = cdiv(*d_nsmall, RG_SMALL);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.engine = 5;
     for (;;) {
         if (threadIdx.x == 0) s_r = atomicAdd(ticket, 1);
         __syncthreads();
-        const int r = s_r;
+        const int t = s_r;
         __syncthreads();
-        if (r >= nreg) break;
-        const int s = a.cls_start[r], e = r + 1 < nreg ? a.cls_start[r + 1] : nv;
-        for (int base = s; base < e; base += RG_EDGES)
-            lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
+        if (t < nbig) {
+            const int r = nsr + t;
+            const int s = a.cls_start[r], e = r + 1 < nreg ? a.cls_start[r + 1] : nv;
+            for (int base = s; base < e; base += RG_EDGES)
+                lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
+        } else if (t - nbig < nbuckets) {
+            const int lo = wb_lo[t - nbig], hi = wb_hi[t - nbig];
+            if (lo < hi) lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, lo, hi - lo);
+        } else {
+            break;
+        }
     }
+}
+
+__global__ void k_fill_int_f(int* p, int n, int v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
 }
 
 __global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int* best2, int* minid, int* loc, int N)
@@ -845,21 +949,26 @@ void launch_forest(Ctx& c, int l, int hdp)
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         if (hdp && small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
     } else if (hdp && N < c.tune.region_max_nodes) {
-        // HDP layer: regions.  Label the connected same-set regions (the
-        // minimum spanning forest of the same-set edges), sort the edges by
-        // region, resolve the first pass region by region, then link by
-        // Boruvka.  With risky edges every step but the last returns at once
+        // HDP layer: regions.  Label the connected same-set regions
+        // (lock-free union-find), sort the edges by region, resolve the
+        // first pass region by region, then link by Boruvka.  With risky edges every step but the last returns at once
         // and the reservation engine runs both passes.
-        a.dr_if_risky = 0;
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        k_cc_hook<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.parent);
         k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
         int* nvalid = c.ints + IDX_TMP3;
+        int* nsmall = c.ints + IDX_CTR3;
+        int* nsmall_regions = c.ints + IDX_CTR4;
         cudaMemsetAsync(nvalid, 0, sizeof(int), c.s);
-        k_region_keys<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, (uint32_t*)c.listA, (uint32_t*)c.listB, nvalid);
-        int rbits = 1;
+        cudaMemsetAsync(nsmall, 0, 2 * sizeof(int), c.s);   // and nsmall_regions
+        int* rcnt = c.minid;   // free until k_forest_init below
+        cudaMemsetAsync(rcnt, 0, sizeof(int) * (size_t)N, c.s);
+        k_region_count<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, rcnt);
+        int rbits = 1;   // labels < N < 2^rbits, so no big key equals the all-ones "other" key
         while ((1 << rbits) <= N) ++rbits;
+        k_region_keys<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, rcnt, rbits, (uint32_t*)c.listA,
+                                                          (uint32_t*)c.listB, nvalid, nsmall);
         const int where = radix_sort((uint32_t*)c.listA, (uint32_t*)c.listB, (uint32_t*)c.raA, (uint32_t*)c.raB,
-                                     c.ints + IDX_NEDGES, 2 * N, rbits, c.tmp, c.s);
+                                     c.ints + IDX_NEDGES, 2 * N, rbits + 1, c.tmp, c.s);
         const uint32_t* rk = (const uint32_t*)(where ? c.raA : c.listA);
         const uint32_t* rv = (const uint32_t*)(where ? c.raB : c.listB);
         uint32_t* flags = (uint32_t*)c.rbA;
@@ -868,6 +977,12 @@ void launch_forest(Ctx& c, int l, int hdp)
         k_class_flags<<<cdiv(2 * N, 256), 256, 0, c.s>>>(rk, nvalid, 0, flags);
         scan_u32(flags, pos, nvalid, 2 * N, true, c.tmp, total, c.s);
         k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, nvalid, c.cls_start, total, c.ints + IDX_NCLS);
+        int* wb_lo = c.rbA;     // buckets (at most 2N / RG_SMALL): the flag/scan buffers are free again
+        int* wb_hi = c.rbB;
+        const int nb = cdiv(2 * N, RG_SMALL);
+        k_fill_int_f<<<cdiv(nb, 256), 256, 0, c.s>>>(wb_lo, nb, INT_MAX);
+        cudaMemsetAsync(wb_hi, 0, sizeof(int) * (size_t)nb, c.s);
+        k_region_buckets<<<cdiv(N, 256), 256, 0, c.s>>>(a, nvalid, nsmall, wb_lo, wb_hi, nsmall_regions);
         k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
         cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
         int* ticket = c.ints + IDX_TMP2;
@@ -879,8 +994,9 @@ void launch_forest(Ctx& c, int l, int hdp)
             if (rg_per_sm < 1) rg_per_sm = 1;
         }
         const int rg = min(rg_per_sm, c.tune.region_ctas_per_sm);
-        k_fh_regions<<<c.num_sms * rg, RG_THREADS, sizeof(RegionWin), c.s>>>(a, rv, nvalid, c.rootof, ticket);
-        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), c.s);
+        k_fh_regions<<<c.num_sms * rg, RG_THREADS, sizeof(RegionWin), c.s>>>(a, rv, nvalid, nsmall, nsmall_regions,
+                                                                            wb_lo, wb_hi, c.rootof, ticket);
+        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
         a.passes = 2;
         a.crit_first = 1;
