@@ -259,7 +259,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
     const int kp = a.kp[b];
     const int q = kp >> 2;
     const int qe = q + (FP16 ? 1 : 0);          // FP16: an extra column carries the support mass
-    int e = b + tile_rows_of(kp);
+    int e = b + tile_rows_of(kp, FP16 ? 4 : 0);
     if (u + 1 < ntiles) e = min(e, a.tbeg[u + 1]);
     e = min(e, a.N);
     const int n = e - b;
@@ -284,7 +284,9 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
 
     // ---- phase 1a: per-row inputs, one lane per row (every load of a row in
     // flight at once), kept in shared memory for the element loop
-    //   up:   Pi = node, PTi = its first light child, Qi = its column | child count << 28, M
+    //   up:   Pi = node, PTi = its first light child, M, and Qi = its column
+    //         (bits 0-18) | light children (19-20) | label set is one interval
+    //         (21) | padding of the row (22-23) | first label (24-31)
     //   down: Pi = parent row offset (-1: none), PT = parent weight, Q = own weight, M
     int c_base = 0, c_end = 0;
     if (UP) {
@@ -296,7 +298,24 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
             const int c0 = (int)a.lcoff[row];
             Pi[r] = v;
             PTi[r] = c0;
-            Qi[r] = (v % a.W) | (((int)a.lcoff[row + 1] - c0) << 28);
+            uint32_t qi = (uint32_t)(v % a.W) | ((uint32_t)((int)a.lcoff[row + 1] - c0) << 19);
+            if (!a.full) {
+                // the row's labels are its tree's set; most sets are one interval
+                const uint32_t* m = a.T + (size_t)a.rdt[row] * HDP_WORDS;
+                int k = 0, lo = -1, hi = -1;
+#pragma unroll
+                for (int w = 0; w < HDP_WORDS; ++w) {
+                    const uint32_t x = m[w];
+                    if (x) {
+                        if (lo < 0) lo = 32 * w + __ffs(x) - 1;
+                        hi = 32 * w + 31 - __clz(x);
+                        k += __popc(x);
+                    }
+                }
+                if (k > 0 && hi - lo + 1 == k)
+                    qi |= (1u << 21) | ((uint32_t)(kp - k) << 22) | ((uint32_t)lo << 24);
+            }
+            Qi[r] = (int)qi;
             float m = 0.f;
             if (row + 1 < a.N) {
                 const float s1 = a.rs[row + 1];
@@ -344,7 +363,8 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
             const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe, row = b + r;
             float4 x;
             if (UP) {
-                const int cb = PTi[r], ce = cb + (int)((unsigned)Qi[r] >> 28);
+                const uint32_t qi = (uint32_t)Qi[r];
+                const int cb = PTi[r], ce = cb + (int)((qi >> 19) & 3u);
                 const int lo = max(cb, cc) - cc, hi = min(ce, cc + cn) - cc;
                 if (j < q) {
                     if (first) {
@@ -356,8 +376,14 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
                             for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
                         } else {
                             int lab[4];
-                            slot_labels(a, row, j, lab, nullptr);
-                            const int px = Qi[r] & 0x0fffffff;
+                            if (qi & (1u << 21)) {   // one interval: slot s holds label lo + s
+                                const int lo = (int)(qi >> 24), k = kp - (int)((qi >> 22) & 3u);
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) lab[i] = 4 * j + i < k ? lo + 4 * j + i : -1;
+                            } else {
+                                slot_labels(a, row, j, lab, nullptr);
+                            }
+                            const int px = (int)(qi & 0x7ffffu);
                             const int4 Lp = a.imL[v];
                             const int4* Rrow = a.imR + (size_t)(v - px);
 #pragma unroll
@@ -638,7 +664,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
 }
 
 template <bool FP16>
-__host__ __device__ constexpr int agg_xcap() { return TILE_FLOATS / 4 + (FP16 ? TILE_ROWS_MAX : 0); }   // float4 per warp
+__host__ __device__ constexpr int agg_xcap() { return TILE_FLOATS / 4; }   // float4 per warp (tile_rows_of fits FP16's mass column)
 // per warp: X | M, P, PT, Q (TILE_ROWS_MAX each) | CIN (80 float4) | CO, CS (AGG_CHUNK each)
 template <bool FP16>
 __host__ __device__ constexpr int agg_warp_f4() { return agg_xcap<FP16>() + TILE_ROWS_MAX + 80 + AGG_CHUNK / 2; }

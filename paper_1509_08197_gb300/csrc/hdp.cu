@@ -195,10 +195,11 @@ static void layout_buffers(Ctx& c)
         size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
         K = std::max(K, (size_t)c.dim[l].N * kp);
         // every tile but the last of a run is full: with one label set per
-        // layer (full range, top layer) it holds tile_rows_of(kp) rows,
+        // layer (full range, top layer) it holds tile_rows_of(kp, extra) rows,
         // otherwise at least 4 * TILE_ROWS_MAX costs (the narrowest rows)
         const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.nlev - 1;
-        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp) : (size_t)c.dim[l].N * kp / (4 * TILE_ROWS_MAX);
+        const int extra = c.p.storage == HDP_STORE_FP16 ? 4 : 0;
+        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp, extra) : (size_t)c.dim[l].N * kp / (4 * TILE_ROWS_MAX);
         tiles = std::max(tiles, t);
     }
     c.vol_elems = K;
@@ -216,6 +217,7 @@ static const char* setup_params(Ctx& c, const hdp_params* p)
 {
     c.p = *p;
     if (p->width < 2 || p->height < 2) return "width and height must be >= 2";
+    if (p->width >= (1 << 19)) return "width must be below 2^19";   // packed with row data in the aggregation
     if (p->max_disp < 1 || p->max_disp > HDP_MAX_DISP) return "max_disp must be in 1..255";
     if (p->levels < 1 || p->levels > HDP_MAX_LEVELS) return "levels must be in 1..8";
     if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST) return "unknown tree";
@@ -669,7 +671,11 @@ extern "C" int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, siz
             for (int k = 0; k < HDP_WORDS; ++k) o[(size_t)v * HDP_WORDS + k] = T[(size_t)r[v] * HDP_WORDS + k];
         break;
     }
-    case HDP_STAGE_BFS: TRY_CUDA(cudaMemcpy(h_dst, c.bfs, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_BFS:
+        launch_bfs(c, level);
+        TRY_CUDA(cudaStreamSynchronize(c.s));
+        TRY_CUDA(cudaMemcpy(h_dst, c.bfs, bytes, cudaMemcpyDeviceToHost));
+        break;
     case HDP_STAGE_PARENT: TRY_CUDA(cudaMemcpy(h_dst, c.par, bytes, cudaMemcpyDeviceToHost)); break;
     case HDP_STAGE_DEPTH: TRY_CUDA(cudaMemcpy(h_dst, c.depth, bytes, cudaMemcpyDeviceToHost)); break;
     case HDP_STAGE_PRIOR: TRY_CUDA(cudaMemcpy(h_dst, c.prior[level], bytes, cudaMemcpyDeviceToHost)); break;

@@ -20,9 +20,11 @@
 // HDP: 3.3 ms at 1, 17.8 ms at 16), so only isolated tiles are "chains".
 #define CHAIN_MAX 1
 #define TILE_ROWS_MAX 256   // rows per tile at most (the narrowest rows, kp = 4, fill 1024 floats)
-__host__ __device__ __forceinline__ int tile_rows_of(int kp)
+// rows of width kp per tile; FP16 storage adds a support-mass float4 per row
+// in shared memory (extra = 4), so that a tile always fits TILE_FLOATS floats
+__host__ __device__ __forceinline__ int tile_rows_of(int kp, int extra)
 {
-    const int r = kp >= TILE_FLOATS ? 1 : TILE_FLOATS / kp;
+    const int r = kp + extra >= TILE_FLOATS ? 1 : TILE_FLOATS / (kp + extra);
     return r < TILE_ROWS_MAX ? r : TILE_ROWS_MAX;
 }
 
@@ -169,6 +171,7 @@ int edge_bits(int N);
 
 // order.cu
 void launch_order(Ctx& c, int l);
+void launch_bfs(Ctx& c, int l);
 
 // aggregate.cu
 void launch_aggregate(Ctx& c, int l);

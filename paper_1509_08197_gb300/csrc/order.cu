@@ -278,13 +278,13 @@ __global__ void k_runstart(const uint32_t* keys_sorted, int N, int* runstart)
 
 // a tile starts at every (light level, width) run start and every
 // tile_rows(width) rows after it; tiles may split heavy paths
-__global__ void k_tile_flags(const uint32_t* keys_sorted, const int* runstart, int N, uint32_t* flag)
+__global__ void k_tile_flags(const uint32_t* keys_sorted, const int* runstart, int N, int extra, uint32_t* flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     uint32_t key = keys_sorted[i];
     int kp = 4 * (int)((key & 63u) + 1);
-    flag[i] = ((i - runstart[key]) % tile_rows_of(kp)) == 0;
+    flag[i] = ((i - runstart[key]) % tile_rows_of(kp, extra)) == 0;
 }
 
 __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uint32_t* keys_sorted, int N, int* tbeg,
@@ -378,16 +378,11 @@ void launch_order(Ctx& c, int l)
     k_keys<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tbase, c.nbase, c.tour, N, c.depth, c.pre2, c.pre3, c.light,
                              c.ints + IDX_NTREES);
 
-    // breadth-first order: preorder (children by id) stably sorted by depth
-    k_scatter_bfs<<<g, 256, 0, s>>>(c.pre2, c.depth, N, c.ka, c.va, c.st);
-    int dbits = 1;
-    while ((1 << dbits) < N) ++dbits;
-    int where = radix_sort(c.ka, c.va, c.kb, c.vb, dN, N, dbits, c.tmp, s);
-    cudaMemcpyAsync(c.bfs, where ? c.vb : c.va, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
+    // (the breadth-first order itself is only an output: launch_bfs, on request)
 
     // aggregation layout: heavy-first preorder stably sorted by (light level, width)
     k_scatter_layout<<<g, 256, 0, s>>>(c.pre3, c.light, c.rootof, c.T, N, c.ka, c.va, c.st);
-    where = radix_sort(c.ka, c.va, c.kb, c.vb, dN, N, 11, c.tmp, s);
+    int where = radix_sort(c.ka, c.va, c.kb, c.vb, dN, N, 11, c.tmp, s);
     uint32_t* ksorted = where ? c.kb : c.ka;
     cudaMemcpyAsync(c.lay, where ? c.vb : c.va, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
     uint32_t* lccnt = where ? c.ka : c.kb;   // the free ping-pong buffer
@@ -405,7 +400,7 @@ void launch_order(Ctx& c, int l)
     // tiles
     k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
     k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
-    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.ustart_flag);
+    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0, c.ustart_flag);
     scan_u32(c.ustart_flag, c.uid, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NUNITS), s);
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
@@ -424,4 +419,19 @@ void launch_order(Ctx& c, int l)
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_wfirst, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_wcount, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
     k_work_fill<<<g, 256, 0, s>>>(c.wflag, c.wid, c.ubeg, ksorted, dT, c.wbeg, c.lvl_wfirst, c.lvl_wcount);
+}
+
+// The breadth-first order of layer l (R15): the preorder with children by id,
+// stably sorted by depth.  The aggregation does not need it (it walks the
+// heavy-path layout), so it is built only when asked for, from the depths and
+// preorder that stay in place while layer l's tree is the current one.
+void launch_bfs(Ctx& c, int l)
+{
+    const int N = c.dim[l].N;
+    cudaStream_t s = c.s;
+    k_scatter_bfs<<<cdiv(N, 256), 256, 0, s>>>(c.pre2, c.depth, N, c.ka, c.va, c.st);
+    int dbits = 1;
+    while ((1 << dbits) < N) ++dbits;
+    const int where = radix_sort(c.ka, c.va, c.kb, c.vb, c.ints + IDX_N, N, dbits, c.tmp, s);
+    cudaMemcpyAsync(c.bfs, where ? c.vb : c.va, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
 }

@@ -22,23 +22,30 @@ __device__ __forceinline__ void warp_argmin(int& v, int& x)
 // ties) of the 5x5 box sum of the exact integer cost, for the left view; the
 // right view is checked at (cx - dL, cy) with the right-reference cost (box
 // columns clamped to the image).  Consistent centres vote for dL.
-__global__ void k_prior(const int4* __restrict__ L, const int4* __restrict__ R, int W, int H, int dl, CostK ck,
-                        unsigned long long* hist)
+#define PRIOR_THREADS 256
+
+__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const int4* __restrict__ L, const int4* __restrict__ R, int W,
+                                                         int H, int dl, CostK ck, unsigned long long* hist)
 {
+    // the 25 pixels of the box in the reference view are the same for every
+    // label: one copy per warp in shared memory
+    __shared__ int4 box[PRIOR_THREADS / 32][25];
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int na = W / 5, nb = H / 5;
-    if (wid >= na * nb) return;
+    if (wid >= na * nb) return;   // whole warps leave together
+    int4* sb = box[threadIdx.x >> 5];
     const int cx = 5 * (wid % na) + 2, cy = 5 * (wid / na) + 2;
+    if (lane < 25) sb[lane] = L[(size_t)(cy + lane / 5 - 2) * W + cx + lane % 5 - 2];
+    __syncwarp();
     int best = INT_MAX, bx = INT_MAX;
     for (int x = lane; x <= dl; x += 32) {
         int t = 0;
         for (int dy = -2; dy <= 2; ++dy) {
-            const int4* rowL = L + (size_t)(cy + dy) * W;
             const int4* rowR = R + (size_t)(cy + dy) * W;
             for (int dx = -2; dx <= 2; ++dx) {
                 int px = cx + dx;
-                t += cost_q(rowL[px], rowR[max(px - x, 0)], ck);
+                t += cost_q(sb[(dy + 2) * 5 + dx + 2], rowR[max(px - x, 0)], ck);
             }
         }
         if (t < best) { best = t; bx = x; }
@@ -47,15 +54,17 @@ __global__ void k_prior(const int4* __restrict__ L, const int4* __restrict__ R, 
     const int dL = bx;
     const int u = cx - dL;
     if (u < 0) return;
+    __syncwarp();
+    if (lane < 25) sb[lane] = R[(size_t)(cy + lane / 5 - 2) * W + min(max(u + lane % 5 - 2, 0), W - 1)];
+    __syncwarp();
     best = INT_MAX; bx = INT_MAX;
     for (int x = lane; x <= dl; x += 32) {
         int t = 0;
         for (int dy = -2; dy <= 2; ++dy) {
             const int4* rowL = L + (size_t)(cy + dy) * W;
-            const int4* rowR = R + (size_t)(cy + dy) * W;
             for (int dx = -2; dx <= 2; ++dx) {
                 int uu = min(max(u + dx, 0), W - 1);
-                t += cost_q(rowR[uu], rowL[min(uu + x, W - 1)], ck);
+                t += cost_q(sb[(dy + 2) * 5 + dx + 2], rowL[min(uu + x, W - 1)], ck);
             }
         }
         if (t < best) { best = t; bx = x; }
@@ -79,7 +88,8 @@ void launch_prior(Ctx& c, int l)
     if (!uniform) {
         int centres = (d.W / 5) * (d.H / 5);
         if (centres > 0)
-            k_prior<<<cdiv(centres * 32, 256), 256, 0, c.s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d, cost_consts(c, l), hist);
+            k_prior<<<cdiv(centres * 32, PRIOR_THREADS), PRIOR_THREADS, 0, c.s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d,
+                                                                               cost_consts(c, l), hist);
     }
     k_prior_finish<<<1, 256, 0, c.s>>>(hist, d.d, c.prior[l], uniform);
 }
