@@ -274,12 +274,23 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
     int* PTi = (int*)PT;
     int* Qi = (int*)Q;
 
+    // FP16 rows of a multiple of 8 labels starting on a 16-byte boundary move
+    // with TMA bulk copies too (full range: always); other FP16 tiles use
+    // vector loads and stores
+    const bool tma16 = FP16 && (kp & 7) == 0 && (base & 7) == 0;
+    // half rows staged at the tail of X (widened in place by phase 1b)
+    const uint32_t s16 = TILE_FLOATS * 4 - (uint32_t)(n * kp * 2);
+    const __half* X16 = (const __half*)((const char*)X + s16);
+
     // the previous tile's bulk store reads X: let it finish before X is rewritten
-    if (!FP16 && lane == 0) bulk_store_drain();
+    if (lane == 0) bulk_store_drain();
     __syncwarp();
-    if (!FP16 && !UP) {
+    if (!UP && (!FP16 || tma16)) {
         // the tile's U rows are one contiguous run: one TMA bulk copy into X
-        if (lane == 0) bulk_load(X, a.vol + base, (uint32_t)(n * kp * sizeof(float)), bar);
+        if (lane == 0) {
+            if (FP16) bulk_load((char*)X + s16, a.volh + base, (uint32_t)(n * kp * 2), bar);
+            else bulk_load(X, a.vol + base, (uint32_t)(n * kp * sizeof(float)), bar);
+        }
     }
 
     // ---- phase 1a: per-row inputs, one lane per row (every load of a row in
@@ -337,9 +348,30 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
         }
     }
     __syncwarp();
-    if (!FP16 && !UP) {
+    if (!UP && (!FP16 || tma16)) {
         mbar_wait(a.st, bar, bar_phase);
         bar_phase ^= 1u;
+    }
+    if (!UP && tma16) {
+        // widen the staged half rows in place into X's layout (q vectors and a
+        // mass slot per row), 32 vectors per step, all reads of a step before
+        // its writes.  Element e's float slot lies below its own half slot
+        // (a tile fits TILE_FLOATS floats), and half slots grow with e, so a
+        // step never overwrites halves of a later step.
+        for (int e0 = 0; e0 < n * qe; e0 += 32) {
+            const int e = e0 + lane;
+            const int r = qe > 1 ? (int)__umulhi((uint32_t)e, mqe) : e, j = e - r * qe;
+            const bool ok = e < n * qe && j < q;
+            uint2 raw = make_uint2(0u, 0u);
+            if (ok) raw = *(const uint2*)(X16 + (size_t)r * kp + 4 * j);
+            __syncwarp();
+            if (ok) {
+                const float2 lo = __half22float2(*(const __half2*)&raw.x);
+                const float2 hi = __half22float2(*(const __half2*)&raw.y);
+                X[e] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+            __syncwarp();
+        }
     }
 
     // ---- phase 1b: the affine inputs of every (row, column) of the tile.  Up:
@@ -404,7 +436,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
                 const int po = Pi[r];
                 const float cw = Q[r];
                 if (j < q) {
-                    const float4 U = FP16 ? load_row4<FP16>(a, base + (size_t)r * kp + 4 * j) : X[idx];
+                    const float4 U = (!FP16 || tma16) ? X[idx] : load_row4<FP16>(a, base + (size_t)r * kp + 4 * j);
                     x = make_float4(cw * U.x, cw * U.y, cw * U.z, cw * U.w);
                     if (po >= 0) {
                         const float4 cp = FP16 ? load_row4_cg<FP16>(a, (size_t)po + 4 * j)
@@ -577,7 +609,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
         X[idx] = fma4(PT[r], CIN[j], X[idx]);
     }
     __syncwarp();
-    if (FP16) {
+    if (FP16 && !tma16) {
         for (int idx = lane; idx < n * q; idx += 32) {
             const int r = q > 1 ? (int)__umulhi((uint32_t)idx, mq) : idx, j = idx - r * q;
             float4 x = X[r * qe + j];
@@ -585,7 +617,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
             x = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);
             store_row4<FP16>(a, base + (size_t)r * kp + 4 * j, x);
         }
-    } else {
+    } else if (!FP16) {
         // X holds the tile's rows exactly as laid out in HBM: one TMA bulk store
         __syncwarp();
         if (lane == 0) bulk_store((UP ? a.vol : a.vout) + base, X, (uint32_t)(n * kp * sizeof(float)));
@@ -661,6 +693,35 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
         for (int f = lane; f < nf; f += 32) cin[f] = xl[f];
         __syncwarp();
     }
+    if (tma16) {
+        // narrow in place to normalised halves, 32 vectors per step in
+        // increasing order, all reads of a step (vector and its row's mass)
+        // before its writes: a vector's half slot ends before the float slot
+        // of any vector or mass of a later step
+        __half* H16 = (__half*)X;
+        for (int e0 = 0; e0 < n * qe; e0 += 32) {
+            const int e = e0 + lane;
+            const int r = qe > 1 ? (int)__umulhi((uint32_t)e, mqe) : e, j = e - r * qe;
+            const bool ok = e < n * qe && j < q;
+            float4 v = f4(0.f);
+            float inv = 0.f;
+            if (ok) {
+                v = X[e];
+                inv = 1.f / X[r * qe + q].x;
+            }
+            __syncwarp();
+            if (ok) {
+                const __half2 h0 = __floats2half2_rn(v.x * inv, v.y * inv);
+                const __half2 h1 = __floats2half2_rn(v.z * inv, v.w * inv);
+                uint2 raw;
+                raw.x = *(const unsigned*)&h0;
+                raw.y = *(const unsigned*)&h1;
+                *(uint2*)(H16 + (size_t)r * kp + 4 * j) = raw;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) bulk_store(a.volh + base, X, (uint32_t)(n * kp * 2));
+    }
 }
 
 template <bool FP16>
@@ -708,7 +769,7 @@ __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
         else
             for (int u = s; u < e; ++u) tile_pass<FP16, UP>(a, u, chained, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
-    if (!FP16 && lane == 0) bulk_store_complete();
+    if (lane == 0) bulk_store_complete();
 }
 
 static size_t agg_smem(bool fp16)

@@ -172,9 +172,16 @@ def test_end_to_end_match_and_host_path():
     assert (D == D_ref).mean() > 0.995
 
 
-def test_fp16_storage_error():
-    pair = workload_pair("third")
-    base = dict(width=463, height=370, max_disp=79, levels=4, tree="mst")
+@pytest.mark.parametrize("case", ["hdp_mst_463x370", "full_st_96x72"])
+def test_fp16_storage_error(case):
+    # HDP layers mix row widths (tiles with and without TMA bulk copies); the
+    # full-range case has 16-label rows, so every tile moves by bulk copies
+    if case == "hdp_mst_463x370":
+        pair = workload_pair("third")
+        base = dict(width=463, height=370, max_disp=79, levels=4, tree="mst")
+    else:
+        pair = workload_pair("tiny")
+        base = dict(width=96, height=72, max_disp=15, levels=1, mode="full", tree="st")
     r32 = _run_layers(hdp.HDPParams(**base), pair)
     r16 = _run_layers(hdp.HDPParams(storage="fp16", **base), pair)
     for l in r32:
