@@ -45,11 +45,6 @@ struct AggArgs {
     const int* d_ntiles;
     const int* lvl_first;
     const int* lvl_count;
-    const int* cstart;
-    const int* cend;
-    const int* wbeg;
-    const int* lvl_wfirst;
-    const int* lvl_wcount;
     float* vol;          // up-pass values U (and the down pass input)
     float* vout;         // down-pass output C (== vol for in-place aggregation)
     const float* Ein;    // optional dense cost volume [N][X] (all labels) instead of the matching cost
@@ -250,7 +245,7 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 }
 
 template <bool FP16, bool UP>
-__device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, float* M, float* P, float* PT, float* Q,
+__device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float* Q,
                           float4* CIN, int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
 {
     const int lane = threadIdx.x & 31;
@@ -519,7 +514,7 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
     const bool need = M[rfirst] != 0.f;
     const int nf = 4 * qe;
     float* cin = (float*)CIN;
-    if (need && !chained) {
+    if (need) {
         const int dir = UP ? 1 : -1;
         int D = 0;            // distance of the inclusive value (0: wait failed)
         // the neighbour's inclusive value is often out already: then this
@@ -597,10 +592,9 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
             }
             __syncwarp();
         }
-    } else if (!need) {
+    } else {
         for (int f = lane; f < nf; f += 32) cin[f] = 0.f;
     }
-    // (chained and linked: CIN already holds the previous tile's boundary row)
     __syncwarp();
 
     // ---- phase 4: final values, stores, inclusive value for the next tile
@@ -624,7 +618,16 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
     }
     if (FP16)
         for (int r = lane; r < n; r += 32) (UP ? a.nup : a.nd)[b + r] = X[r * qe + q].x;
-    if (!chained) {
+    // the inclusive value is read only by the neighbour that continues this
+    // tile's last path (up: the tile above, if this tile's first row is not a
+    // path top; down: the tile below, if its first row is not a top)
+    bool linked;
+    if (UP) {
+        linked = !signbit(a.rs[b]) && u > 0;
+    } else {
+        linked = u + 1 < ntiles && !signbit(a.rs[a.tbeg[u + 1]]);
+    }
+    if (linked) {
         float* dst = a.inclA + (size_t)u * SCR_STRIDE;
         const float* xl = (const float*)(X + rlast * qe);
         for (int f = lane; f < nf; f += 32) dst[f] = xl[f];
@@ -687,12 +690,6 @@ __device__ void tile_pass(const AggArgs& a, int u, bool chained, float4* X, floa
         }
     }
     __syncwarp();
-    if (chained) {
-        // the boundary row is the carry of the next tile of the chain
-        const float* xl = (const float*)(X + rlast * qe);
-        for (int f = lane; f < nf; f += 32) cin[f] = xl[f];
-        __syncwarp();
-    }
     if (tma16) {
         // narrow in place to normalised halves, 32 vectors per step in
         // increasing order, all reads of a step (vector and its row's mass)
@@ -734,9 +731,9 @@ template <bool FP16, bool UP>
 __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
 {
     extern __shared__ float4 smem[];
-    const int cnt = a.lvl_wcount[a.level];
+    const int cnt = a.lvl_count[a.level];
     if (cnt == 0) return;
-    const int first = a.lvl_wfirst[a.level];
+    const int first = a.lvl_first[a.level];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* X = smem + (size_t)warp * agg_warp_f4<FP16>();
     float* M = (float*)(X + agg_xcap<FP16>());
@@ -757,17 +754,10 @@ __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
         if (lane == 0) t = atomicAdd(tk, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= cnt) break;
-        // up: bottom units first (carries flow upwards); down: top units first.
+        // up: bottom tiles first (carries flow upwards); down: top tiles first.
         // A tile only waits on tiles with earlier tickets, so the waits end.
-        const int k = UP ? first + cnt - 1 - t : first + t;
-        const int s = a.wbeg[k], e = a.wbeg[k + 1];
-        // a short chain runs on this warp alone, in recurrence order, each tile
-        // handing its boundary row to the next in shared memory
-        const bool chained = a.cend[s] - a.cstart[s] + 1 <= CHAIN_MAX;
-        if (UP)
-            for (int u = e - 1; u >= s; --u) tile_pass<FP16, UP>(a, u, chained, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
-        else
-            for (int u = s; u < e; ++u) tile_pass<FP16, UP>(a, u, chained, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
+        const int u = UP ? first + cnt - 1 - t : first + t;
+        tile_pass<FP16, UP>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
     if (lane == 0) bulk_store_complete();
 }
@@ -830,11 +820,6 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.d_ntiles = c.ints + IDX_NUNITS;
     a.lvl_first = c.lvl_first;
     a.lvl_count = c.lvl_count;
-    a.cstart = c.cstart;
-    a.cend = c.cend;
-    a.wbeg = c.wbeg;
-    a.lvl_wfirst = c.lvl_wfirst;
-    a.lvl_wcount = c.lvl_wcount;
     a.vol = vol_up ? vol_up : c.vol;
     a.vout = vol_down ? vol_down : a.vol;
     a.Ein = Ein;

@@ -968,14 +968,14 @@ void launch_forest(Ctx& c, int l, int hdp)
         k_region_keys<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, rcnt, rbits, (uint32_t*)c.listA,
                                                           (uint32_t*)c.listB, nvalid, nsmall);
         const int where = radix_sort((uint32_t*)c.listA, (uint32_t*)c.listB, (uint32_t*)c.raA, (uint32_t*)c.raB,
-                                     c.ints + IDX_NEDGES, 2 * N, rbits + 1, c.tmp, c.s);
+                                     c.ints + IDX_NEDGES, 2 * N, rbits + 1, c.tmp, c.scan, c.s);
         const uint32_t* rk = (const uint32_t*)(where ? c.raA : c.listA);
         const uint32_t* rv = (const uint32_t*)(where ? c.raB : c.listB);
         uint32_t* flags = (uint32_t*)c.rbA;
         uint32_t* pos = (uint32_t*)c.rbB;
         uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
         k_class_flags<<<cdiv(2 * N, 256), 256, 0, c.s>>>(rk, nvalid, 0, flags);
-        scan_u32(flags, pos, nvalid, 2 * N, true, c.tmp, total, c.s);
+        scan_u32(flags, pos, nvalid, 2 * N, true, c.scan, total, c.s);
         k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, nvalid, c.cls_start, total, c.ints + IDX_NCLS);
         int* wb_lo = c.rbA;     // buckets (at most 2N / RG_SMALL): the flag/scan buffers are free again
         int* wb_hi = c.rbB;
@@ -1010,7 +1010,7 @@ void launch_forest(Ctx& c, int l, int hdp)
         uint32_t* pos = (uint32_t*)c.listA;
         uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
         k_class_flags<<<cdiv(2 * N, 256), 256, 0, c.s>>>(c.sorted, c.ints + IDX_NEDGES, a.ebits, flags);
-        scan_u32(flags, pos, c.ints + IDX_NEDGES, 2 * N, true, c.tmp, total, c.s);
+        scan_u32(flags, pos, c.ints + IDX_NEDGES, 2 * N, true, c.scan, total, c.s);
         k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, c.ints + IDX_NEDGES, c.cls_start, total,
                                                            c.ints + IDX_NCLS);
         static bool configured = false;

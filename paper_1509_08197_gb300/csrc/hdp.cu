@@ -176,13 +176,6 @@ static void layout_buffers(Ctx& c)
     c.ubeg = carve<int>(c, N0);
     c.lvl_first = carve<int>(c, MAX_LIGHT_LEVELS);
     c.lvl_count = carve<int>(c, MAX_LIGHT_LEVELS);
-    c.cstart = carve<int>(c, N0);
-    c.cend = carve<int>(c, N0);
-    c.wflag = carve<uint32_t>(c, N0);
-    c.wid = carve<uint32_t>(c, N0);
-    c.wbeg = carve<int>(c, N0 + 1);
-    c.lvl_wfirst = carve<int>(c, MAX_LIGHT_LEVELS);
-    c.lvl_wcount = carve<int>(c, MAX_LIGHT_LEVELS);
     c.tickets = carve<int>(c, 2 * MAX_LIGHT_LEVELS);
     c.nup = carve<float>(c, N0);
     c.nfull = carve<float>(c, N0);
@@ -190,6 +183,11 @@ static void layout_buffers(Ctx& c)
     c.st = carve<DevStatus>(c, 1);
     c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
     c.tmp = carve<uint32_t>(c, c.tmp_words);
+    // single-pass scans: the longest is over the 2N edge slots (radix
+    // histograms are shorter)
+    c.scan.max_tiles = scan_state_tiles((int)E2);
+    c.scan.state = carve<unsigned long long>(c, c.scan.max_tiles);
+    c.scan.ctr = carve<unsigned int>(c, 2);
     size_t K = 0, tiles = 0;
     for (int l = 0; l < c.nlev; ++l) {
         size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
@@ -320,6 +318,9 @@ extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
     TRY_CUDA(cudaMemcpy(c.full_mask, hc.fm, sizeof(hc.fm), cudaMemcpyHostToDevice));
     TRY_CUDA(cudaMemset(c.st, 0, sizeof(DevStatus)));
     TRY_CUDA(cudaMemset(c.ints, 0, sizeof(int) * IDX_COUNT));
+    c.scan.st = c.st;
+    TRY_CUDA(cudaMemset(c.scan.state, 0, sizeof(unsigned long long) * c.scan.max_tiles));
+    TRY_CUDA(cudaMemset(c.scan.ctr, 0, 2 * sizeof(unsigned int)));
     *out = ctx;
     return HDP_OK;
 }
@@ -885,6 +886,9 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
     TRY_CUDA(cudaMemcpyAsync(c.full_mask, hc.fm, sizeof(hc.fm), cudaMemcpyHostToDevice, c.s));
     TRY_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
     TRY_CUDA(cudaMemsetAsync(c.ints, 0, sizeof(int) * IDX_COUNT, c.s));
+    c.scan.st = c.st;
+    TRY_CUDA(cudaMemsetAsync(c.scan.state, 0, sizeof(unsigned long long) * c.scan.max_tiles, c.s));
+    TRY_CUDA(cudaMemsetAsync(c.scan.ctr, 0, 2 * sizeof(unsigned int), c.s));
     // the host constants above must outlive the copies: wait for them
     TRY_CUDA(cudaStreamSynchronize(c.s));
     int rc = hdp_build_trees(ctx, d_left, d_right, pitch);

@@ -13,12 +13,6 @@
 // aggregation tiles: consecutive rows of one width holding about TILE_FLOATS costs
 #define TILE_FLOATS 2048
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
-// chains of linked tiles up to this length run on one warp, in order, with
-// the carry in shared memory; longer chains use the decoupled look-back.
-// Measured: a warp walking a chain serially loses the overlap that parallel
-// tiles with look-back have (1390x1110 full range: 7.4 ms at 1, 8.7 ms at 16;
-// HDP: 3.3 ms at 1, 17.8 ms at 16), so only isolated tiles are "chains".
-#define CHAIN_MAX 1
 #define TILE_ROWS_MAX 256   // rows per tile at most (the narrowest rows, kp = 4, fill 1024 floats)
 // rows of width kp per tile; FP16 storage adds a support-mass float4 per row
 // in shared memory (extra = 4), so that a tile always fits TILE_FLOATS floats
@@ -117,15 +111,6 @@ struct Ctx {
     float* aggM = nullptr;           // [max_tiles]
     int* lvl_first = nullptr;        // [MAX_LIGHT_LEVELS] first tile of the level
     int* lvl_count = nullptr;        // [MAX_LIGHT_LEVELS]
-    // work units: a chain of at most CHAIN_MAX linked tiles (tiles that cut the
-    // same heavy path) is one unit; every tile of a longer chain is its own
-    int* cstart = nullptr;           // [tiles] first tile of the tile's chain
-    int* cend = nullptr;             // [tiles] last tile of the tile's chain
-    uint32_t* wflag = nullptr;       // [tiles] 1 where a unit starts
-    uint32_t* wid = nullptr;         // [tiles] exclusive count of unit starts
-    int* wbeg = nullptr;             // [units + 1] first tile of each unit (+ the tile count)
-    int* lvl_wfirst = nullptr;       // [MAX_LIGHT_LEVELS] first unit of the level
-    int* lvl_wcount = nullptr;       // [MAX_LIGHT_LEVELS]
     int* tickets = nullptr;          // [2][MAX_LIGHT_LEVELS]
     int* nunits = nullptr;
 
@@ -139,6 +124,7 @@ struct Ctx {
 
     // scalars on the device
     int* ints = nullptr;   // see IDX_* below
+    ScanState scan = {};   // single-pass scan scratch (zero between scans)
     uint32_t* tmp = nullptr;   // scan / sort scratch
     size_t tmp_words = 0;
     DevStatus* st = nullptr;
@@ -151,7 +137,7 @@ struct Ctx {
 // slots of Ctx::ints
 enum {
     IDX_NEDGES = 0, IDX_RISKY, IDX_NCLS, IDX_NARCS, IDX_N, IDX_CTR0, IDX_CTR1, IDX_CTR2, IDX_CTR3, IDX_CTR4,
-    IDX_K, IDX_NTREES, IDX_NLC, IDX_NUNITS, IDX_ENGINE, IDX_CHANGED, IDX_DRROUNDS, IDX_DRWINDOWS, IDX_NNODES, IDX_NWORK,
+    IDX_K, IDX_NTREES, IDX_NLC, IDX_NUNITS, IDX_ENGINE, IDX_CHANGED, IDX_DRROUNDS, IDX_DRWINDOWS, IDX_NNODES,
     IDX_TMP0 = 24, IDX_TMP1, IDX_TMP2, IDX_TMP3, IDX_COUNT = 32
 };
 

@@ -133,6 +133,6 @@ void launch_edges(Ctx& c, int l, int hdp)
                                                    c.p.beta_num, c.p.beta_den, c.keys0, c.ints + IDX_NEDGES,
                                                    c.weights, c.ints + IDX_RISKY);
     int bits = ebits + 8 + 2 * l;
-    int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, c.ints + IDX_NEDGES, 2 * d.N, bits, c.tmp, c.s);
+    int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, c.ints + IDX_NEDGES, 2 * d.N, bits, c.tmp, c.scan, c.s);
     c.sorted = where ? c.keys1 : c.keys0;
 }

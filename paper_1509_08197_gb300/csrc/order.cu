@@ -301,39 +301,6 @@ __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uin
     atomicAdd(lvl_count + lv, 1);
 }
 
-// chains of tiles: tile u links to u + 1 when the first row of u + 1 is not
-// the top of a heavy path (the boundary cuts a path; never across runs, whose
-// first row is always a top)
-__global__ void k_chain_marks(const int* tbeg, const int* d_ntiles, const float* rs, int* st_in, int* en_in)
-{
-    const int u = blockIdx.x * blockDim.x + threadIdx.x, nt = *d_ntiles;
-    if (u >= nt) return;
-    st_in[u] = (u == 0 || signbit(rs[tbeg[u]])) ? u : -1;
-    en_in[u] = (u + 1 == nt || signbit(rs[tbeg[u + 1]])) ? u : INT_MAX;
-}
-
-__global__ void k_work_flags(const int* cstart, const int* cend, const int* d_ntiles, uint32_t* wflag)
-{
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= *d_ntiles) return;
-    wflag[u] = u == cstart[u] || cend[u] - cstart[u] + 1 > CHAIN_MAX;
-}
-
-__global__ void k_work_fill(const uint32_t* wflag, const uint32_t* wid, const int* tbeg, const uint32_t* keys_sorted,
-                            const int* d_ntiles, int* wbeg, int* lvl_wfirst, int* lvl_wcount)
-{
-    const int u = blockIdx.x * blockDim.x + threadIdx.x, nt = *d_ntiles;
-    if (u >= nt) return;
-    if (u + 1 == nt) wbeg[wid[u] + wflag[u]] = nt;
-    if (!wflag[u]) return;
-    const int k = (int)wid[u];
-    wbeg[k] = u;
-    const int lv = (int)(keys_sorted[tbeg[u]] >> 6);
-    if (lv >= MAX_LIGHT_LEVELS) return;
-    atomicMin(lvl_wfirst + lv, k);
-    atomicAdd(lvl_wcount + lv, 1);
-}
-
 __global__ void k_fill_int(int* p, int n, int v)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -352,7 +319,7 @@ void launch_order(Ctx& c, int l)
     // arcs and their successors
     uint32_t* cnt = c.ka;
     k_arc_count<<<g, 256, 0, s>>>(c.adj, N, cnt);
-    scan_u32(cnt, c.aoff, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NARCS), s);
+    scan_u32(cnt, c.aoff, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NARCS), s);
     k_tour_succ<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, N, d.W, c.succ, c.val);
     cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), s);
     cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), s);
@@ -368,8 +335,8 @@ void launch_order(Ctx& c, int l)
     k_orient<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, c.val, N, d.W, c.par, c.pdir, c.sub, c.tpos_down,
                                c.tpos_up, c.ka, c.kb);
     k_children<<<g, 256, 0, s>>>(c.adj, c.pdir, c.sub, N, d.W, c.vals4, c.hdir);
-    scan_u32(c.ka, c.tbase, dN, N, true, c.tmp, nullptr, s);
-    scan_u32(c.kb, c.nbase, dN, N, true, c.tmp, nullptr, s);
+    scan_u32(c.ka, c.tbase, dN, N, true, c.scan, nullptr, s);
+    scan_u32(c.kb, c.nbase, dN, N, true, c.scan, nullptr, s);
     k_tour_fill<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tpos_up, c.tbase, c.vals4, N, c.ints + IDX_NARCS, c.tour,
                                   c.st);
     device_scan<I4, OpSum>(c.tour, c.tour, c.ints + IDX_NARCS, 2 * N, I4{0, 0, 0, 0}, OpSum(), false, false,
@@ -382,7 +349,7 @@ void launch_order(Ctx& c, int l)
 
     // aggregation layout: heavy-first preorder stably sorted by (light level, width)
     k_scatter_layout<<<g, 256, 0, s>>>(c.pre3, c.light, c.rootof, c.T, N, c.ka, c.va, c.st);
-    int where = radix_sort(c.ka, c.va, c.kb, c.vb, dN, N, 11, c.tmp, s);
+    int where = radix_sort(c.ka, c.va, c.kb, c.vb, dN, N, 11, c.tmp, c.scan, s);
     uint32_t* ksorted = where ? c.kb : c.ka;
     cudaMemcpyAsync(c.lay, where ? c.vb : c.va, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
     uint32_t* lccnt = where ? c.ka : c.kb;   // the free ping-pong buffer
@@ -393,32 +360,20 @@ void launch_order(Ctx& c, int l)
     int* dN1 = c.ints + IDX_TMP1;
     k_set_ints<<<1, 1, 0, s>>>(dN1, N + 1, 0);
     cudaMemsetAsync(lccnt + N, 0, sizeof(uint32_t), s);
-    scan_u32(lccnt, c.lcoff, dN1, N + 1, true, c.tmp, (uint32_t*)(c.ints + IDX_NLC), s);
+    scan_u32(lccnt, c.lcoff, dN1, N + 1, true, c.scan, (uint32_t*)(c.ints + IDX_NLC), s);
     k_rows2<<<g, 256, 0, s>>>(c.lay, c.rowof, c.par, c.pdir, c.hdir, c.adj, c.lcoff, N, d.W, c.prow, c.lcrow);
-    scan_u32((const uint32_t*)c.kp, c.roff, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_K), s);
+    scan_u32((const uint32_t*)c.kp, c.roff, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_K), s);
 
     // tiles
     k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
     k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
     k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0, c.ustart_flag);
-    scan_u32(c.ustart_flag, c.uid, dN, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NUNITS), s);
+    scan_u32(c.ustart_flag, c.uid, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NUNITS), s);
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
     k_tile_fill<<<g, 256, 0, s>>>(c.ustart_flag, c.uid, ksorted, N, c.ubeg, c.lvl_first, c.lvl_count, (int)c.max_tiles,
                                   c.st);
 
-    // chains of linked tiles and the work units over them
-    const int* dT = c.ints + IDX_NUNITS;
-    int* st_in = (int*)c.va;   // the sort's value buffers are free again (the order was copied to lay)
-    int* en_in = (int*)c.vb;
-    k_chain_marks<<<g, 256, 0, s>>>(c.ubeg, dT, c.rs, st_in, en_in);
-    device_scan<int, OpMax>(st_in, c.cstart, dT, N, -1, OpMax(), false, false, (int*)c.tmp, nullptr, s);
-    device_scan<int, OpMin>(en_in, c.cend, dT, N, INT_MAX, OpMin(), false, true, (int*)c.tmp, nullptr, s);
-    k_work_flags<<<g, 256, 0, s>>>(c.cstart, c.cend, dT, c.wflag);
-    scan_u32(c.wflag, c.wid, dT, N, true, c.tmp, (uint32_t*)(c.ints + IDX_NWORK), s);
-    k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_wfirst, MAX_LIGHT_LEVELS, INT_MAX);
-    cudaMemsetAsync(c.lvl_wcount, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
-    k_work_fill<<<g, 256, 0, s>>>(c.wflag, c.wid, c.ubeg, ksorted, dT, c.wbeg, c.lvl_wfirst, c.lvl_wcount);
 }
 
 // The breadth-first order of layer l (R15): the preorder with children by id,
@@ -432,6 +387,6 @@ void launch_bfs(Ctx& c, int l)
     k_scatter_bfs<<<cdiv(N, 256), 256, 0, s>>>(c.pre2, c.depth, N, c.ka, c.va, c.st);
     int dbits = 1;
     while ((1 << dbits) < N) ++dbits;
-    const int where = radix_sort(c.ka, c.va, c.kb, c.vb, c.ints + IDX_N, N, dbits, c.tmp, s);
+    const int where = radix_sort(c.ka, c.va, c.kb, c.vb, c.ints + IDX_N, N, dbits, c.tmp, c.scan, s);
     cudaMemcpyAsync(c.bfs, where ? c.vb : c.va, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
 }

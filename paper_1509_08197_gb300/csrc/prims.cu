@@ -82,8 +82,92 @@ size_t radix_tmp_words(int n_max)
 
 __global__ void k_set_int(int* out, int v) { out[0] = v; }
 
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, uint32_t* out, const int* d_n,
+                                                            int exclusive, ScanState ss, uint32_t* total)
+{
+    __shared__ uint32_t smem[33];
+    __shared__ int s_tile;
+    __shared__ uint32_t s_pre;
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    if (t == 0) s_tile = (int)atomicAdd(ss.ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int n = *d_n;
+    const int nt = (int)cdiv<long long>(n, SCAN_TILE);
+    if (tile < nt && tile >= ss.max_tiles && t == 0) dev_fail(ss.st, DEV_BAD_INPUT, 61);   // scratch too small
+    if (tile < nt && tile < ss.max_tiles) {
+        const long long base = (long long)tile * SCAN_TILE;
+        uint32_t v[SCAN_IPT], x[SCAN_IPT];
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const long long idx = base + (long long)t * SCAN_IPT + i;
+            x[i] = idx < n ? in[idx] : 0u;
+            v[i] = x[i];
+        }
+        const uint32_t tot = block_scan_excl<uint32_t, OpSum>(v, 0u, OpSum(), smem);
+        if (t == 0) {
+            unsigned long long* stp = ss.state;
+            uint32_t pre = 0;
+            if (tile == 0) {
+                atomicExch(stp, (2ull << 32) | tot);
+            } else {
+                atomicExch(stp + tile, (1ull << 32) | tot);
+                // walk back to the nearest inclusive prefix
+                unsigned it = 0;
+                for (int j = tile - 1; j >= 0;) {
+                    const unsigned long long w = *(volatile unsigned long long*)(stp + j);
+                    const uint32_t f = (uint32_t)(w >> 32);
+                    if (f == 0u) {
+                        if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
+                            dev_fail(ss.st, DEV_TIMEOUT, 60);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    pre += (uint32_t)w;
+                    if (f == 2u) break;
+                    --j;
+                }
+                atomicExch(stp + tile, (2ull << 32) | (uint32_t)(pre + tot));
+            }
+            s_pre = pre;
+            if (total && tile == nt - 1) *total = pre + tot;
+        }
+        __syncthreads();
+        const uint32_t pre = s_pre;
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const long long idx = base + (long long)t * SCAN_IPT + i;
+            if (idx < n) out[idx] = pre + v[i] + (exclusive ? 0u : x[i]);
+        }
+    } else if (t == 0 && total && n == 0 && tile == 0) {
+        *total = 0;
+    }
+    // the last block to finish clears the tile states and the counters
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(ss.ctr + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        const int m = min(nt, ss.max_tiles);
+        for (int j = t; j < m; j += SCAN_THREADS) ss.state[j] = 0ull;
+        __syncthreads();
+        if (t == 0) {
+            ss.ctr[0] = 0u;
+            ss.ctr[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+int scan_state_tiles(int n_max) { return (int)cdiv<long long>(n_max > 0 ? n_max : 1, SCAN_TILE) + 1; }
+
 int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
-               uint32_t* tmp, cudaStream_t s)
+               uint32_t* tmp, const ScanState& ss, cudaStream_t s)
 {
     if (n_max <= 0 || key_bits <= 0) return 0;
     int nb = (int)cdiv<long long>(n_max, RS_TILE);
@@ -92,6 +176,9 @@ int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int
     uint32_t* hist = tmp;
     uint32_t* stmp = tmp + 256 * (size_t)nb;
     int* hlen = (int*)(stmp + scan_tmp_words(256 * nb));
+    // digit-major histogram with a fixed stride of nb tiles (tiles past the
+    // live count hold zeros): every pass scans all of it
+    k_set_int<<<1, 1, 0, s>>>(hlen, 256 * nb);
     int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
         const uint32_t* ki = cur ? k1 : k0;
@@ -99,18 +186,17 @@ int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int
         uint32_t* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
         k_rs_hist<<<nb, RS_THREADS, 0, s>>>(ki, d_n, shift, hist, nb);
-        // digit-major histogram with a fixed stride of nb tiles (tiles past the
-        // live count hold zeros): scan all of it
-        k_set_int<<<1, 1, 0, s>>>(hlen, 256 * nb);
-        device_scan<uint32_t, OpSum>(hist, hist, hlen, 256 * nb, 0u, OpSum(), true, false, stmp, nullptr, s);
+        scan_u32(hist, hist, hlen, 256 * nb, true, ss, nullptr, s);
         k_rs_scatter<<<nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, d_n, shift, hist, nb);
         cur ^= 1;
     }
     return cur;
 }
 
-void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, uint32_t* tmp,
+void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, const ScanState& ss,
               uint32_t* total, cudaStream_t s)
 {
-    device_scan<uint32_t, OpSum>(in, out, d_n, n_max, 0u, OpSum(), exclusive, false, tmp, total, s);
+    if (n_max <= 0) return;
+    const int nb = (int)cdiv<long long>(n_max, SCAN_TILE);
+    k_scan1_u32<<<nb, SCAN_THREADS, 0, s>>>(in, out, d_n, exclusive ? 1 : 0, ss, total);
 }

@@ -19,9 +19,6 @@ struct OpSum {
 struct OpMin {
     template <typename T> __device__ __forceinline__ T operator()(T a, T b) const { return b < a ? b : a; }
 };
-struct OpMax {
-    template <typename T> __device__ __forceinline__ T operator()(T a, T b) const { return b > a ? b : a; }
-};
 
 __device__ __forceinline__ int shfl_up(int v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ unsigned shfl_up(unsigned v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
@@ -161,6 +158,20 @@ void device_scan(const T* in, T* out, const int* d_n, int n_max, T ident, Op op,
                                                     reverse ? 1 : 0);
 }
 
+// ------------------------------------------------- single-pass u32 scan ---
+// Sum scan of unsigned ints in one launch: tiles take ids from an atomic
+// ticket (so every tile's predecessors are resident), publish their
+// aggregate, then walk back over published aggregates to the nearest
+// inclusive prefix (decoupled look-back).  The last tile to finish resets the
+// ticket and the tile states, so the scratch is ready for the next call
+// without a clearing launch.  Waits are bounded (DEV_TIMEOUT).
+struct ScanState {
+    unsigned long long* state;   // per tile: flag << 32 | value (flag 1: aggregate, 2: inclusive prefix)
+    unsigned int* ctr;           // [2]: ticket, tiles finished
+    DevStatus* st;
+    int max_tiles;
+};
+
 // ------------------------------------------------------------ radix sort ---
 #define RS_THREADS 256
 #define RS_TILE 2048     // 8 warps x 256 items
@@ -174,10 +185,11 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* _
 // return value says where the result is: 0 -> (k0, v0), 1 -> (k1, v1).
 // tmp: at least 256 * cdiv(n_max, RS_TILE) + cdiv(that, SCAN_TILE) uint32.
 int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
-               uint32_t* tmp, cudaStream_t s);
+               uint32_t* tmp, const ScanState& ss, cudaStream_t s);
 size_t radix_tmp_words(int n_max);
 
 // Exclusive scans used across the library.
-void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, uint32_t* tmp,
+void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, const ScanState& ss,
               uint32_t* total, cudaStream_t s);
+int scan_state_tiles(int n_max);
 size_t scan_tmp_words(int n_max);
