@@ -804,10 +804,10 @@ __global__ void k_forest_init(int* parent, int* size, int* intw, int* best, int*
 __global__ void k_T_init(uint32_t* T, const int* pixset, const uint32_t* table, int N, const int* risky, int always)
 {
     if (!always && !__ldcg(risky)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N * HDP_WORDS) return;
-    int v = i / HDP_WORDS, k = i % HDP_WORDS;
-    T[i] = table[(size_t)pixset[v] * HDP_WORDS + k];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * HDP_WORDS; i += gridDim.x * blockDim.x) {
+        const int v = i / HDP_WORDS, k = i % HDP_WORDS;
+        T[i] = table[(size_t)pixset[v] * HDP_WORDS + k];
+    }
 }
 
 __global__ void k_class_flags(const uint32_t* keys, const int* d_n, int ebits, uint32_t* flags)
@@ -935,7 +935,9 @@ void launch_forest(Ctx& c, int l, int hdp)
     if (hdp) {
         // the reservation engine needs every TreeIntv when it may run
         int always = 0;
-        k_T_init<<<cdiv(N * HDP_WORDS, 256), 256, 0, c.s>>>(c.T, c.pixset, c.table[l], N, c.ints + IDX_RISKY, always);
+        // grid-stride over one wave: it returns at once unless the layer is risky
+        k_T_init<<<min(cdiv(N * HDP_WORDS, 256), c.num_sms * 8), 256, 0, c.s>>>(c.T, c.pixset, c.table[l], N,
+                                                                               c.ints + IDX_RISKY, always);
     }
     void* args[] = {&a};
     // grids sized by the layer (one block per 4K edges at most, one wave at

@@ -188,6 +188,11 @@ static void layout_buffers(Ctx& c)
     c.scan.max_tiles = scan_state_tiles((int)E2);
     c.scan.state = carve<unsigned long long>(c, c.scan.max_tiles);
     c.scan.ctr = carve<unsigned int>(c, 2);
+    c.scan4.max_tiles = c.scan.max_tiles;
+    c.scan4.flags = carve<unsigned int>(c, c.scan4.max_tiles);
+    c.scan4.aggv = carve<I4>(c, c.scan4.max_tiles);
+    c.scan4.inclv = carve<I4>(c, c.scan4.max_tiles);
+    c.scan4.ctr = carve<unsigned int>(c, 2);
     size_t K = 0, tiles = 0;
     for (int l = 0; l < c.nlev; ++l) {
         size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
@@ -319,8 +324,11 @@ extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
     TRY_CUDA(cudaMemset(c.st, 0, sizeof(DevStatus)));
     TRY_CUDA(cudaMemset(c.ints, 0, sizeof(int) * IDX_COUNT));
     c.scan.st = c.st;
+    c.scan4.st = c.st;
     TRY_CUDA(cudaMemset(c.scan.state, 0, sizeof(unsigned long long) * c.scan.max_tiles));
     TRY_CUDA(cudaMemset(c.scan.ctr, 0, 2 * sizeof(unsigned int)));
+    TRY_CUDA(cudaMemset(c.scan4.flags, 0, sizeof(unsigned int) * c.scan4.max_tiles));
+    TRY_CUDA(cudaMemset(c.scan4.ctr, 0, 2 * sizeof(unsigned int)));
     *out = ctx;
     return HDP_OK;
 }
@@ -887,8 +895,11 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
     TRY_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
     TRY_CUDA(cudaMemsetAsync(c.ints, 0, sizeof(int) * IDX_COUNT, c.s));
     c.scan.st = c.st;
+    c.scan4.st = c.st;
     TRY_CUDA(cudaMemsetAsync(c.scan.state, 0, sizeof(unsigned long long) * c.scan.max_tiles, c.s));
     TRY_CUDA(cudaMemsetAsync(c.scan.ctr, 0, 2 * sizeof(unsigned int), c.s));
+    TRY_CUDA(cudaMemsetAsync(c.scan4.flags, 0, sizeof(unsigned int) * c.scan4.max_tiles, c.s));
+    TRY_CUDA(cudaMemsetAsync(c.scan4.ctr, 0, 2 * sizeof(unsigned int), c.s));
     // the host constants above must outlive the copies: wait for them
     TRY_CUDA(cudaStreamSynchronize(c.s));
     int rc = hdp_build_trees(ctx, d_left, d_right, pitch);

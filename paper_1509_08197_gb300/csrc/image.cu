@@ -72,8 +72,10 @@ void launch_pyramid(Ctx& c)
 // 4^l).  With predicted sets (pixset != null), DT-Rule 1 (Eq. cri1) drops
 // edges whose end points' PixelIntv do not intersect; an edge between
 // different sets whose Jaccard ratio already reaches beta marks the layer as
-// "risky" (DT-Rule 2 may then merge different sets).  Surviving edges are
-// appended as keys (w << ebits | e); their order is fixed by the later sort.
+// "risky" (DT-Rule 2 may then merge different sets).  Every edge id has its
+// own key slot: (w << ebits | e) for a surviving edge, all ones otherwise, so
+// that a stable sort on the weight bits alone yields the strict (w, id)
+// order with the dropped slots last; count receives the survivors.
 __global__ void k_edges(const int4* __restrict__ img, int W, int H, int ebits, const int* __restrict__ pixset,
                         const uint32_t* __restrict__ table, const int* __restrict__ canon, int bnum, int bden,
                         uint32_t* keys, int* count, int* weights, int* risky)
@@ -111,15 +113,9 @@ __global__ void k_edges(const int4* __restrict__ img, int W, int H, int ebits, c
             key = ((uint32_t)w << ebits) | (uint32_t)e;
         }
     }
-    unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (m) {
-        int lane = threadIdx.x & 31;
-        int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(count, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (keep) keys[base + __popc(m & ((1u << lane) - 1u))] = key;
-    }
+    if (e < 2 * N) keys[e] = keep ? key : 0xffffffffu;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, __popc(m));
 }
 
 void launch_edges(Ctx& c, int l, int hdp)
@@ -132,7 +128,11 @@ void launch_edges(Ctx& c, int l, int hdp)
                                                    hdp ? c.table[l] : nullptr, hdp ? c.canon[l] : nullptr,
                                                    c.p.beta_num, c.p.beta_den, c.keys0, c.ints + IDX_NEDGES,
                                                    c.weights, c.ints + IDX_RISKY);
-    int bits = ebits + 8 + 2 * l;
-    int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, c.ints + IDX_NEDGES, 2 * d.N, bits, c.tmp, c.scan, c.s);
+    // stable radix sort of all 2N slots on the weight field [ebits, ebits + 8 + 2l):
+    // weights at layer l are below 255 * 4^l < 2^(8 + 2l) - 1, so the dropped
+    // slots (all ones) come after every survivor
+    int* slots = c.ints + IDX_ESLOTS;
+    k_set_int<<<1, 1, 0, c.s>>>(slots, 2 * d.N);
+    int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, slots, 2 * d.N, 8 + 2 * l, c.tmp, c.scan, c.s, ebits);
     c.sorted = where ? c.keys1 : c.keys0;
 }

@@ -339,8 +339,7 @@ void launch_order(Ctx& c, int l)
     scan_u32(c.kb, c.nbase, dN, N, true, c.scan, nullptr, s);
     k_tour_fill<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tpos_up, c.tbase, c.vals4, N, c.ints + IDX_NARCS, c.tour,
                                   c.st);
-    device_scan<I4, OpSum>(c.tour, c.tour, c.ints + IDX_NARCS, 2 * N, I4{0, 0, 0, 0}, OpSum(), false, false,
-                           (I4*)c.tmp, nullptr, s);
+    scan_i4_inclusive(c.tour, c.tour, c.ints + IDX_NARCS, 2 * N, c.scan4, s);
     cudaMemsetAsync(c.ints + IDX_NTREES, 0, sizeof(int), s);
     k_keys<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tbase, c.nbase, c.tour, N, c.depth, c.pre2, c.pre3, c.light,
                              c.ints + IDX_NTREES);

@@ -164,10 +164,97 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
     }
 }
 
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan1_i4(const I4* in, I4* out, const int* d_n, ScanStateI4 ss)
+{
+    __shared__ I4 smem[33];
+    __shared__ int s_tile;
+    __shared__ I4 s_pre;
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    if (t == 0) s_tile = (int)atomicAdd(ss.ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int n = *d_n;
+    const int nt = (int)cdiv<long long>(n, SCAN_TILE);
+    if (tile < nt && tile >= ss.max_tiles && t == 0) dev_fail(ss.st, DEV_BAD_INPUT, 62);   // scratch too small
+    if (tile < nt && tile < ss.max_tiles) {
+        const long long base = (long long)tile * SCAN_TILE;
+        const I4 z = I4{0, 0, 0, 0};
+        I4 v[SCAN_IPT], x[SCAN_IPT];
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const long long idx = base + (long long)t * SCAN_IPT + i;
+            x[i] = idx < n ? in[idx] : z;
+            v[i] = x[i];
+        }
+        const I4 tot = block_scan_excl<I4, OpSum>(v, z, OpSum(), smem);
+        if (t == 0) {
+            I4 pre = z;
+            if (tile > 0) {
+                ss.aggv[tile] = tot;
+                __threadfence();
+                atomicExch(ss.flags + tile, 1u);
+                unsigned it = 0;
+                for (int j = tile - 1; j >= 0;) {
+                    const unsigned f = *(volatile unsigned*)(ss.flags + j);
+                    if (f == 0u) {
+                        if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
+                            dev_fail(ss.st, DEV_TIMEOUT, 63);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    __threadfence();
+                    const I4* src = f == 2u ? ss.inclv : ss.aggv;
+                    const I4 w = I4{__ldcg(&src[j].x), __ldcg(&src[j].y), __ldcg(&src[j].z), __ldcg(&src[j].w)};
+                    pre = w + pre;
+                    if (f == 2u) break;
+                    --j;
+                }
+            }
+            ss.inclv[tile] = pre + tot;
+            __threadfence();
+            atomicExch(ss.flags + tile, 2u);
+            s_pre = pre;
+        }
+        __syncthreads();
+        const I4 pre = s_pre;
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const long long idx = base + (long long)t * SCAN_IPT + i;
+            if (idx < n) out[idx] = pre + v[i] + x[i];   // inclusive
+        }
+    }
+    // the last block to finish clears the flags and the counters
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(ss.ctr + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        const int m = min(nt, ss.max_tiles);
+        for (int j = t; j < m; j += SCAN_THREADS) ss.flags[j] = 0u;
+        __syncthreads();
+        if (t == 0) {
+            ss.ctr[0] = 0u;
+            ss.ctr[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+void scan_i4_inclusive(const I4* in, I4* out, const int* d_n, int n_max, const ScanStateI4& ss, cudaStream_t s)
+{
+    if (n_max <= 0) return;
+    k_scan1_i4<<<(int)cdiv<long long>(n_max, SCAN_TILE), SCAN_THREADS, 0, s>>>(in, out, d_n, ss);
+}
+
 int scan_state_tiles(int n_max) { return (int)cdiv<long long>(n_max > 0 ? n_max : 1, SCAN_TILE) + 1; }
 
 int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
-               uint32_t* tmp, const ScanState& ss, cudaStream_t s)
+               uint32_t* tmp, const ScanState& ss, cudaStream_t s, int first_bit)
 {
     if (n_max <= 0 || key_bits <= 0) return 0;
     int nb = (int)cdiv<long long>(n_max, RS_TILE);
@@ -180,7 +267,7 @@ int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int
     // live count hold zeros): every pass scans all of it
     k_set_int<<<1, 1, 0, s>>>(hlen, 256 * nb);
     int cur = 0;
-    for (int shift = 0; shift < key_bits; shift += 8) {
+    for (int shift = first_bit; shift < first_bit + key_bits; shift += 8) {
         const uint32_t* ki = cur ? k1 : k0;
         const uint32_t* vi = cur ? v1 : v0;
         uint32_t* ko = cur ? k0 : k1;

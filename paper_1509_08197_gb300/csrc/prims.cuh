@@ -172,6 +172,19 @@ struct ScanState {
     int max_tiles;
 };
 
+// The same for int4 sums (in place allowed).  A tile's aggregate and
+// inclusive prefix live in separate arrays, written before flags 1 and 2, so a
+// reader never mistakes one for the other.
+struct ScanStateI4 {
+    unsigned int* flags;   // per tile: 0, 1 (aggregate out), 2 (inclusive prefix out)
+    I4* aggv;
+    I4* inclv;
+    unsigned int* ctr;     // [2]: ticket, tiles finished
+    DevStatus* st;
+    int max_tiles;
+};
+void scan_i4_inclusive(const I4* in, I4* out, const int* d_n, int n_max, const ScanStateI4& ss, cudaStream_t s);
+
 // ------------------------------------------------------------ radix sort ---
 #define RS_THREADS 256
 #define RS_TILE 2048     // 8 warps x 256 items
@@ -180,16 +193,17 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, const int* d_n, int
 __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* kout,
                              uint32_t* vout, const int* d_n, int shift, const uint32_t* hist, int nblocks);
 
-// Stable LSD radix sort of (key, value) pairs on bits [0, key_bits).  vals may
+// Stable LSD radix sort of (key, value) pairs on bits [first_bit, first_bit + key_bits).  vals may
 // be null (keys only).  Buffers ping-pong between (k0, v0) and (k1, v1); the
 // return value says where the result is: 0 -> (k0, v0), 1 -> (k1, v1).
 // tmp: at least 256 * cdiv(n_max, RS_TILE) + cdiv(that, SCAN_TILE) uint32.
 int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
-               uint32_t* tmp, const ScanState& ss, cudaStream_t s);
+               uint32_t* tmp, const ScanState& ss, cudaStream_t s, int first_bit = 0);
 size_t radix_tmp_words(int n_max);
 
 // Exclusive scans used across the library.
 void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool exclusive, const ScanState& ss,
               uint32_t* total, cudaStream_t s);
 int scan_state_tiles(int n_max);
+__global__ void k_set_int(int* out, int v);
 size_t scan_tmp_words(int n_max);
