@@ -244,7 +244,7 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
     }
 }
 
-template <bool FP16, bool UP>
+template <bool FP16, bool UP, int TF>
 __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float* Q,
                           float4* CIN, int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
 {
@@ -254,7 +254,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     const int kp = a.kp[b];
     const int q = kp >> 2;
     const int qe = q + (FP16 ? 1 : 0);          // FP16: an extra column carries the support mass
-    int e = b + tile_rows_of(kp, FP16 ? 4 : 0);
+    int e = b + tile_rows_of(kp, FP16 ? 4 : 0, TF);
     if (u + 1 < ntiles) e = min(e, a.tbeg[u + 1]);
     e = min(e, a.N);
     const int n = e - b;
@@ -274,7 +274,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     // vector loads and stores
     const bool tma16 = FP16 && (kp & 7) == 0 && (base & 7) == 0;
     // half rows staged at the tail of X (widened in place by phase 1b)
-    const uint32_t s16 = TILE_FLOATS * 4 - (uint32_t)(n * kp * 2);
+    const uint32_t s16 = TF * 4 - (uint32_t)(n * kp * 2);
     const __half* X16 = (const __half*)((const char*)X + s16);
 
     // the previous tile's bulk store reads X: let it finish before X is rewritten
@@ -351,7 +351,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         // widen the staged half rows in place into X's layout (q vectors and a
         // mass slot per row), 32 vectors per step, all reads of a step before
         // its writes.  Element e's float slot lies below its own half slot
-        // (a tile fits TILE_FLOATS floats), and half slots grow with e, so a
+        // (a tile fits TF floats), and half slots grow with e, so a
         // step never overwrites halves of a later step.
         for (int e0 = 0; e0 < n * qe; e0 += 32) {
             const int e = e0 + lane;
@@ -721,26 +721,25 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     }
 }
 
-template <bool FP16>
-__host__ __device__ constexpr int agg_xcap() { return TILE_FLOATS / 4; }   // float4 per warp (tile_rows_of fits FP16's mass column)
-// per warp: X | M, P, PT, Q (TILE_ROWS_MAX each) | CIN (80 float4) | CO, CS (AGG_CHUNK each)
-template <bool FP16>
-__host__ __device__ constexpr int agg_warp_f4() { return agg_xcap<FP16>() + TILE_ROWS_MAX + 80 + AGG_CHUNK / 2; }
+// per warp: X (TF floats) | M, P, PT, Q (tile_rows_max(TF) each) | CIN (80 float4) | CO, CS (AGG_CHUNK each)
+template <int TF>
+__host__ __device__ constexpr int agg_warp_f4() { return TF / 4 + tile_rows_max(TF) + 80 + AGG_CHUNK / 2; }
 
-template <bool FP16, bool UP>
-__global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
+template <bool FP16, bool UP, int TF>
+__global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? 4 : 5) k_agg(AggArgs a)
 {
+    constexpr int RM = tile_rows_max(TF);
     extern __shared__ float4 smem[];
     const int cnt = a.lvl_count[a.level];
     if (cnt == 0) return;
     const int first = a.lvl_first[a.level];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* X = smem + (size_t)warp * agg_warp_f4<FP16>();
-    float* M = (float*)(X + agg_xcap<FP16>());
-    float* P = M + TILE_ROWS_MAX;
-    float* PT = P + TILE_ROWS_MAX;
-    float* Q = PT + TILE_ROWS_MAX;
-    float4* CIN = (float4*)(Q + TILE_ROWS_MAX);
+    float4* X = smem + (size_t)warp * agg_warp_f4<TF>();
+    float* M = (float*)(X + TF / 4);
+    float* P = M + RM;
+    float* PT = P + RM;
+    float* Q = PT + RM;
+    float4* CIN = (float4*)(Q + RM);
     int* CO = (int*)(CIN + 80);
     float* CS = (float*)(CO + AGG_CHUNK);
     __shared__ __align__(8) uint64_t bars[AGG_WARPS];
@@ -757,15 +756,13 @@ __global__ void __launch_bounds__(AGG_THREADS, 4) k_agg(AggArgs a)
         // up: bottom tiles first (carries flow upwards); down: top tiles first.
         // A tile only waits on tiles with earlier tickets, so the waits end.
         const int u = UP ? first + cnt - 1 - t : first + t;
-        tile_pass<FP16, UP>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
+        tile_pass<FP16, UP, TF>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
     if (lane == 0) bulk_store_complete();
 }
 
-static size_t agg_smem(bool fp16)
-{
-    return (size_t)AGG_WARPS * (fp16 ? agg_warp_f4<true>() : agg_warp_f4<false>()) * sizeof(float4);
-}
+template <int TF>
+static size_t agg_smem() { return (size_t)AGG_WARPS * agg_warp_f4<TF>() * sizeof(float4); }
 
 CostK cost_consts(const Ctx& c, int l)
 {
@@ -780,17 +777,24 @@ CostK cost_consts(const Ctx& c, int l)
 }
 
 // one resident wave: SMs x the blocks that fit on one SM
-template <bool FP16, bool UP>
+template <bool FP16, bool UP, int TF>
 static void launch_level(const AggArgs& a, int num_sms, int max_per_sm, cudaStream_t s)
 {
-    const size_t sm = agg_smem(FP16);
+    const size_t sm = agg_smem<TF>();
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_agg<FP16, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg<FP16, UP>, AGG_THREADS, sm);
+        cudaFuncSetAttribute(k_agg<FP16, UP, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg<FP16, UP, TF>, AGG_THREADS, sm);
         if (per_sm < 1) per_sm = 1;
     }
-    k_agg<FP16, UP><<<num_sms * min(per_sm, max_per_sm), AGG_THREADS, sm, s>>>(a);
+    k_agg<FP16, UP, TF><<<num_sms * min(per_sm, max_per_sm), AGG_THREADS, sm, s>>>(a);
+}
+
+template <bool UP, int TF>
+static void launch_level_s(const AggArgs& a, bool fp16, int num_sms, int max_per_sm, cudaStream_t s)
+{
+    if (fp16) launch_level<true, UP, TF>(a, num_sms, max_per_sm, s);
+    else launch_level<false, UP, TF>(a, num_sms, max_per_sm, s);
 }
 
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
@@ -841,15 +845,17 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     cudaMemsetAsync(c.tickets, 0, sizeof(int) * 2 * MAX_LIGHT_LEVELS, c.s);
     cudaMemsetAsync(c.tflags, 0, sizeof(int) * 2 * c.max_tiles, c.s);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
+    const bool small_tiles = layer_tile_floats(c, l) == TILE_FLOATS_HDP;
+    const int cap = c.tune.agg_ctas_per_sm;
     for (int lv = levels - 1; lv >= 0; --lv) {
         a.level = lv;
-        if (fp16) launch_level<true, true>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
-        else launch_level<false, true>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
+        if (small_tiles) launch_level_s<true, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
+        else launch_level_s<true, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
     }
     for (int lv = 0; lv < levels; ++lv) {
         a.level = lv;
-        if (fp16) launch_level<true, false>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
-        else launch_level<false, false>(a, c.num_sms, c.tune.agg_ctas_per_sm, c.s);
+        if (small_tiles) launch_level_s<false, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
+        else launch_level_s<false, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
     }
 }
 

@@ -198,11 +198,13 @@ static void layout_buffers(Ctx& c)
         size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
         K = std::max(K, (size_t)c.dim[l].N * kp);
         // every tile but the last of a run is full: with one label set per
-        // layer (full range, top layer) it holds tile_rows_of(kp, extra) rows,
-        // otherwise at least 4 * TILE_ROWS_MAX costs (the narrowest rows)
+        // layer (full range, top layer) it holds tile_rows_of(kp, extra, tf) rows,
+        // otherwise at least 4 * tile_rows_max(tf) costs (the narrowest rows)
         const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.nlev - 1;
         const int extra = c.p.storage == HDP_STORE_FP16 ? 4 : 0;
-        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp, extra) : (size_t)c.dim[l].N * kp / (4 * TILE_ROWS_MAX);
+        const int tf = layer_tile_floats(c, l);
+        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp, extra, tf)
+                           : (size_t)c.dim[l].N * kp / (4 * tile_rows_max(tf));
         tiles = std::max(tiles, t);
     }
     c.vol_elems = K;
@@ -423,7 +425,7 @@ extern "C" int hdp_sync(hdp_ctx* ctx)
 // ------------------------------------------------------------ tuning ---
 static const char* tuning_error(const hdp_tuning& t)
 {
-    if (t.agg_ctas_per_sm < 1 || t.agg_ctas_per_sm > 4) return "agg_ctas_per_sm out of 1..4";
+    if (t.agg_ctas_per_sm < 1 || t.agg_ctas_per_sm > 5) return "agg_ctas_per_sm out of 1..5";
     if (t.region_ctas_per_sm < 1 || t.region_ctas_per_sm > 4) return "region_ctas_per_sm out of 1..4";
     if (t.big_class_edges < 64 || t.big_class_edges > 4096) return "big_class_edges out of 64..4096";
     if (t.one_cta_nodes < 1024 || t.one_cta_nodes > (1 << 24)) return "one_cta_nodes out of 1024..1<<24";
@@ -493,7 +495,7 @@ extern "C" int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* 
                                    {32768, 131072, 524288, 0, 0},
                                    {262144, 1 << 20, 1 << 24, 0, 0},
                                    {1, 2, 4, 0, 0},
-                                   {2, 3, 4, 0, 0}};
+                                   {3, 4, 5, 0, 0}};
     for (int k = 0; k < 6 && rc == HDP_OK; ++k) {
         hdp_tuning keep = c.tune;
         for (int j = 0; j < 5 && cand[k][j] && rc == HDP_OK; ++j) {

@@ -278,13 +278,13 @@ __global__ void k_runstart(const uint32_t* keys_sorted, int N, int* runstart)
 
 // a tile starts at every (light level, width) run start and every
 // tile_rows(width) rows after it; tiles may split heavy paths
-__global__ void k_tile_flags(const uint32_t* keys_sorted, const int* runstart, int N, int extra, uint32_t* flag)
+__global__ void k_tile_flags(const uint32_t* keys_sorted, const int* runstart, int N, int extra, int tf, uint32_t* flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     uint32_t key = keys_sorted[i];
     int kp = 4 * (int)((key & 63u) + 1);
-    flag[i] = ((i - runstart[key]) % tile_rows_of(kp, extra)) == 0;
+    flag[i] = ((i - runstart[key]) % tile_rows_of(kp, extra, tf)) == 0;
 }
 
 __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uint32_t* keys_sorted, int N, int* tbeg,
@@ -366,7 +366,8 @@ void launch_order(Ctx& c, int l)
     // tiles
     k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
     k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
-    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0, c.ustart_flag);
+    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0,
+                                   layer_tile_floats(c, l), c.ustart_flag);
     scan_u32(c.ustart_flag, c.uid, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NUNITS), s);
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
