@@ -423,6 +423,63 @@ __device__ __forceinline__ int g_find(int* parent, int v)
     return v;
 }
 
+// Pending edges below this count per round hand the rest of a window to one warp.
+#define LW_SEQ_BELOW 16
+
+// Sequential Kruskal over the pending edges of a window (bitmap bm, window
+// order), run by one full warp: each lane finds the roots of one edge of a
+// group of 32, then the group is decided edge by edge with the roots and the
+// edge's weight broadcast by shuffles; every lane takes the same decision and
+// lane 0 writes it.  Roots are renamed in registers after each merge.
+template <int NE>
+__device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S, const uint32_t* bm, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    for (int g = 0; g < (cnt + 31) / 32; ++g) {
+        const uint32_t m = bm[g];
+        if (m == 0u) continue;
+        const int i = 32 * g + lane;
+        int x = -1, y = -1, e = 0, w = 0;
+        if (m >> lane & 1u) {
+            int p, q;
+            x = lw_find(S.parent, S.la[i]);
+            y = lw_find(S.parent, S.lb[i]);
+            decode(S.key[i], a.ebits, a.W, e, w, p, q);
+        }
+        for (uint32_t mm = m; mm; mm &= mm - 1u) {
+            const int k = __ffs(mm) - 1;
+            const int xk = __shfl_sync(0xffffffffu, x, k), yk = __shfl_sync(0xffffffffu, y, k);
+            const long long wk = __shfl_sync(0xffffffffu, w, k);
+            if (xk == yk) continue;                                   // a cycle
+            const uint32_t bx = S.best[xk], by = S.best[yk];
+            if (bx == 0u || by == 0u) continue;                       // a frozen tree
+            const long long sx = S.size[xk], sy = S.size[yk];
+            const long long ix = S.intw[xk], iy = S.intw[yk];
+            const bool fx = (wk - ix) * sx > a.kq, fy = (wk - iy) * sy > a.kq;
+            __syncwarp();
+            if (fx || fy) {   // criterion fails: that tree can never merge again
+                if (lane == 0) {
+                    if (fx) S.best[xk] = 0u;
+                    if (fy) S.best[yk] = 0u;
+                }
+                __syncwarp();
+                continue;
+            }
+            int big = xk, small = yk;
+            if (sx < sy) { big = yk; small = xk; }
+            if (lane == 0) {
+                S.parent[small] = big;
+                S.size[big] = (int)(sx + sy);
+                S.intw[big] = (int)wk;
+            }
+            if (lane == k) a.in_tree[e] = 1;
+            if (x == small) x = big;
+            if (y == small) y = big;
+            __syncwarp();
+        }
+    }
+}
+
 // One window [base, base + cnt) of the list `keys` (a run of the strict
 // order), resolved by the calling CTA of NT threads.  loc[] is INT_MAX on
 // entry and on exit.
@@ -506,6 +563,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     // least one edge and the loop ends within NE rounds
     for (int round = 0; round <= NE; ++round) {
         const uint32_t stamp = (uint32_t)(0xffff - round) << 13;
+        const unsigned live0 = live;
         int xa[LW_PER], xb[LW_PER];
 #pragma unroll
         for (int k = 0; k < LW_PER; ++k) {
@@ -514,6 +572,10 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
             const int i = t + k * NT;
             xa[k] = lw_find(S.parent, S.la[i]);
             xb[k] = lw_find(S.parent, S.lb[i]);
+            // the next round starts from today's roots (a hop or two), not
+            // from the end points' original local ids; only this thread reads them
+            S.la[i] = (uint16_t)xa[k];
+            S.lb[i] = (uint16_t)xb[k];
             if (xa[k] == xb[k] || S.best[xa[k]] == 0u || S.best[xb[k]] == 0u) {
                 live &= ~(1u << k);   // a cycle, or a frozen tree: rejected
             } else {
@@ -551,7 +613,32 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
             S.intw[big] = w;
             a.in_tree[e] = 1;
         }
-        if (!__syncthreads_or(live != 0)) {
+        const int lt = __syncthreads_count(live != 0);          // threads still holding edges
+        const int rt = __syncthreads_count(live != live0);      // threads that resolved one this round
+        if (lt == 0 || (round >= 1 && rt < LW_SEQ_BELOW)) {
+            if (lt != 0) {
+                // Few edges resolve per round: the rest wait in chains on a few
+                // big trees, and every further round would re-examine all of
+                // them.  Warp 0 finishes the window as the sequential algorithm
+                // does: the pending edges in window order, on the current trees.
+                // This is exact: every tree that a pending edge touches holds
+                // only merged edges of lower index (an edge merges only while
+                // it holds the reservation of both its trees), so the lowest
+                // pending edge always sees its sequential state.
+                uint32_t* bm = reinterpret_cast<uint32_t*>(S.rep);   // NE bits (rep is free after the gather)
+                for (int j = t; j < NE / 32; j += NT) bm[j] = 0u;
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < LW_PER; ++k)
+                    if (live >> k & 1u) {
+                        const int i = t + k * NT;
+                        atomicOr(bm + (i >> 5), 1u << (i & 31));
+                    }
+                live = 0;
+                __syncthreads();
+                if (t < 32) lw_sequential(a, S, bm, cnt);
+                __syncthreads();
+            }
             if (t == 0 && a.stats) {
                 atomicAdd(a.stats, round + 1);   // reservation rounds
                 atomicAdd(a.stats + 1, 1);       // windows
