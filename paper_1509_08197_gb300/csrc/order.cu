@@ -42,15 +42,24 @@ __global__ void k_arc_count(const uint8_t* adj, int N, uint32_t* cnt)
     if (v < N) cnt[v] = __popc((unsigned)adj[v]);
 }
 
+// Splitters of the list ranking: every tour head, and the arcs whose hashed
+// index (Fibonacci hashing) has its top lg bits zero, one arc in 2^lg on
+// average.  A head is never a successor, so "the next arc is a splitter" is
+// the hash test alone.
+__device__ __forceinline__ bool lr_pick(int a, int lg) { return ((uint32_t)a * 0x9E3779B1u) >> (32 - lg) == 0u; }
+
 // successor of arc (v -> u): leave u by the next existing direction after the
 // one pointing back to v (cyclic order up, left, right, down); the arc that
-// would re-enter the root's first arc ends the tour
+// would re-enter the root's first arc ends the tour.  Splitters take a ticket:
+// sid[a] is its number (-1 for other arcs) and spl lists them.
 __global__ void k_tour_succ(const uint8_t* adj, const uint32_t* aoff, const int* dtroot, int N, int W, int* succ,
-                            int* val)
+                            int* sid, int lg, int* nspl, int* spl)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
-    unsigned m = adj[v];
+    const unsigned mv = adj[v];
+    const bool root = dtroot[v] == v;
+    unsigned m = mv;
     while (m) {
         int k = __ffs(m) - 1;
         m &= m - 1;
@@ -64,8 +73,45 @@ __global__ void k_tour_succ(const uint8_t* adj, const uint32_t* aoff, const int*
         }
         bool end = dtroot[u] == u && d == first_dir(mu);
         succ[a] = end ? HDP_END : arc_index(aoff, adj, u, d);
-        val[a] = 1;
+        int id = -1;
+        if ((root && k == first_dir(mv)) || lr_pick(a, lg)) {
+            id = atomicAdd(nspl, 1);
+            spl[id] = a;
+        }
+        sid[a] = id;
     }
+}
+
+// Each splitter walks its segment (up to the next splitter or the tour end),
+// giving every arc its owner and its offset in the segment; the segments form
+// the reduced list (rs: next segment, rv: length) that pointer jumping ranks.
+__global__ void k_lr_walk(const int* __restrict__ succ, const int* __restrict__ sid, const int* __restrict__ spl,
+                          const int* nspl, int lg, int limit, int* owner, int* offs, int* rs, int* rv, DevStatus* st)
+{
+    const int n = *nspl;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        int cur = spl[j], off = 0, nxt = HDP_END;
+        for (int it = 0; it <= limit; ++it) {
+            owner[cur] = j;
+            offs[cur] = off++;
+            nxt = succ[cur];
+            if (nxt == HDP_END || lr_pick(nxt, lg)) break;
+            if (it == limit) {   // longer than the whole arc list: not a tour
+                dev_fail(st, DEV_BAD_INPUT, 50);
+                nxt = HDP_END;
+                break;
+            }
+            cur = nxt;
+        }
+        rs[j] = nxt == HDP_END ? HDP_END : sid[nxt];
+        rv[j] = off;
+    }
+}
+
+// distance of arc x to its tour end, from its segment's rank and its offset
+__device__ __forceinline__ int tour_rank(const int* R, const int* owner, const int* offs, int x)
+{
+    return R[owner[x]] - offs[x];
 }
 
 // Wyllie pointer jumping: val = number of arcs from the arc to its tour end.
@@ -101,7 +147,8 @@ __global__ void k_rank(int* succ, int* val, int* succ2, int* val2, const int* d_
 
 // parent = the neighbour whose arc into v comes first in the tour; subtree size
 // and tour positions of the entering (down) and leaving (up) arcs
-__global__ void k_orient(const uint8_t* adj, const uint32_t* aoff, const int* dtroot, const int* val, int N, int W,
+__global__ void k_orient(const uint8_t* adj, const uint32_t* aoff, const int* dtroot, const int* R, const int* owner, const int* offs, int N,
+                         int W,
                          int* par, int* pdir, int* sub, int* tpos_down, int* tpos_up, uint32_t* root_tl,
                          uint32_t* root_sz)
 {
@@ -109,7 +156,7 @@ __global__ void k_orient(const uint8_t* adj, const uint32_t* aoff, const int* dt
     if (v >= N) return;
     int r = dtroot[v];
     unsigned mr = adj[r];
-    int tl = mr ? val[arc_index(aoff, adj, r, first_dir(mr))] : 0;
+    int tl = mr ? tour_rank(R, owner, offs, arc_index(aoff, adj, r, first_dir(mr))) : 0;
     if (r == v) {
         par[v] = -1;
         pdir[v] = -1;
@@ -127,12 +174,13 @@ __global__ void k_orient(const uint8_t* adj, const uint32_t* aoff, const int* dt
         int u = nb_of(v, k, W);
         int up = arc_index(aoff, adj, v, k);          // v -> u
         int dn = arc_index(aoff, adj, u, 3 - k);      // u -> v
-        if (val[dn] > val[up]) {
+        const int vd = tour_rank(R, owner, offs, dn), vu = tour_rank(R, owner, offs, up);
+        if (vd > vu) {
             par[v] = u;
             pdir[v] = k;
-            sub[v] = (val[dn] - val[up] + 1) / 2;
-            tpos_down[v] = tl - val[dn];
-            tpos_up[v] = tl - val[up];
+            sub[v] = (vd - vu + 1) / 2;
+            tpos_down[v] = tl - vd;
+            tpos_up[v] = tl - vu;
         }
     }
 }
@@ -320,19 +368,29 @@ void launch_order(Ctx& c, int l)
     uint32_t* cnt = c.ka;
     k_arc_count<<<g, 256, 0, s>>>(c.adj, N, cnt);
     scan_u32(cnt, c.aoff, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NARCS), s);
-    k_tour_succ<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, N, d.W, c.succ, c.val);
+    // list ranking by splitters: about one arc in 2^lg starts a segment
+    const int lg = N >= (1 << 19) ? 5 : N >= (1 << 16) ? 4 : 3;
+    int* nspl = c.ints + IDX_TMP2;
+    cudaMemsetAsync(nspl, 0, sizeof(int), s);
+    int* sid = c.val;
+    int* spl = c.succ2;
+    int *owner = c.listA, *offs = c.listB, *rs = c.raA, *rv = c.rbA, *rs2 = c.raB, *rv2 = c.rbB;
+    k_tour_succ<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, N, d.W, c.succ, sid, lg, nspl, spl);
+    const int est = (2 * N >> lg) + 1024;   // expected segments, for the grid sizes only
+    k_lr_walk<<<min(cdiv(est, 128), c.num_sms * 16), 128, 0, s>>>(c.succ, sid, spl, nspl, lg, 2 * N, owner, offs,
+                                                                 rs, rv, c.st);
     cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), s);
     cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), s);
     {
-        int* a0 = c.succ; int* a1 = c.val; int* a2 = c.succ2; int* a3 = c.val2;
-        const int* nar = c.ints + IDX_NARCS;
+        int* a0 = rs; int* a1 = rv; int* a2 = rs2; int* a3 = rv2;
+        const int* nar = nspl;
         int* ctr = c.ints + IDX_CTR0;
         DevStatus* st = c.st;
         void* args[] = {&a0, &a1, &a2, &a3, &nar, &ctr, &st};
-        // about four arcs per thread per round, at most one wave
-        coop_launch((const void*)k_rank, 256, args, s, 0, nullptr, 0, cdiv(2 * N, 256 * 4));
+        // about four segments per thread per round, at most one wave
+        coop_launch((const void*)k_rank, 256, args, s, 0, nullptr, 0, cdiv(est, 256 * 4));
     }
-    k_orient<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, c.val, N, d.W, c.par, c.pdir, c.sub, c.tpos_down,
+    k_orient<<<g, 256, 0, s>>>(c.adj, c.aoff, c.dtroot, rv, owner, offs, N, d.W, c.par, c.pdir, c.sub, c.tpos_down,
                                c.tpos_up, c.ka, c.kb);
     k_children<<<g, 256, 0, s>>>(c.adj, c.pdir, c.sub, N, d.W, c.vals4, c.hdir);
     scan_u32(c.ka, c.tbase, dN, N, true, c.scan, nullptr, s);
