@@ -1,5 +1,7 @@
 // Shared device helpers of the HDP CUDA library (sm_103a).
 #pragma once
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +75,37 @@ __device__ __forceinline__ int uf_find(int* parent, int v)
         v = gp;
     }
     return v;
+}
+
+// A slot in a list or a count shared by the whole grid: one atomic per group
+// of converged lanes instead of one per lane (the counter is one address, so
+// per-lane atomics would serialise).
+__device__ __forceinline__ int grid_ticket(int* ctr)
+{
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(ctr, (int)g.size());
+    return g.shfl(base, 0) + (int)g.thread_rank();
+}
+
+// Add 1 to cnt[key]: one atomic per distinct key among the converged lanes.
+__device__ __forceinline__ void count_by_key(int* cnt, int key)
+{
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    cg::coalesced_group same = cg::labeled_partition(g, key);
+    if (same.thread_rank() == 0) atomicAdd(cnt + key, (int)same.size());
+}
+
+// atomicMin(arr + key, v), one atomic per distinct key among the converged lanes.
+__device__ __forceinline__ void min_by_key(int* arr, int key, int v)
+{
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    cg::coalesced_group same = cg::labeled_partition(g, key);
+    const int m = cg::reduce(same, v, cg::less<int>());
+    if (same.thread_rank() == 0) atomicMin(arr + key, m);
 }
 
 __device__ __forceinline__ int set_popc(const uint32_t* m)

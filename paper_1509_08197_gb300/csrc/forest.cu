@@ -80,7 +80,7 @@ __device__ __forceinline__ bool same_set(const ForestArgs& a, int p, int q)
 
 __device__ __forceinline__ void append(const ForestArgs& a, int which, int idx, int ra, int rb)
 {
-    int pos = atomicAdd(a.ctr + which, 1);
+    const int pos = grid_ticket(a.ctr + which);
     int* L = which ? a.listB : a.listA;
     int* RA = which ? a.raB : a.raA;
     int* RB = which ? a.rbB : a.rbA;
@@ -116,11 +116,11 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool rec
             if (ba == idx || bb == idx) a.in_tree[a.keys[idx] & ((1u << a.ebits) - 1u)] = 1;
             if (ba == idx && !(bb == idx && ra < rb)) {
                 __stcg(a.parent + ra, rb);
-                if (record_hooks) hk[atomicAdd(a.ctr + 2 + par, 1)] = ra;
+                if (record_hooks) hk[grid_ticket(a.ctr + 2 + par)] = ra;
             }
             if (bb == idx && !(ba == idx && rb < ra)) {
                 __stcg(a.parent + rb, ra);
-                if (record_hooks) hk[atomicAdd(a.ctr + 2 + par, 1)] = rb;
+                if (record_hooks) hk[grid_ticket(a.ctr + 2 + par)] = rb;
             }
         }
         if (tid == 0) {
@@ -147,8 +147,8 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool rec
             decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
             int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
             if (ra != rb) {
-                atomicMin(bnext + ra, idx);
-                atomicMin(bnext + rb, idx);
+                min_by_key(bnext, ra, idx);
+                min_by_key(bnext, rb, idx);
                 append(a, nxt, idx, ra, rb);
             }
         }
@@ -181,8 +181,8 @@ __global__ void k_boruvka(ForestArgs a)
         if (!same_set(a, p, q)) continue;
         int ra = uf_find(a.parent, p), rb = uf_find(a.parent, q);
         if (ra != rb) {
-            atomicMin(a.best + ra, idx);
-            atomicMin(a.best + rb, idx);
+            min_by_key(a.best, ra, idx);
+            min_by_key(a.best, rb, idx);
             append(a, 0, idx, ra, rb);
         }
     }
@@ -707,8 +707,8 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
                 long long sa = __ldcg(a.size + ra), sb = __ldcg(a.size + rb);
                 long long ia = __ldcg(a.intw + ra), ib = __ldcg(a.intw + rb);
                 if ((w - ia) * sa > a.kq || (w - ib) * sb > a.kq) continue;
-                atomicMin(best_of(a, par) + ra, idx);
-                atomicMin(best_of(a, par) + rb, idx);
+                min_by_key(best_of(a, par), ra, idx);
+                min_by_key(best_of(a, par), rb, idx);
                 append(a, cur, idx, ra, rb);
             }
             if (!grid_sync(a.st, gridDim.x)) return;
@@ -783,7 +783,7 @@ __global__ void k_region_count(ForestArgs a, const int* label, int* rcnt)
     if (idx >= *a.d_n) return;
     int e, w, p, q;
     decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
-    if (same_set(a, p, q)) atomicAdd(rcnt + label[p], 1);
+    if (same_set(a, p, q)) count_by_key(rcnt, label[p]);
 }
 
 // sort key of every same-set edge: its region label, with bit rbits set for
@@ -919,7 +919,7 @@ __global__ void k_flatten(int* parent, int* rootof, int* minid, int N)
     if (v >= N) return;
     int r = uf_find(parent, v);
     rootof[v] = r;
-    atomicMin(minid + r, v);
+    min_by_key(minid, r, v);
 }
 
 // dt_root = smallest pixel id of the tree; TreeIntv at union-find roots for

@@ -75,7 +75,7 @@ __global__ void k_tour_succ(const uint8_t* adj, const uint32_t* aoff, const int*
         succ[a] = end ? HDP_END : arc_index(aoff, adj, u, d);
         int id = -1;
         if ((root && k == first_dir(mv)) || lr_pick(a, lg)) {
-            id = atomicAdd(nspl, 1);
+            id = grid_ticket(nspl);
             spl[id] = a;
         }
         sid[a] = id;
