@@ -427,56 +427,68 @@ __device__ __forceinline__ int g_find(int* parent, int v)
 #define LW_SEQ_BELOW 16
 
 // Sequential Kruskal over the pending edges of a window (bitmap bm, window
-// order), run by one full warp: each lane finds the roots of one edge of a
-// group of 32, then the group is decided edge by edge with the roots and the
-// edge's weight broadcast by shuffles; every lane takes the same decision and
-// lane 0 writes it.  Roots are renamed in registers after each merge.
+// order), run by one full warp.  Each lane takes one edge of a group of 32 and
+// caches the state of its two trees (root, frozen, size, Int) in registers;
+// the group is then decided edge by edge from that edge's cache, broadcast by
+// shuffles, and every merge or freeze is applied to the caches of all lanes
+// (so no shared-memory round trip sits on the serial path).  Lane 0 writes
+// the same changes to shared memory for the next group.
 template <int NE>
 __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S, const uint32_t* bm, int cnt)
 {
+    static_assert(2 * NE <= (1 << 14), "local ids take 14 bits");
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (int g = 0; g < (cnt + 31) / 32; ++g) {
         const uint32_t m = bm[g];
         if (m == 0u) continue;
         const int i = 32 * g + lane;
-        int x = -1, y = -1, e = 0, w = 0;
+        int x = 0, y = 0, e = 0, w = 0, sx = 0, sy = 0, ix = 0, iy = 0;
+        bool zx = true, zy = true;   // frozen trees
         if (m >> lane & 1u) {
             int p, q;
             x = lw_find(S.parent, S.la[i]);
             y = lw_find(S.parent, S.lb[i]);
             decode(S.key[i], a.ebits, a.W, e, w, p, q);
+            zx = S.best[x] == 0u;
+            zy = S.best[y] == 0u;
+            sx = S.size[x]; sy = S.size[y];
+            ix = S.intw[x]; iy = S.intw[y];
         }
+        __syncwarp();   // every lane has read before lane 0 writes
         for (uint32_t mm = m; mm; mm &= mm - 1u) {
             const int k = __ffs(mm) - 1;
-            const int xk = __shfl_sync(0xffffffffu, x, k), yk = __shfl_sync(0xffffffffu, y, k);
-            const long long wk = __shfl_sync(0xffffffffu, w, k);
-            if (xk == yk) continue;                                   // a cycle
-            const uint32_t bx = S.best[xk], by = S.best[yk];
-            if (bx == 0u || by == 0u) continue;                       // a frozen tree
-            const long long sx = S.size[xk], sy = S.size[yk];
-            const long long ix = S.intw[xk], iy = S.intw[yk];
-            const bool fx = (wk - ix) * sx > a.kq, fy = (wk - iy) * sy > a.kq;
-            __syncwarp();
+            const int xy = __shfl_sync(FULL, x | y << 14 | (int)zx << 28 | (int)zy << 29, k);
+            const int xk = xy & 0x3fff, yk = (xy >> 14) & 0x3fff;
+            if (xk == yk || (xy >> 28) != 0) continue;   // a cycle, or a frozen tree
+            const long long wk = __shfl_sync(FULL, w, k);
+            const long long sxk = __shfl_sync(FULL, sx, k), syk = __shfl_sync(FULL, sy, k);
+            const long long ixk = __shfl_sync(FULL, ix, k), iyk = __shfl_sync(FULL, iy, k);
+            const bool fx = (wk - ixk) * sxk > a.kq, fy = (wk - iyk) * syk > a.kq;
             if (fx || fy) {   // criterion fails: that tree can never merge again
+                if (fx) { zx |= x == xk; zy |= y == xk; }
+                if (fy) { zx |= x == yk; zy |= y == yk; }
                 if (lane == 0) {
                     if (fx) S.best[xk] = 0u;
                     if (fy) S.best[yk] = 0u;
                 }
-                __syncwarp();
                 continue;
             }
             int big = xk, small = yk;
-            if (sx < sy) { big = yk; small = xk; }
+            if (sxk < syk) { big = yk; small = xk; }
+            const int ns = (int)(sxk + syk);
+            if (x == small) x = big;
+            if (y == small) y = big;
+            if (x == big) { sx = ns; ix = (int)wk; }
+            if (y == big) { sy = ns; iy = (int)wk; }
             if (lane == 0) {
                 S.parent[small] = big;
-                S.size[big] = (int)(sx + sy);
+                S.size[big] = ns;
                 S.intw[big] = (int)wk;
             }
             if (lane == k) a.in_tree[e] = 1;
-            if (x == small) x = big;
-            if (y == small) y = big;
-            __syncwarp();
         }
+        __syncwarp();   // lane 0's writes are seen by the next group's reads
     }
 }
 

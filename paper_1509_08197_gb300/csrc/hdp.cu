@@ -103,6 +103,8 @@ static void layout_buffers(Ctx& c)
         c.table[l] = carve<uint32_t>(c, 256 * HDP_WORDS);
         c.canon[l] = carve<int>(c, 256);
     }
+    c.pk0[0] = carve<uint2>(c, N0);
+    c.pk0[1] = carve<uint2>(c, N0);
     c.stage_l = carve<uint8_t>(c, 3 * (size_t)N0);
     c.stage_r = carve<uint8_t>(c, 3 * (size_t)N0);
     c.disp_host_stage = carve<int32_t>(c, N0);

@@ -58,6 +58,7 @@ struct Ctx {
     // images: int4 (R, G, B at scale 4^l, horizontal gradient g)
     int4* imL[HDP_MAX_LEVELS] = {};
     int4* imR[HDP_MAX_LEVELS] = {};
+    uint2* pk0[2] = {};   // layer 0 packed for the prior: R | G << 8 | B << 16, gradient
     uint8_t* stage_l = nullptr;   // upload buffers (tightly packed RGB)
     uint8_t* stage_r = nullptr;
     int32_t* disp[HDP_MAX_LEVELS] = {};

@@ -34,15 +34,22 @@ __global__ void k_pyr(const int4* __restrict__ src, int W, int H, int4* dst, int
 }
 
 // horizontal gradient of the grey sum, central difference, replicated border:
-// g = Sum(x+1) - Sum(x-1) with Sum = R + G + B (real gradient g / (6 * 4^l))
-__global__ void k_grad(int4* img, int W, int H)
+// g = Sum(x+1) - Sum(x-1) with Sum = R + G + B (real gradient g / (6 * 4^l)).
+// On layer 0 (channels are bytes) pk also receives the pixel packed for the
+// prior's byte-wise absolute differences.
+__global__ void k_grad(int4* img, int W, int H, uint2* pk)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * H) return;
     int x = i % W, y = i / W;
     int4 a = img[y * W + min(x + 1, W - 1)];
     int4 b = img[y * W + max(x - 1, 0)];
-    img[i].w = (a.x + a.y + a.z) - (b.x + b.y + b.z);
+    const int g = (a.x + a.y + a.z) - (b.x + b.y + b.z);
+    img[i].w = g;
+    if (pk) {
+        const int4 v = img[i];
+        pk[i] = make_uint2((uint32_t)v.x | (uint32_t)v.y << 8 | (uint32_t)v.z << 16, (uint32_t)g);
+    }
 }
 
 void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch)
@@ -50,7 +57,7 @@ void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch)
     const LayerDims& d = c.dim[0];
     int4* out = which ? c.imR[0] : c.imL[0];
     k_level0<<<cdiv(d.N, 256), 256, 0, c.s>>>(d_img, pitch, d.W, d.H, out);
-    k_grad<<<cdiv(d.N, 256), 256, 0, c.s>>>(out, d.W, d.H);
+    k_grad<<<cdiv(d.N, 256), 256, 0, c.s>>>(out, d.W, d.H, c.pk0[which]);
 }
 
 void launch_pyramid(Ctx& c)
@@ -62,7 +69,7 @@ void launch_pyramid(Ctx& c)
             int4* src = side ? c.imR[l - 1] : c.imL[l - 1];
             int4* dst = side ? c.imR[l] : c.imL[l];
             k_pyr<<<cdiv(b.N, 256), 256, 0, c.s>>>(src, a.W, a.H, dst, b.W, b.H);
-            k_grad<<<cdiv(b.N, 256), 256, 0, c.s>>>(dst, b.W, b.H);
+            k_grad<<<cdiv(b.N, 256), 256, 0, c.s>>>(dst, b.W, b.H, nullptr);
         }
     }
 }

@@ -21,20 +21,32 @@ __device__ __forceinline__ void warp_argmin(int& v, int& x)
 // full 5x5 square.  The centre's disparity is the argmin (lowest label on
 // ties) of the 5x5 box sum of the exact integer cost, for the left view; the
 // right view is checked at (cx - dL, cy) with the right-reference cost (box
-// columns clamped to the image).  Consistent centres vote for dL.
+// columns clamped to the image).  Consistent centres vote for dL.  Pixels are
+// int4 (R, G, B, gradient) on every layer, or on layer 0, whose channels are
+// bytes, uint2 (packed R, G, B; gradient) so that one byte-wise sum of
+// absolute differences gives the colour term.
 #define PRIOR_THREADS 256
 
-__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const int4* __restrict__ L, const int4* __restrict__ R, int W,
+__device__ __forceinline__ int cost_px(int4 a, int4 b, const CostK& k) { return cost_q(a, b, k); }
+__device__ __forceinline__ int cost_px(uint2 a, uint2 b, const CostK& k)
+{
+    const int sum = (int)__vsadu4(a.x, b.x);
+    const int dg = abs((int)a.y - (int)b.y);
+    return k.A * min(sum, k.Tc) + k.B * min(dg, k.Tg);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const P* __restrict__ L, const P* __restrict__ R, int W,
                                                          int H, int dl, CostK ck, unsigned long long* hist)
 {
     // the 25 pixels of the box in the reference view are the same for every
     // label: one copy per warp in shared memory
-    __shared__ int4 box[PRIOR_THREADS / 32][25];
+    __shared__ P box[PRIOR_THREADS / 32][25];
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int na = W / 5, nb = H / 5;
     if (wid >= na * nb) return;   // whole warps leave together
-    int4* sb = box[threadIdx.x >> 5];
+    P* sb = box[threadIdx.x >> 5];
     const int cx = 5 * (wid % na) + 2, cy = 5 * (wid / na) + 2;
     if (lane < 25) sb[lane] = L[(size_t)(cy + lane / 5 - 2) * W + cx + lane % 5 - 2];
     __syncwarp();
@@ -42,10 +54,10 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const int4* __restrict_
     for (int x = lane; x <= dl; x += 32) {
         int t = 0;
         for (int dy = -2; dy <= 2; ++dy) {
-            const int4* rowR = R + (size_t)(cy + dy) * W;
+            const P* rowR = R + (size_t)(cy + dy) * W;
             for (int dx = -2; dx <= 2; ++dx) {
                 int px = cx + dx;
-                t += cost_q(sb[(dy + 2) * 5 + dx + 2], rowR[max(px - x, 0)], ck);
+                t += cost_px(sb[(dy + 2) * 5 + dx + 2], rowR[max(px - x, 0)], ck);
             }
         }
         if (t < best) { best = t; bx = x; }
@@ -61,10 +73,10 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const int4* __restrict_
     for (int x = lane; x <= dl; x += 32) {
         int t = 0;
         for (int dy = -2; dy <= 2; ++dy) {
-            const int4* rowL = L + (size_t)(cy + dy) * W;
+            const P* rowL = L + (size_t)(cy + dy) * W;
             for (int dx = -2; dx <= 2; ++dx) {
                 int uu = min(max(u + dx, 0), W - 1);
-                t += cost_q(sb[(dy + 2) * 5 + dx + 2], rowL[min(uu + x, W - 1)], ck);
+                t += cost_px(sb[(dy + 2) * 5 + dx + 2], rowL[min(uu + x, W - 1)], ck);
             }
         }
         if (t < best) { best = t; bx = x; }
@@ -87,9 +99,15 @@ void launch_prior(Ctx& c, int l)
     int uniform = c.p.prior == HDP_PRIOR_UNIFORM;
     if (!uniform) {
         int centres = (d.W / 5) * (d.H / 5);
-        if (centres > 0)
-            k_prior<<<cdiv(centres * 32, PRIOR_THREADS), PRIOR_THREADS, 0, c.s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d,
-                                                                               cost_consts(c, l), hist);
+        if (centres > 0) {
+            const int blocks = cdiv(centres * 32, PRIOR_THREADS);
+            if (l == 0)
+                k_prior<uint2><<<blocks, PRIOR_THREADS, 0, c.s>>>(c.pk0[0], c.pk0[1], d.W, d.H, d.d,
+                                                                  cost_consts(c, l), hist);
+            else
+                k_prior<int4><<<blocks, PRIOR_THREADS, 0, c.s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d,
+                                                                 cost_consts(c, l), hist);
+        }
     }
     k_prior_finish<<<1, 256, 0, c.s>>>(hist, d.d, c.prior[l], uniform);
 }
