@@ -185,6 +185,7 @@ static void layout_buffers(Ctx& c)
     c.st = carve<DevStatus>(c, 1);
     c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
     c.tmp = carve<uint32_t>(c, c.tmp_words);
+    c.hist = carve<unsigned long long>(c, HDP_MAX_LEVELS * 256);
     // single-pass scans: the longest is over the 2N edge slots (radix
     // histograms are shorter)
     c.scan.max_tiles = scan_state_tiles((int)E2);
@@ -333,6 +334,9 @@ extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
     TRY_CUDA(cudaMemset(c.scan.ctr, 0, 2 * sizeof(unsigned int)));
     TRY_CUDA(cudaMemset(c.scan4.flags, 0, sizeof(unsigned int) * c.scan4.max_tiles));
     TRY_CUDA(cudaMemset(c.scan4.ctr, 0, 2 * sizeof(unsigned int)));
+    TRY_CUDA(cudaStreamCreateWithFlags(&c.s2, cudaStreamNonBlocking));
+    TRY_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) TRY_CUDA(cudaEventCreateWithFlags(&c.ev_side[l], cudaEventDisableTiming));
     *out = ctx;
     return HDP_OK;
 }
@@ -364,9 +368,26 @@ extern "C" int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_
     if (!ctx) return HDP_ERR_ARG;
     Ctx& c = ctx->c;
     if (!d_left || !d_right || pitch < 3 * c.p.width) return fail(ctx, HDP_ERR_ARG, "bad image pointers or pitch");
+    // side work of an earlier call that no level joined still reads the images
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        if (c.side_pending[l]) {
+            TRY_CUDA(cudaStreamWaitEvent(c.s, c.ev_side[l], 0));
+            c.side_pending[l] = 0;
+        }
     launch_level0(c, 0, d_left, pitch);
     launch_level0(c, 1, d_right, pitch);
     launch_pyramid(c);
+    if (c.s2 && c.p.mode == HDP_MODE_HDP && c.top > 0) {
+        // priors and tables of every predicted layer, beside layers top..1
+        TRY_CUDA(cudaEventRecord(c.ev_fork, c.s));
+        TRY_CUDA(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
+        for (int l = c.top - 1; l >= 0; --l) {
+            launch_prior(c, l, c.s2);
+            launch_table(c, l, c.s2);
+            TRY_CUDA(cudaEventRecord(c.ev_side[l], c.s2));
+            c.side_pending[l] = 1;
+        }
+    }
     mark(ctx, c.top, 0);
     mark(ctx, c.top, 1);
     build_layer_tree(ctx, c.top);
@@ -384,9 +405,15 @@ extern "C" int hdp_run_level(hdp_ctx* ctx, int level)
     const bool hdp = c.p.mode == HDP_MODE_HDP && level < c.top;
     if (hdp || c.tree_level != level) mark(ctx, level, 0);
     if (hdp) {
-        if (!ctx->prior_injected[level]) launch_prior(c, level);
+        if (c.side_pending[level]) {
+            TRY_CUDA(cudaStreamWaitEvent(c.s, c.ev_side[level], 0));
+            c.side_pending[level] = 0;
+            if (ctx->prior_injected[level]) launch_table(c, level, c.s);
+        } else {
+            if (!ctx->prior_injected[level]) launch_prior(c, level, c.s);
+            launch_table(c, level, c.s);
+        }
         ctx->prior_injected[level] = 0;
-        launch_table(c, level);
         launch_pixsets(c, level);
     }
     if (c.tree_level != level || hdp) {
@@ -417,6 +444,7 @@ extern "C" int hdp_sync(hdp_ctx* ctx)
     if (!ctx) return HDP_ERR_ARG;
     Ctx& c = ctx->c;
     TRY_CUDA(cudaStreamSynchronize(c.s));
+    if (c.s2) TRY_CUDA(cudaStreamSynchronize(c.s2));
     DevStatus st;
     TRY_CUDA(cudaMemcpy(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost));
     if (st.err == DEV_TIMEOUT) return fail(ctx, HDP_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(st.where) + ")");
@@ -559,6 +587,13 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
     if (ctx->c.gacc) cudaFree(ctx->c.gacc);
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->c.s2) {
+        cudaStreamSynchronize(ctx->c.s2);
+        cudaStreamDestroy(ctx->c.s2);
+    }
+    if (ctx->c.ev_fork) cudaEventDestroy(ctx->c.ev_fork);
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        if (ctx->c.ev_side[l]) cudaEventDestroy(ctx->c.ev_side[l]);
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     if (ctx->own_stream && ctx->c.s) cudaStreamDestroy(ctx->c.s);
@@ -766,6 +801,7 @@ extern "C" int hdp_set_stage(hdp_ctx* ctx, int level, int what, const void* h_sr
         return HDP_OK;
     }
     if (what == HDP_STAGE_PRIOR) {
+        if (c.s2) TRY_CUDA(cudaStreamSynchronize(c.s2));   // the side stream may still write this prior
         TRY_CUDA(cudaMemcpyAsync(c.prior[level], h_src, bytes, cudaMemcpyHostToDevice, c.s));
         TRY_CUDA(cudaStreamSynchronize(c.s));
         ctx->prior_injected[level] = 1;
@@ -813,6 +849,9 @@ extern "C" int hdp_graph_capture(hdp_ctx* ctx, const uint8_t* d_left, const uint
     if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
     for (int l = 0; l < HDP_MAX_LEVELS; ++l)
         for (int k = 0; k < 6; ++k) ctx->ev_used[l][k] = 0;
+    // a capture cannot wait on work recorded before it
+    if (c.s2) TRY_CUDA(cudaStreamSynchronize(c.s2));
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l) c.side_pending[l] = 0;
     TRY_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
     int rc = hdp_build_trees(ctx, d_left, d_right, pitch);
     if (!rc) rc = hdp_match(ctx, d_out);
@@ -1011,6 +1050,10 @@ extern "C" int hdp_batch_graph_capture(hdp_ctx** ctxs, int n, const uint8_t* con
         if (!ctxs[i]) return HDP_ERR_ARG;
         if (!ctxs[i]->fork) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->fork, cudaEventDisableTiming));
         if (!ctxs[i]->join) TRY_CUDA(cudaEventCreateWithFlags(&ctxs[i]->join, cudaEventDisableTiming));
+    }
+    for (int i = 0; i < n; ++i) {
+        if (ctxs[i]->c.s2) TRY_CUDA(cudaStreamSynchronize(ctxs[i]->c.s2));
+        for (int l = 0; l < HDP_MAX_LEVELS; ++l) ctxs[i]->c.side_pending[l] = 0;
     }
     TRY_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeGlobal));
     int rc = hdp_match_batch(ctxs, n, d_left, d_right, pitch, d_out);

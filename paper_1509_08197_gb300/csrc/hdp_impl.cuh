@@ -45,6 +45,13 @@ struct Ctx {
     hdp_params p;
     hdp_tuning tune = {5, 4, 2048, 131072, 4096, 1 << 20};
     cudaStream_t s = nullptr;
+    // side stream: the priors and interval tables of the predicted layers need
+    // only that layer's images, so they run beside the coarser layers' work
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_side[HDP_MAX_LEVELS] = {};
+    int side_pending[HDP_MAX_LEVELS] = {};
+    unsigned long long* hist = nullptr;   // [HDP_MAX_LEVELS][256] prior histograms
     int nlev = 0;     // layers processed
     int top = 0;      // index of the top layer
     LayerDims dim[HDP_MAX_LEVELS];
@@ -163,8 +170,8 @@ void launch_pyramid(Ctx& c);
 void launch_edges(Ctx& c, int l, int hdp);
 
 // range.cu
-void launch_prior(Ctx& c, int l);
-void launch_table(Ctx& c, int l);
+void launch_prior(Ctx& c, int l, cudaStream_t s);
+void launch_table(Ctx& c, int l, cudaStream_t s);
 void launch_pixsets(Ctx& c, int l);
 
 // forest.cu

@@ -91,25 +91,25 @@ __global__ void k_prior_finish(const unsigned long long* hist, int dl, long long
     if (j <= dl) prior[j] = uniform ? 1 : (long long)hist[j] + 1;   // Laplace count
 }
 
-void launch_prior(Ctx& c, int l)
+void launch_prior(Ctx& c, int l, cudaStream_t s)
 {
     const LayerDims& d = c.dim[l];
-    unsigned long long* hist = (unsigned long long*)c.tmp;
-    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 256, c.s);
+    unsigned long long* hist = c.hist + (size_t)l * 256;
+    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 256, s);
     int uniform = c.p.prior == HDP_PRIOR_UNIFORM;
     if (!uniform) {
         int centres = (d.W / 5) * (d.H / 5);
         if (centres > 0) {
             const int blocks = cdiv(centres * 32, PRIOR_THREADS);
             if (l == 0)
-                k_prior<uint2><<<blocks, PRIOR_THREADS, 0, c.s>>>(c.pk0[0], c.pk0[1], d.W, d.H, d.d,
+                k_prior<uint2><<<blocks, PRIOR_THREADS, 0, s>>>(c.pk0[0], c.pk0[1], d.W, d.H, d.d,
                                                                   cost_consts(c, l), hist);
             else
-                k_prior<int4><<<blocks, PRIOR_THREADS, 0, c.s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d,
+                k_prior<int4><<<blocks, PRIOR_THREADS, 0, s>>>(c.imL[l], c.imR[l], d.W, d.H, d.d,
                                                                  cost_consts(c, l), hist);
         }
     }
-    k_prior_finish<<<1, 256, 0, c.s>>>(hist, d.d, c.prior[l], uniform);
+    k_prior_finish<<<1, 256, 0, s>>>(hist, d.d, c.prior[l], uniform);
 }
 
 // GMM_l(o) = sum_k pi_k N(o | mu_k, sd_k), evaluated term by term without
@@ -203,13 +203,13 @@ __global__ void k_canon(const uint32_t* masks, int dup, int* canon)
     canon[i] = c;
 }
 
-void launch_table(Ctx& c, int l)
+void launch_table(Ctx& c, int l, cudaStream_t s)
 {
     const LayerDims& d = c.dim[l];
     const LayerDims& u = c.dim[l + 1];
     double delta = c.p.delta0 * (double)(1 << l);
-    k_table<<<u.d + 1, 256, 0, c.s>>>(c.prior[l], d.d, u.d, c.gmm, c.gmm_k, l, delta, c.table[l]);
-    k_canon<<<cdiv(u.d + 1, 128), 128, 0, c.s>>>(c.table[l], u.d, c.canon[l]);
+    k_table<<<u.d + 1, 256, 0, s>>>(c.prior[l], d.d, u.d, c.gmm, c.gmm_k, l, delta, c.table[l]);
+    k_canon<<<cdiv(u.d + 1, 128), 128, 0, s>>>(c.table[l], u.d, c.canon[l]);
 }
 
 // PixelIntv(p) = row D_{l+1}(floor(x/2), floor(y/2)) of the table.
