@@ -138,6 +138,7 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool rec
                 const int R = uf_find(a.parent, r);
                 atomicAdd(a.size + R, __ldcg(a.size + r));
                 __stcg(a.intw + R, wclass);
+                __stcg(a.parent + r, R);   // shortcut: hook chains would lengthen every later find
             }
         }
         for (int j = tid; j < m; j += nth) {
@@ -423,6 +424,53 @@ __device__ __forceinline__ int g_find(int* parent, int v)
     return v;
 }
 
+// Roots of the end points of up to M edges (a[k], b[k] for the edges in
+// `live`), walked in lockstep with path halving: one hop of every unfinished
+// chain per step, so the chains' load latencies overlap.
+template <bool L2, int M>
+__device__ __forceinline__ void g_find_many(int* parent, int* a, int* b, unsigned live)
+{
+    int v[2 * M];
+    unsigned pend = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+        if (live >> k & 1u) pend |= 3u << (2 * k);
+    }
+    for (int it = 0; pend && it < (1 << 26); ++it) {
+        int pv[2 * M], gv[2 * M];
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j)   // parents of every unfinished chain, loads in flight together
+            pv[j] = (pend >> j & 1u) ? (L2 ? __ldcg(parent + v[j]) : parent[v[j]]) : v[j];
+        unsigned hop = 0;
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j)
+            if (pv[j] != v[j]) hop |= 1u << j;
+        pend &= hop;
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j)   // grandparents
+            gv[j] = (hop >> j & 1u) ? (L2 ? __ldcg(parent + pv[j]) : parent[pv[j]]) : 0;
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j) {
+            if (!(hop >> j & 1u)) continue;
+            if (gv[j] == pv[j]) {
+                v[j] = pv[j];
+                pend &= ~(1u << j);
+            } else {
+                if (L2) __stcg(parent + v[j], gv[j]);
+                else parent[v[j]] = gv[j];
+                v[j] = gv[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        a[k] = v[2 * k];
+        b[k] = v[2 * k + 1];
+    }
+}
+
 // Pending edges below this count per round hand the rest of a window to one warp.
 #define LW_SEQ_BELOW 16
 
@@ -506,28 +554,46 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     }
     __syncthreads();
     // gather: current global roots of both end points; one representative
-    // end point per distinct root (smallest code) allocates its local id
+    // end point per distinct root (smallest code) allocates its local id.
+    // The loads of a thread's edges are issued together (keys, then sets,
+    // then the finds in lockstep), so their latencies overlap.
     int ra[LW_PER], rb[LW_PER];
+    uint32_t kk[LW_PER];
     unsigned live = 0;
     int wl = INT_MAX;
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         const int i = t + k * NT;
         ra[k] = rb[k] = -1;
-        if (i >= cnt) continue;
-        const uint32_t key = keys[base + i];
+        if (i < cnt) {
+            kk[k] = keys[base + i];
+            live |= 1u << k;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        if (!(live >> k & 1u)) continue;
         int e, w, p, q;
-        decode(key, a.ebits, a.W, e, w, p, q);
+        decode(kk[k], a.ebits, a.W, e, w, p, q);
         wl = min(wl, w);
-        if (!same_set(a, p, q)) continue;
-        const int x = g_find<L2>(a.parent, p), y = g_find<L2>(a.parent, q);
-        if (x == y) continue;
-        ra[k] = x;
-        rb[k] = y;
-        S.key[i] = key;
-        atomicMin(loc + x, 2 * i);
-        atomicMin(loc + y, 2 * i + 1);
-        live |= 1u << k;
+        ra[k] = p;
+        rb[k] = q;
+    }
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k)
+        if ((live >> k & 1u) && !same_set(a, ra[k], rb[k])) live &= ~(1u << k);
+    g_find_many<L2, LW_PER>(a.parent, ra, rb, live);
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        if (!(live >> k & 1u)) continue;
+        const int i = t + k * NT;
+        if (ra[k] == rb[k]) {
+            live &= ~(1u << k);
+            continue;
+        }
+        S.key[i] = kk[k];
+        atomicMin(loc + ra[k], 2 * i);
+        atomicMin(loc + rb[k], 2 * i + 1);
     }
     if (wl != INT_MAX) atomicMin(&S.wmin, wl);
     __syncthreads();
