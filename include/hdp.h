@@ -110,7 +110,7 @@ typedef struct {
  *                          (at most one wave), 512..1<<20 [4096]
  *   region_max_nodes       HDP layers with fewer nodes run the first pass
  *                          region by region (bigger ones by weight class),
- *                          0..1<<30 [1<<20]
+ *                          0..1<<30 [1<<24]
  */
 typedef struct {
     int agg_ctas_per_sm;

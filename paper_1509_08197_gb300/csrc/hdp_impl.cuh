@@ -43,7 +43,7 @@ struct CostK {
 
 struct Ctx {
     hdp_params p;
-    hdp_tuning tune = {5, 4, 2048, 131072, 4096, 1 << 20};
+    hdp_tuning tune = {5, 4, 2048, 131072, 4096, 1 << 24};
     cudaStream_t s = nullptr;
     // side stream: the priors and interval tables of the predicted layers need
     // only that layer's images, so they run beside the coarser layers' work
