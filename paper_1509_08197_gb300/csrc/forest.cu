@@ -888,11 +888,11 @@ __global__ void k_region_keys(ForestArgs a, const int* label, const int* rcnt, i
         rk[idx] = k;
         rv[idx] = key;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, valid);
-    const unsigned ms = __ballot_sync(0xffffffffu, small);
-    if ((threadIdx.x & 31) == 0) {
-        if (m) atomicAdd(nvalid, __popc(m));
-        if (ms) atomicAdd(nsmall, __popc(ms));
+    // one atomic per block on each grid-wide count
+    const int cv = __syncthreads_count(valid), cs = __syncthreads_count(small);
+    if (threadIdx.x == 0) {
+        if (cv) atomicAdd(nvalid, cv);
+        if (cs) atomicAdd(nsmall, cs);
     }
 }
 
@@ -911,7 +911,7 @@ __global__ void k_region_buckets(ForestArgs a, const int* d_nvalid, const int* d
     const int b = s / RG_SMALL;
     atomicMin(wb_lo + b, s);
     atomicMax(wb_hi + b, e);
-    atomicAdd(nsmall_regions, 1);
+    grid_ticket(nsmall_regions);   // a count: one atomic per group of lanes
 }
 
 // Work items: every big region (its windows in order, on one CTA), then one

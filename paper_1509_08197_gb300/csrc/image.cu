@@ -121,8 +121,8 @@ __global__ void k_edges(const int4* __restrict__ img, int W, int H, int ebits, c
         }
     }
     if (e < 2 * N) keys[e] = keep ? key : 0xffffffffu;
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, __popc(m));
+    const int kept = __syncthreads_count(keep);   // one atomic per block on the grid-wide count
+    if (threadIdx.x == 0 && kept) atomicAdd(count, kept);
 }
 
 void launch_edges(Ctx& c, int l, int hdp)
