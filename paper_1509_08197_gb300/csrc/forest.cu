@@ -819,8 +819,10 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
 typedef LocalWinT<RG_EDGES> RegionWin;
 
 // Connected same-set regions: lock-free union-find over the same-set edges,
-// the larger root hooked under the smaller (so a region's root is its
-// smallest pixel); parent pointers only decrease, so shortcuts are safe.
+// the larger root hooked under the smaller by atomicMin (so a region's root
+// is its smallest pixel); parent pointers only decrease, so shortcuts are
+// safe, and a lowered parent that cut a node from its old tree is followed by
+// joining that old tree too.
 __device__ __forceinline__ int cc_find(int* par, int v)
 {
     for (int it = 0; it < (1 << 26); ++it) {
@@ -837,18 +839,24 @@ __device__ __forceinline__ int cc_find(int* par, int v)
 __global__ void k_cc_hook(ForestArgs a, int* par)
 {
     if (a.risky && __ldcg(a.risky)) return;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= *a.d_n) return;
-    int e, w, p, q;
-    decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
+    // edge ids in image order (the regions do not depend on the order), so
+    // that neighbouring threads share parent cache lines
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * a.N) return;
+    const int p = e >> 1;
+    if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) return;   // no neighbour there
+    const int q = (e & 1) ? p + a.W : p + 1;
     if (!same_set(a, p, q)) return;
-    int u = p, v = q;
+    int u = cc_find(par, p), v = cc_find(par, q);
     for (int it = 0; it < (1 << 20); ++it) {
-        u = cc_find(par, u);
-        v = cc_find(par, v);
         if (u == v) return;
         if (u < v) { const int t = u; u = v; v = t; }
-        if (atomicCAS(par + u, u, v) == u) return;   // else u was hooked meanwhile: retry
+        // lower u's parent to v: if u was a root, it now hangs under v; else
+        // its old parent (smaller than u) still has to be joined with v
+        const int old = atomicMin(par + u, v);
+        if (old == u) return;
+        u = cc_find(par, old);
+        v = cc_find(par, v);
     }
     dev_fail(a.st, DEV_TIMEOUT, 41);
 }
@@ -857,10 +865,11 @@ __global__ void k_cc_hook(ForestArgs a, int* par)
 __global__ void k_region_count(ForestArgs a, const int* label, int* rcnt)
 {
     if (a.risky && __ldcg(a.risky)) return;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= *a.d_n) return;
-    int e, w, p, q;
-    decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // image order: neighbouring lanes share a region
+    if (e >= 2 * a.N) return;
+    const int p = e >> 1;
+    if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) return;
+    const int q = (e & 1) ? p + a.W : p + 1;
     if (same_set(a, p, q)) count_by_key(rcnt, label[p]);
 }
 

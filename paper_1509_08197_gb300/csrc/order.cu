@@ -345,8 +345,8 @@ __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uin
     tbeg[t] = i;
     int lv = (int)(keys_sorted[i] >> 6);
     if (lv >= MAX_LIGHT_LEVELS) return;
-    atomicMin(lvl_first + lv, t);
-    atomicAdd(lvl_count + lv, 1);
+    min_by_key(lvl_first, lv, t);   // tiles come sorted by level: one atomic per level and warp
+    count_by_key(lvl_count, lv);
 }
 
 __global__ void k_fill_int(int* p, int n, int v)
