@@ -82,6 +82,81 @@ size_t radix_tmp_words(int n_max)
 
 __global__ void k_set_int(int* out, int v) { out[0] = v; }
 
+// Decoupled look-back by one full warp: the 32 predecessors j0, j0-1, ...
+// are read at once; the nearest inclusive prefix ends the walk, a window of
+// aggregates only moves it back by 32.  Returns the exclusive prefix of
+// `tile` on every lane.  Waits are bounded (DEV_TIMEOUT).
+__device__ __forceinline__ uint32_t lookback_u32(const unsigned long long* stp, int tile, DevStatus* st, int where)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t pre = 0;
+    unsigned it = 0;
+    for (int j0 = tile - 1; j0 >= 0;) {
+        const int j = j0 - lane;
+        const unsigned long long w = j >= 0 ? *(volatile const unsigned long long*)(stp + j) : (2ull << 32);
+        const uint32_t f = (uint32_t)(w >> 32);
+        const unsigned incl = __ballot_sync(FULL, f == 2u), none = __ballot_sync(FULL, f == 0u);
+        const int k = incl ? __ffs(incl) - 1 : 31;
+        const unsigned need = k == 31 ? FULL : (2u << k) - 1u;   // lanes 0..k
+        if (none & need) {
+            if (++it > HDP_SPIN_LIMIT || dev_err(st)) {
+                if (lane == 0) dev_fail(st, DEV_TIMEOUT, where);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        uint32_t v = (need >> lane & 1u) ? (uint32_t)w : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        pre += v;
+        if (incl) break;
+        j0 -= 32;
+    }
+    return pre;
+}
+
+__device__ __forceinline__ I4 lookback_i4(const ScanStateI4& ss, int tile, int where)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    I4 pre = I4{0, 0, 0, 0};
+    unsigned it = 0;
+    for (int j0 = tile - 1; j0 >= 0;) {
+        const int j = j0 - lane;
+        const unsigned f = j >= 0 ? *(volatile const unsigned*)(ss.flags + j) : 2u;
+        const unsigned incl = __ballot_sync(FULL, f == 2u), none = __ballot_sync(FULL, f == 0u);
+        const int k = incl ? __ffs(incl) - 1 : 31;
+        const unsigned need = k == 31 ? FULL : (2u << k) - 1u;
+        if (none & need) {
+            if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
+                if (lane == 0) dev_fail(ss.st, DEV_TIMEOUT, where);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        __threadfence();   // the value was written before its flag
+        I4 v = I4{0, 0, 0, 0};
+        if ((need >> lane & 1u) && j >= 0) {
+            const I4* src = f == 2u ? ss.inclv : ss.aggv;
+            v = I4{__ldcg(&src[j].x), __ldcg(&src[j].y), __ldcg(&src[j].z), __ldcg(&src[j].w)};
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_xor_sync(FULL, v.x, o);
+            v.y += __shfl_xor_sync(FULL, v.y, o);
+            v.z += __shfl_xor_sync(FULL, v.z, o);
+            v.w += __shfl_xor_sync(FULL, v.w, o);
+        }
+        pre = pre + v;
+        if (incl) break;
+        j0 -= 32;
+    }
+    return pre;
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, uint32_t* out, const int* d_n,
                                                             int exclusive, ScanState ss, uint32_t* total)
 {
@@ -106,34 +181,20 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
             v[i] = x[i];
         }
         const uint32_t tot = block_scan_excl<uint32_t, OpSum>(v, 0u, OpSum(), smem);
-        if (t == 0) {
+        if (t < 32) {
             unsigned long long* stp = ss.state;
             uint32_t pre = 0;
             if (tile == 0) {
-                atomicExch(stp, (2ull << 32) | tot);
+                if (t == 0) atomicExch(stp, (2ull << 32) | tot);
             } else {
-                atomicExch(stp + tile, (1ull << 32) | tot);
-                // walk back to the nearest inclusive prefix
-                unsigned it = 0;
-                for (int j = tile - 1; j >= 0;) {
-                    const unsigned long long w = *(volatile unsigned long long*)(stp + j);
-                    const uint32_t f = (uint32_t)(w >> 32);
-                    if (f == 0u) {
-                        if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
-                            dev_fail(ss.st, DEV_TIMEOUT, 60);
-                            break;
-                        }
-                        __nanosleep(32);
-                        continue;
-                    }
-                    pre += (uint32_t)w;
-                    if (f == 2u) break;
-                    --j;
-                }
-                atomicExch(stp + tile, (2ull << 32) | (uint32_t)(pre + tot));
+                if (t == 0) atomicExch(stp + tile, (1ull << 32) | tot);
+                pre = lookback_u32(stp, tile, ss.st, 60);
+                if (t == 0) atomicExch(stp + tile, (2ull << 32) | (uint32_t)(pre + tot));
             }
-            s_pre = pre;
-            if (total && tile == nt - 1) *total = pre + tot;
+            if (t == 0) {
+                s_pre = pre;
+                if (total && tile == nt - 1) *total = pre + tot;
+            }
         }
         __syncthreads();
         const uint32_t pre = s_pre;
@@ -188,35 +249,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_i4(const I4* in, I4* out
             v[i] = x[i];
         }
         const I4 tot = block_scan_excl<I4, OpSum>(v, z, OpSum(), smem);
-        if (t == 0) {
+        if (t < 32) {
             I4 pre = z;
             if (tile > 0) {
-                ss.aggv[tile] = tot;
-                __threadfence();
-                atomicExch(ss.flags + tile, 1u);
-                unsigned it = 0;
-                for (int j = tile - 1; j >= 0;) {
-                    const unsigned f = *(volatile unsigned*)(ss.flags + j);
-                    if (f == 0u) {
-                        if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
-                            dev_fail(ss.st, DEV_TIMEOUT, 63);
-                            break;
-                        }
-                        __nanosleep(32);
-                        continue;
-                    }
+                if (t == 0) {
+                    ss.aggv[tile] = tot;
                     __threadfence();
-                    const I4* src = f == 2u ? ss.inclv : ss.aggv;
-                    const I4 w = I4{__ldcg(&src[j].x), __ldcg(&src[j].y), __ldcg(&src[j].z), __ldcg(&src[j].w)};
-                    pre = w + pre;
-                    if (f == 2u) break;
-                    --j;
+                    atomicExch(ss.flags + tile, 1u);
                 }
+                pre = lookback_i4(ss, tile, 63);
             }
-            ss.inclv[tile] = pre + tot;
-            __threadfence();
-            atomicExch(ss.flags + tile, 2u);
-            s_pre = pre;
+            if (t == 0) {
+                ss.inclv[tile] = pre + tot;
+                __threadfence();
+                atomicExch(ss.flags + tile, 2u);
+                s_pre = pre;
+            }
         }
         __syncthreads();
         const I4 pre = s_pre;
