@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
                                                             int exclusive, ScanState ss, uint32_t* total)
 {
     __shared__ uint32_t smem[33];
+    __shared__ uint32_t stage[SCAN_TILE + SCAN_TILE / 32];
     __shared__ int s_tile;
     __shared__ uint32_t s_pre;
     __shared__ int s_last;
@@ -174,10 +175,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
     if (tile < nt && tile < ss.max_tiles) {
         const long long base = (long long)tile * SCAN_TILE;
         uint32_t v[SCAN_IPT], x[SCAN_IPT];
+        // coalesced loads, transposed through shared memory (padded: no bank
+        // conflicts) so that each thread scans SCAN_IPT consecutive items
 #pragma unroll
         for (int i = 0; i < SCAN_IPT; ++i) {
-            const long long idx = base + (long long)t * SCAN_IPT + i;
-            x[i] = idx < n ? in[idx] : 0u;
+            const int e = i * SCAN_THREADS + t;
+            stage[e + (e >> 5)] = base + e < n ? in[base + e] : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const int e = t * SCAN_IPT + i;
+            x[i] = stage[e + (e >> 5)];
             v[i] = x[i];
         }
         const uint32_t tot = block_scan_excl<uint32_t, OpSum>(v, 0u, OpSum(), smem);
@@ -200,8 +209,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
         const uint32_t pre = s_pre;
 #pragma unroll
         for (int i = 0; i < SCAN_IPT; ++i) {
-            const long long idx = base + (long long)t * SCAN_IPT + i;
-            if (idx < n) out[idx] = pre + v[i] + (exclusive ? 0u : x[i]);
+            const int e = t * SCAN_IPT + i;
+            stage[e + (e >> 5)] = pre + v[i] + (exclusive ? 0u : x[i]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const int e = i * SCAN_THREADS + t;
+            if (base + e < n) out[base + e] = stage[e + (e >> 5)];
         }
     } else if (t == 0 && total && n == 0 && tile == 0) {
         *total = 0;
@@ -228,6 +243,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_u32(const uint32_t* in, 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_i4(const I4* in, I4* out, const int* d_n, ScanStateI4 ss)
 {
     __shared__ I4 smem[33];
+    __shared__ I4 stage4[SCAN_TILE + SCAN_TILE / 8];
     __shared__ int s_tile;
     __shared__ I4 s_pre;
     __shared__ int s_last;
@@ -242,10 +258,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_i4(const I4* in, I4* out
         const long long base = (long long)tile * SCAN_TILE;
         const I4 z = I4{0, 0, 0, 0};
         I4 v[SCAN_IPT], x[SCAN_IPT];
+        // coalesced loads, transposed through shared memory (one pad per 8
+        // items: no bank conflicts for 16-byte items)
 #pragma unroll
         for (int i = 0; i < SCAN_IPT; ++i) {
-            const long long idx = base + (long long)t * SCAN_IPT + i;
-            x[i] = idx < n ? in[idx] : z;
+            const int e = i * SCAN_THREADS + t;
+            stage4[e + (e >> 3)] = base + e < n ? in[base + e] : z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const int e = t * SCAN_IPT + i;
+            x[i] = stage4[e + (e >> 3)];
             v[i] = x[i];
         }
         const I4 tot = block_scan_excl<I4, OpSum>(v, z, OpSum(), smem);
@@ -270,8 +294,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan1_i4(const I4* in, I4* out
         const I4 pre = s_pre;
 #pragma unroll
         for (int i = 0; i < SCAN_IPT; ++i) {
-            const long long idx = base + (long long)t * SCAN_IPT + i;
-            if (idx < n) out[idx] = pre + v[i] + x[i];   // inclusive
+            const int e = t * SCAN_IPT + i;
+            stage4[e + (e >> 3)] = pre + v[i] + x[i];   // inclusive
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SCAN_IPT; ++i) {
+            const int e = i * SCAN_THREADS + t;
+            if (base + e < n) out[base + e] = stage4[e + (e >> 3)];
         }
     }
     // the last block to finish clears the flags and the counters
