@@ -19,6 +19,7 @@ struct hdp_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool own_stream = false;   // created by hdp_create_own_stream, destroyed with the context
+    int use_side = 1;          // 0 inside a batch: the other pairs already fill the GPU
 };
 
 static void mark(hdp_ctx* ctx, int l, int k)
@@ -377,7 +378,7 @@ extern "C" int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_
     launch_level0(c, 0, d_left, pitch);
     launch_level0(c, 1, d_right, pitch);
     launch_pyramid(c);
-    if (c.s2 && c.p.mode == HDP_MODE_HDP && c.top > 0) {
+    if (c.s2 && ctx->use_side && c.p.mode == HDP_MODE_HDP && c.top > 0) {
         // priors and tables of every predicted layer, beside layers top..1
         TRY_CUDA(cudaEventRecord(c.ev_fork, c.s));
         TRY_CUDA(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
@@ -1023,9 +1024,13 @@ extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_le
     }
     TRY_CUDA(cudaEventRecord(ctx->fork, ctx->c.s));
     for (int i = 1; i < n; ++i) TRY_CUDA(cudaStreamWaitEvent(ctxs[i]->c.s, ctx->fork, 0));
+    // no side streams inside a batch: the pairs already fill the GPU, and twice
+    // the concurrent branches made the batch graph 1.6x slower
     for (int i = 0; i < n; ++i) {
+        ctxs[i]->use_side = 0;
         int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
         if (!rc) rc = hdp_match(ctxs[i], d_out[i]);
+        ctxs[i]->use_side = 1;
         if (rc) return rc;
     }
     for (int i = 1; i < n; ++i) {
