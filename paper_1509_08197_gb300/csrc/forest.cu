@@ -389,7 +389,8 @@ struct LocalWinT {
     int glob[2 * NE];
     uint16_t rep[2 * NE];   // representative end point code -> local id
     int nroots;
-    int wmin;               // smallest weight in the window
+    int wmin, wmax;         // smallest and largest weight in the window
+    int nhook;              // trees hooked in a Boruvka round
 };
 typedef LocalWinT<LW_EDGES> LocalWin;
 
@@ -475,25 +476,37 @@ __device__ __forceinline__ void g_find_many(int* parent, int* a, int* b, unsigne
 #define LW_SEQ_BELOW 16
 
 // Sequential Kruskal over the pending edges of a window (bitmap bm, window
-// order), run by one full warp.  Each lane takes one edge of a group of 32 and
-// caches the state of its two trees (root, frozen, size, Int) in registers;
-// the group is then decided edge by edge from that edge's cache, broadcast by
-// shuffles, and every merge or freeze is applied to the caches of all lanes
-// (so no shared-memory round trip sits on the serial path).  Lane 0 writes
-// the same changes to shared memory for the next group.
+// order), run by one full warp.  The pending edges are first listed densely
+// (after the bitmap, in the same scratch), so that every group of 32 is full.
+// Each lane takes one edge of a group and caches the state of its two trees
+// in registers: root, frozen flag, size, Int, and whether each side's
+// criterion passes at this edge's weight.  The group is then decided edge by
+// edge from that edge's cache, broadcast by shuffles, and every merge or
+// freeze is applied to the caches of all lanes (so no shared-memory round
+// trip sits on the serial path).  Lane 0 writes the same changes to shared
+// memory for the next group.
 template <int NE>
 __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S, const uint32_t* bm, int cnt)
 {
     static_assert(2 * NE <= (1 << 14), "local ids take 14 bits");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    uint16_t* list = reinterpret_cast<uint16_t*>(const_cast<uint32_t*>(bm) + NE / 32);
+    int np = 0;
     for (int g = 0; g < (cnt + 31) / 32; ++g) {
         const uint32_t m = bm[g];
-        if (m == 0u) continue;
-        const int i = 32 * g + lane;
+        if (m >> lane & 1u) list[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(32 * g + lane);
+        np += __popc(m);
+    }
+    __syncwarp();
+    const long long kq = a.kq;
+    for (int g0 = 0; g0 < np; g0 += 32) {
+        const int nb = min(32, np - g0);
+        const uint32_t m = nb == 32 ? FULL : (1u << nb) - 1u;
         int x = 0, y = 0, e = 0, w = 0, sx = 0, sy = 0, ix = 0, iy = 0;
-        bool zx = true, zy = true;   // frozen trees
-        if (m >> lane & 1u) {
+        bool zx = true, zy = true, px = false, py = false;   // frozen; criterion passes
+        if (lane < nb) {
+            const int i = list[g0 + lane];
             int p, q;
             x = lw_find(S.parent, S.la[i]);
             y = lw_find(S.parent, S.lb[i]);
@@ -502,17 +515,17 @@ __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S
             zy = S.best[y] == 0u;
             sx = S.size[x]; sy = S.size[y];
             ix = S.intw[x]; iy = S.intw[y];
+            px = (long long)(w - ix) * sx <= kq;
+            py = (long long)(w - iy) * sy <= kq;
         }
         __syncwarp();   // every lane has read before lane 0 writes
         for (uint32_t mm = m; mm; mm &= mm - 1u) {
             const int k = __ffs(mm) - 1;
-            const int xy = __shfl_sync(FULL, x | y << 14 | (int)zx << 28 | (int)zy << 29, k);
-            const int xk = xy & 0x3fff, yk = (xy >> 14) & 0x3fff;
-            if (xk == yk || (xy >> 28) != 0) continue;   // a cycle, or a frozen tree
-            const long long wk = __shfl_sync(FULL, w, k);
-            const long long sxk = __shfl_sync(FULL, sx, k), syk = __shfl_sync(FULL, sy, k);
-            const long long ixk = __shfl_sync(FULL, ix, k), iyk = __shfl_sync(FULL, iy, k);
-            const bool fx = (wk - ixk) * sxk > a.kq, fy = (wk - iyk) * syk > a.kq;
+            const unsigned v = __shfl_sync(FULL, (unsigned)x | (unsigned)y << 14 | (unsigned)zx << 28 |
+                                                     (unsigned)zy << 29 | (unsigned)!px << 30 | (unsigned)!py << 31, k);
+            const int xk = (int)(v & 0x3fffu), yk = (int)((v >> 14) & 0x3fffu);
+            if (xk == yk || ((v >> 28) & 3u)) continue;   // a cycle, or a frozen tree
+            const bool fx = (v >> 30) & 1u, fy = v >> 31;
             if (fx || fy) {   // criterion fails: that tree can never merge again
                 if (fx) { zx |= x == xk; zy |= y == xk; }
                 if (fy) { zx |= x == yk; zy |= y == yk; }
@@ -522,21 +535,105 @@ __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S
                 }
                 continue;
             }
+            const int sxk = __shfl_sync(FULL, sx, k), syk = __shfl_sync(FULL, sy, k), wk = __shfl_sync(FULL, w, k);
             int big = xk, small = yk;
             if (sxk < syk) { big = yk; small = xk; }
-            const int ns = (int)(sxk + syk);
+            const int ns = sxk + syk;
             if (x == small) x = big;
             if (y == small) y = big;
-            if (x == big) { sx = ns; ix = (int)wk; }
-            if (y == big) { sy = ns; iy = (int)wk; }
+            if (x == big) { sx = ns; ix = wk; px = (long long)(w - ix) * sx <= kq; }
+            if (y == big) { sy = ns; iy = wk; py = (long long)(w - iy) * sy <= kq; }
             if (lane == 0) {
                 S.parent[small] = big;
                 S.size[big] = ns;
-                S.intw[big] = (int)wk;
+                S.intw[big] = wk;
             }
             if (lane == k) a.in_tree[e] = 1;
         }
         __syncwarp();   // lane 0's writes are seen by the next group's reads
+    }
+}
+
+// Minimum spanning forest by index of the window's live edges (roots in
+// S.la / S.lb, frozen trees marked best == 0), by Boruvka rounds in shared
+// memory: every tree takes its smallest edge (which belongs to the forest by
+// the cut property, the indices being distinct) and hooks onto the other end;
+// a pair that took the same edge keeps the smaller root.  Hooked trees fold
+// their sizes into their new roots, whose Int becomes w.  Only 2-cycles can
+// form, so each round at least halves the trees that still have live edges.
+template <int NT, int NE>
+__device__ __noinline__ void lw_boruvka(const ForestArgs& a, LocalWinT<NE>& S, unsigned live, int w)
+{
+    constexpr int LW_PER = NE / NT;
+    constexpr uint32_t MARK = 1u << 14;   // marks MARK | i: above 0 (frozen), below 0xffffffff (free)
+    const int t = threadIdx.x;
+    uint16_t* hooked = S.rep;             // free after the gather
+    int round = 0;
+    for (; round <= NE; ++round) {
+        int xa[LW_PER], xb[LW_PER];
+        if (t == 0) S.nhook = 0;
+#pragma unroll
+        for (int k = 0; k < LW_PER; ++k) {
+            xa[k] = xb[k] = 0;
+            if (!(live >> k & 1u)) continue;
+            const int i = t + k * NT;
+            xa[k] = lw_find(S.parent, S.la[i]);
+            xb[k] = lw_find(S.parent, S.lb[i]);
+            S.la[i] = (uint16_t)xa[k];
+            S.lb[i] = (uint16_t)xb[k];
+            if (xa[k] == xb[k] || S.best[xa[k]] == 0u || S.best[xb[k]] == 0u) {
+                live &= ~(1u << k);   // a cycle, or a frozen tree
+            } else {
+                atomicMin(&S.best[xa[k]], MARK | (uint32_t)i);
+                atomicMin(&S.best[xb[k]], MARK | (uint32_t)i);
+            }
+        }
+        const unsigned marked = live;
+        if (!__syncthreads_or(live != 0)) break;
+#pragma unroll
+        for (int k = 0; k < LW_PER; ++k) {
+            if (!(live >> k & 1u)) continue;
+            const int i = t + k * NT;
+            const uint32_t me = MARK | (uint32_t)i;
+            const bool ha = S.best[xa[k]] == me, hb = S.best[xb[k]] == me;
+            if (!ha && !hb) continue;
+            live &= ~(1u << k);
+            int e, we, p, q;
+            decode(S.key[i], a.ebits, a.W, e, we, p, q);
+            a.in_tree[e] = 1;
+            int r = xb[k], to = xa[k];
+            if (ha && hb) {
+                r = max(xa[k], xb[k]);
+                to = min(xa[k], xb[k]);
+            } else if (ha) {
+                r = xa[k];
+                to = xb[k];
+            }
+            S.parent[r] = to;
+            hooked[atomicAdd(&S.nhook, 1)] = (uint16_t)r;
+        }
+        __syncthreads();
+        // hooked roots are roots after every hook of the round and receive no
+        // size themselves, so the folded sums are exact
+        const int nh = S.nhook;
+        for (int j = t; j < nh; j += NT) {
+            const int r = hooked[j];
+            const int R = lw_find(S.parent, r);
+            atomicAdd(&S.size[R], S.size[r]);
+            S.intw[R] = w;
+        }
+#pragma unroll
+        for (int k = 0; k < LW_PER; ++k)
+            if (marked >> k & 1u) {
+                S.best[xa[k]] = 0xffffffffu;
+                S.best[xb[k]] = 0xffffffffu;
+            }
+        __syncthreads();
+    }
+    if (round > NE) dev_fail(a.st, DEV_TIMEOUT, 42);
+    if (t == 0 && a.stats) {
+        atomicAdd(a.stats, round + 1);   // Boruvka rounds
+        atomicAdd(a.stats + 1, 1);       // windows
     }
 }
 
@@ -551,6 +648,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     if (t == 0) {
         S.nroots = 0;
         S.wmin = INT_MAX;
+        S.wmax = -1;
     }
     __syncthreads();
     // gather: current global roots of both end points; one representative
@@ -560,7 +658,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     int ra[LW_PER], rb[LW_PER];
     uint32_t kk[LW_PER];
     unsigned live = 0;
-    int wl = INT_MAX;
+    int wl = INT_MAX, wh = -1;
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         const int i = t + k * NT;
@@ -576,6 +674,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         int e, w, p, q;
         decode(kk[k], a.ebits, a.W, e, w, p, q);
         wl = min(wl, w);
+        wh = max(wh, w);
         ra[k] = p;
         rb[k] = q;
     }
@@ -595,7 +694,10 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         atomicMin(loc + ra[k], 2 * i);
         atomicMin(loc + rb[k], 2 * i + 1);
     }
-    if (wl != INT_MAX) atomicMin(&S.wmin, wl);
+    if (wl != INT_MAX) {
+        atomicMin(&S.wmin, wl);
+        atomicMax(&S.wmax, wh);
+    }
     __syncthreads();
     // a tree whose criterion already fails at the window's smallest weight
     // can never merge again in this pass (every later edge of its region is
@@ -636,6 +738,14 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         S.lb[i] = S.rep[cb[k]];
     }
     __syncthreads();
+    if (S.wmin == S.wmax) {
+        // one weight class (the usual window of a big region): the trees that
+        // pass at its weight keep passing as they merge (Int becomes w), the
+        // others are frozen, so the window resolves as the minimum spanning
+        // forest by index among the passing trees
+        lw_boruvka<NT, NE>(a, S, live, (int)w0);
+        live = 0;
+    } else
     // deterministic reservations in shared memory; the earliest unresolved
     // edge always holds both of its reservations, so every round resolves at
     // least one edge and the loop ends within NE rounds
@@ -703,7 +813,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
                 // only merged edges of lower index (an edge merges only while
                 // it holds the reservation of both its trees), so the lowest
                 // pending edge always sees its sequential state.
-                uint32_t* bm = reinterpret_cast<uint32_t*>(S.rep);   // NE bits (rep is free after the gather)
+                uint32_t* bm = reinterpret_cast<uint32_t*>(S.rep);   // NE bits, then NE 16-bit slots (rep is free after the gather)
                 for (int j = t; j < NE / 32; j += NT) bm[j] = 0u;
                 __syncthreads();
 #pragma unroll
