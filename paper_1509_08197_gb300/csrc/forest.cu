@@ -390,6 +390,8 @@ struct LocalWinT {
     uint16_t rep[2 * NE];   // representative end point code -> local id
     int nroots;
     int wmin, wmax;         // smallest and largest weight in the window
+    int ntrans;             // weight changes along the window
+    int wnext;              // next weight class of the window
     int nhook;              // trees hooked in a Boruvka round
 };
 typedef LocalWinT<LW_EDGES> LocalWin;
@@ -474,6 +476,11 @@ __device__ __forceinline__ void g_find_many(int* parent, int* a, int* b, unsigne
 
 // Pending edges below this count per round hand the rest of a window to one warp.
 #define LW_SEQ_BELOW 16
+// Windows with fewer weight changes than this go class by class (Boruvka):
+// the 2048-edge region windows, and the 4096-edge windows of the top layer
+// and of the full-range first pass, whose classes are small.
+#define LW_CLASS_RUNS_RG 32
+#define LW_CLASS_RUNS_LW 8
 
 // Sequential Kruskal over the pending edges of a window (bitmap bm, window
 // order), run by one full warp.  The pending edges are first listed densely
@@ -554,8 +561,9 @@ __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S
     }
 }
 
-// Minimum spanning forest by index of the window's live edges (roots in
-// S.la / S.lb, frozen trees marked best == 0), by Boruvka rounds in shared
+// One weight class w of a window: its live edges (roots in S.la / S.lb,
+// frozen trees marked best == 0) resolve as the minimum spanning forest by
+// index among the trees that pass at w, by Boruvka rounds in shared
 // memory: every tree takes its smallest edge (which belongs to the forest by
 // the cut property, the indices being distinct) and hooks onto the other end;
 // a pair that took the same edge keeps the smaller root.  Hooked trees fold
@@ -568,6 +576,16 @@ __device__ __noinline__ void lw_boruvka(const ForestArgs& a, LocalWinT<NE>& S, u
     constexpr uint32_t MARK = 1u << 14;   // marks MARK | i: above 0 (frozen), below 0xffffffff (free)
     const int t = threadIdx.x;
     uint16_t* hooked = S.rep;             // free after the gather
+    // a tree that fails at w (on its state at the class start) can never merge again
+#pragma unroll
+    for (int k = 0; k < LW_PER; ++k) {
+        if (!(live >> k & 1u)) continue;
+        const int i = t + k * NT;
+        const int x = lw_find(S.parent, S.la[i]), y = lw_find(S.parent, S.lb[i]);
+        if (S.best[x] != 0u && (long long)(w - S.intw[x]) * S.size[x] > a.kq) S.best[x] = 0u;
+        if (S.best[y] != 0u && (long long)(w - S.intw[y]) * S.size[y] > a.kq) S.best[y] = 0u;
+    }
+    __syncthreads();
     int round = 0;
     for (; round <= NE; ++round) {
         int xa[LW_PER], xb[LW_PER];
@@ -649,6 +667,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         S.nroots = 0;
         S.wmin = INT_MAX;
         S.wmax = -1;
+        S.ntrans = 0;
     }
     __syncthreads();
     // gather: current global roots of both end points; one representative
@@ -657,8 +676,9 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     // then the finds in lockstep), so their latencies overlap.
     int ra[LW_PER], rb[LW_PER];
     uint32_t kk[LW_PER];
+    int wk[LW_PER];
     unsigned live = 0;
-    int wl = INT_MAX, wh = -1;
+    int wl = INT_MAX, wh = -1, ntr = 0;
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
         const int i = t + k * NT;
@@ -675,8 +695,15 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         decode(kk[k], a.ebits, a.W, e, w, p, q);
         wl = min(wl, w);
         wh = max(wh, w);
+        wk[k] = w;
         ra[k] = p;
         rb[k] = q;
+        const int i = t + k * NT;
+        if (i > 0) {
+            int ep, wp, pp, qp;
+            decode(keys[base + i - 1], a.ebits, a.W, ep, wp, pp, qp);
+            ntr += wp != w;
+        }
     }
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k)
@@ -698,6 +725,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         atomicMin(&S.wmin, wl);
         atomicMax(&S.wmax, wh);
     }
+    if (ntr) atomicAdd(&S.ntrans, ntr);
     __syncthreads();
     // a tree whose criterion already fails at the window's smallest weight
     // can never merge again in this pass (every later edge of its region is
@@ -738,12 +766,32 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         S.lb[i] = S.rep[cb[k]];
     }
     __syncthreads();
-    if (S.wmin == S.wmax) {
-        // one weight class (the usual window of a big region): the trees that
-        // pass at its weight keep passing as they merge (Int becomes w), the
-        // others are frozen, so the window resolves as the minimum spanning
-        // forest by index among the passing trees
-        lw_boruvka<NT, NE>(a, S, live, (int)w0);
+    constexpr int CLASS_RUNS = NE <= 2048 ? LW_CLASS_RUNS_RG : LW_CLASS_RUNS_LW;
+    if (S.ntrans < CLASS_RUNS) {
+        // few weight classes (the usual window of a big region): inside a
+        // class the trees that pass at its weight keep passing as they merge
+        // (Int becomes w) and the others cannot merge, so each class resolves
+        // as the minimum spanning forest by index among its passing trees;
+        // the classes go in increasing weight (regions sharing the window are
+        // independent, so one class step serves all of them)
+        int wc = S.wmin;
+        for (int c = 0; c <= CLASS_RUNS && wc != INT_MAX; ++c) {
+            unsigned lc = 0;
+#pragma unroll
+            for (int k = 0; k < LW_PER; ++k)
+                if ((live >> k & 1u) && wk[k] == wc) lc |= 1u << k;
+            lw_boruvka<NT, NE>(a, S, lc, wc);
+            if (t == 0) S.wnext = INT_MAX;
+            __syncthreads();
+            int m = INT_MAX;
+#pragma unroll
+            for (int k = 0; k < LW_PER; ++k)
+                if ((live >> k & 1u) && wk[k] > wc) m = min(m, wk[k]);
+            if (m != INT_MAX) atomicMin(&S.wnext, m);
+            __syncthreads();
+            wc = S.wnext;
+            __syncthreads();
+        }
         live = 0;
     } else
     // deterministic reservations in shared memory; the earliest unresolved
