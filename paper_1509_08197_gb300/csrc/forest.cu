@@ -375,8 +375,8 @@ __global__ void k_dr(ForestArgs a, int only_if_risky)
 // unresolved edge on both trees, so it is decided on their current state
 // exactly as the sequential algorithm decides it.  At the end of the window
 // the merged local state is written back.
-#define LW_EDGES 4096
-#define LW_THREADS 1024
+#define LW_EDGES 2048
+#define LW_THREADS 512
 
 template <int NE>
 struct LocalWinT {
@@ -476,11 +476,8 @@ __device__ __forceinline__ void g_find_many(int* parent, int* a, int* b, unsigne
 
 // Pending edges below this count per round hand the rest of a window to one warp.
 #define LW_SEQ_BELOW 16
-// Windows with fewer weight changes than this go class by class (Boruvka):
-// the 2048-edge region windows, and the 4096-edge windows of the top layer
-// and of the full-range first pass, whose classes are small.
-#define LW_CLASS_RUNS_RG 32
-#define LW_CLASS_RUNS_LW 8
+// Windows with fewer weight changes than this go class by class (Boruvka).
+#define LW_CLASS_RUNS 32
 
 // Sequential Kruskal over the pending edges of a window (bitmap bm, window
 // order), run by one full warp.  The pending edges are first listed densely
@@ -766,8 +763,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         S.lb[i] = S.rep[cb[k]];
     }
     __syncthreads();
-    constexpr int CLASS_RUNS = NE <= 2048 ? LW_CLASS_RUNS_RG : LW_CLASS_RUNS_LW;
-    if (S.ntrans < CLASS_RUNS) {
+    if (S.ntrans < LW_CLASS_RUNS) {
         // few weight classes (the usual window of a big region): inside a
         // class the trees that pass at its weight keep passing as they merge
         // (Int becomes w) and the others cannot merge, so each class resolves
@@ -775,7 +771,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         // the classes go in increasing weight (regions sharing the window are
         // independent, so one class step serves all of them)
         int wc = S.wmin;
-        for (int c = 0; c <= CLASS_RUNS && wc != INT_MAX; ++c) {
+        for (int c = 0; c <= LW_CLASS_RUNS && wc != INT_MAX; ++c) {
             unsigned lc = 0;
 #pragma unroll
             for (int k = 0; k < LW_PER; ++k)
