@@ -145,6 +145,49 @@ __global__ void k_rank(int* succ, int* val, int* succ2, int* val2, const int* d_
         for (int a = tid; a < n; a += nth) val[a] = __ldcg(v0 + a);
 }
 
+// The same pointer jumping in one block, for short lists: the lists live in
+// shared memory when they fit (RANK_SMALL entries), else in the caller's
+// global scratch (s2, v2), and every round ends with a block barrier instead
+// of a grid barrier.
+#define RANK_SMALL 8192
+__global__ void __launch_bounds__(1024) k_rank_small(int* succ, int* val, int* succ2, int* val2, const int* d_n)
+{
+    extern __shared__ int rk_sm[];
+    const int n = *d_n;
+    const bool in_smem = n <= RANK_SMALL;
+    int *s0 = succ, *v0 = val, *s1 = succ2, *v1 = val2;
+    if (in_smem) {
+        s0 = rk_sm;
+        v0 = rk_sm + RANK_SMALL;
+        s1 = rk_sm + 2 * RANK_SMALL;
+        v1 = rk_sm + 3 * RANK_SMALL;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            s0[i] = succ[i];
+            v0[i] = val[i];
+        }
+        __syncthreads();
+    }
+    for (int it = 0; it < 40; ++it) {
+        int changed = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int sc = s0[i], v = v0[i];
+            if (sc != HDP_END) {
+                v += v0[sc];
+                sc = s0[sc];
+                changed |= sc != HDP_END;
+            }
+            s1[i] = sc;
+            v1[i] = v;
+        }
+        const int any = __syncthreads_or(changed);
+        int* t = s0; s0 = s1; s1 = t;
+        t = v0; v0 = v1; v1 = t;
+        if (!any) break;
+    }
+    if (v0 != val)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) val[i] = v0[i];
+}
+
 // parent = the neighbour whose arc into v comes first in the tour; subtree size
 // and tour positions of the entering (down) and leaving (up) arcs
 __global__ void k_orient(const uint8_t* adj, const uint32_t* aoff, const int* dtroot, const int* R, const int* owner, const int* offs, int N,
@@ -379,9 +422,18 @@ void launch_order(Ctx& c, int l)
     const int est = (2 * N >> lg) + 1024;   // expected segments, for the grid sizes only
     k_lr_walk<<<min(cdiv(est, 128), c.num_sms * 16), 128, 0, s>>>(c.succ, sid, spl, nspl, lg, 2 * N, owner, offs,
                                                                  rs, rv, c.st);
-    cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), s);
-    cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), s);
-    {
+    if ((2 * N >> lg) <= 3 * RANK_SMALL / 4) {
+        // a short list: one block, shared memory
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(k_rank_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * RANK_SMALL * (int)sizeof(int));
+            configured = true;
+        }
+        k_rank_small<<<1, 1024, 4 * RANK_SMALL * sizeof(int), s>>>(rs, rv, rs2, rv2, nspl);
+    } else {
+        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 3 * sizeof(int), s);
+        cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), s);
         int* a0 = rs; int* a1 = rv; int* a2 = rs2; int* a3 = rv2;
         const int* nar = nspl;
         int* ctr = c.ints + IDX_CTR0;
