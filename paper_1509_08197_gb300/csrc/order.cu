@@ -412,7 +412,9 @@ void launch_order(Ctx& c, int l)
     k_arc_count<<<g, 256, 0, s>>>(c.adj, N, cnt);
     scan_u32(cnt, c.aoff, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NARCS), s);
     // list ranking by splitters: about one arc in 2^lg starts a segment
-    const int lg = N >= (1 << 19) ? 5 : N >= (1 << 16) ? 4 : 3;
+    // (layers of 64K..128K nodes take 1 in 32, so that their segment list is
+    // short enough for the one-block ranking)
+    const int lg = N >= (1 << 19) ? 5 : N >= (1 << 17) ? 4 : N >= (1 << 16) ? 5 : 3;
     int* nspl = c.ints + IDX_TMP2;
     cudaMemsetAsync(nspl, 0, sizeof(int), s);
     int* sid = c.val;
