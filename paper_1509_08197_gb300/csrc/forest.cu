@@ -990,6 +990,26 @@ __device__ __forceinline__ int cc_find(int* par, int v)
     return v;
 }
 
+// Runs first: one thread per CC_RUN pixels of a row links every pixel to the
+// first pixel of its same-set run inside that stretch (parents only decrease),
+// so the hooking below skips those horizontal edges and starts from short
+// chains.
+#define CC_RUN 32
+__global__ void k_cc_runs(ForestArgs a, int* par)
+{
+    if (a.risky && __ldcg(a.risky)) return;
+    const int per_row = (a.W + CC_RUN - 1) / CC_RUN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= per_row * (a.N / a.W)) return;
+    const int y = c / per_row, x0 = (c - y * per_row) * CC_RUN, x1 = min(x0 + CC_RUN, a.W);
+    int run = y * a.W + x0;
+    for (int x = x0 + 1; x < x1; ++x) {
+        const int v = y * a.W + x;
+        if (same_set(a, v - 1, v)) par[v] = run;
+        else run = v;
+    }
+}
+
 __global__ void k_cc_hook(ForestArgs a, int* par)
 {
     if (a.risky && __ldcg(a.risky)) return;
@@ -999,6 +1019,7 @@ __global__ void k_cc_hook(ForestArgs a, int* par)
     if (e >= 2 * a.N) return;
     const int p = e >> 1;
     if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) return;   // no neighbour there
+    if (!(e & 1) && (p % a.W) % CC_RUN != CC_RUN - 1) return;      // linked by k_cc_runs
     const int q = (e & 1) ? p + a.W : p + 1;
     if (!same_set(a, p, q)) return;
     int u = cc_find(par, p), v = cc_find(par, q);
@@ -1283,6 +1304,7 @@ void launch_forest(Ctx& c, int l, int hdp)
         // (lock-free union-find), sort the edges by region, resolve the
         // first pass region by region, then link by Boruvka.  With risky edges every step but the last returns at once
         // and the reservation engine runs both passes.
+        k_cc_runs<<<cdiv(cdiv(d.W, CC_RUN) * d.H, 256), 256, 0, c.s>>>(a, c.parent);
         k_cc_hook<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.parent);
         k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
         int* nvalid = c.ints + IDX_TMP3;
