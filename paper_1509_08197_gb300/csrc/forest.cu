@@ -2,22 +2,28 @@
 // (w, edge id) order with Rule 2, DT-Rule 2 (Eq. DTrules) and, for the
 // segment tree, the merge criterion w <= Int(C) + k/|C|.
 //
-// Four engines produce the sequential-Kruskal result exactly:
+// Five engines produce the sequential-Kruskal result exactly:
 //  * Boruvka over the sorted list (the list index is the strict order) when
 //    no state-dependent rule is active: plain MST, full-range layers, the
 //    segment tree's linking pass, and HDP layers with no "risky" edge.
 //    Without risky edges every tree keeps the set of its pixels (merges only
 //    join equal sets), so DT-Rule 2 reduces to "same PixelIntv" and the result
 //    is the minimum spanning forest of the same-set subgraph.
-//  * Windowed reservations in shared memory (segment-tree first pass, small
-//    layers): windows of consecutive edges whose trees are copied into shared
-//    memory and resolved there by deterministic reservations; a tree whose
+//  * Windows in shared memory (segment-tree first pass of the top layer):
+//    windows of consecutive edges whose trees are copied into shared memory.
+//    A window of few weight classes goes class by class: inside a class a
+//    tree's criterion cannot change before it merges, and a merge sets
+//    Int = w, which passes for the rest of the class, so a class is the
+//    minimum spanning forest by index among its passing trees (Boruvka in
+//    shared memory).  Other windows use deterministic reservations, and one
+//    warp finishes them sequentially once the rounds stall.  A tree whose
 //    criterion fails at its earliest pending edge is frozen for good.
-//  * Hybrid first pass (big layers): a weight class with many edges is a
-//    Boruvka by edge id among the edges whose two trees pass at the start of
-//    the class (inside a class a tree's criterion cannot change before it
-//    merges, and a merge sets Int = w, which passes for the rest of the
-//    class); runs of small classes form windows resolved as above.
+//  * Regions (segment-tree first pass of predicted layers without risky
+//    edges): connected same-set regions are independent, so persistent CTAs
+//    take whole regions (small ones packed together) window by window.
+//  * Hybrid first pass (big full-range layers): a weight class with many
+//    edges is a Boruvka by edge id over the whole grid, for the same reason;
+//    runs of small classes form windows resolved as above.
 //  * Deterministic reservations over the whole list (general fallback, risky
 //    HDP layers): each round takes a window of the earliest unresolved edges;
 //    an edge that holds the reservation of both its trees is resolved on their
