@@ -181,7 +181,10 @@ int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, 
  * of level+1 exists (from hdp_run_level(level+1) or hdp_set_stage). */
 int hdp_run_level(hdp_ctx* ctx, int level);
 
-/* Wait for the context's stream; report device-side errors. */
+/* Wait for the context's stream (and its internal side stream, which runs
+ * the priors and interval tables of the predicted layers after
+ * hdp_build_trees; each hdp_run_level joins its layer's share before using
+ * it); report device-side errors. */
 int hdp_sync(hdp_ctx* ctx);
 
 int hdp_destroy(hdp_ctx* ctx);
