@@ -9,6 +9,7 @@ costs within 1e-5 relative; WTA identical except near ties (counted).
 import numpy as np
 import pytest
 
+import oracle
 import paper_1509_08197_gb300 as hdp
 from paper_1509_08197_gb300.scenes import workload_pair
 
@@ -85,6 +86,31 @@ def test_tiny_hdp_mst():
     res = _run_layers(hp, pair)
     for l, (g, o) in res.items():
         _assert_layer(l, g, o, hp, None)
+
+
+def test_injected_prior_rebuilds_the_table():
+    # the priors and tables of predicted layers run on the context's side
+    # stream after hdp_build_trees; a prior set afterwards must win, and the
+    # layer's table must be rebuilt from it
+    pair = workload_pair("tiny")
+    hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, tree="mst")
+    dev = torch.device("cuda:0")
+    ctx = hdp.hdp_create(hp)
+    try:
+        left = torch.from_numpy(pair.left).to(dev).contiguous()
+        right = torch.from_numpy(pair.right).to(dev).contiguous()
+        hdp.hdp_build_trees(ctx, left, right)
+        op = oracle_params(hp)
+        d0, d1 = ctx.dims[0][2], ctx.dims[1][2]
+        custom = np.random.default_rng(7).integers(1, 60, d0 + 1).astype(np.int64)
+        hdp.hdp_set_stage(ctx, 0, "prior", custom)
+        hdp.hdp_run_level(ctx, 1)
+        hdp.hdp_run_level(ctx, 0)
+        assert np.array_equal(hdp.hdp_get_stage(ctx, 0, "prior"), custom)
+        want = oracle.range_table(custom, d0, d1, op.gmm_for(0), op.delta0)
+        assert np.array_equal(hdp.hdp_get_stage(ctx, 0, "table"), want)
+    finally:
+        hdp.hdp_destroy(ctx)
 
 
 def test_tiny_hdp_st_and_full():
