@@ -661,10 +661,18 @@ __device__ __noinline__ void lw_boruvka(const ForestArgs& a, LocalWinT<NE>& S, u
 // One window [base, base + cnt) of the list `keys` (a run of the strict
 // order), resolved by the calling CTA of NT threads.  loc[] is INT_MAX on
 // entry and on exit.
-template <bool L2, int NT, int NE>
-__device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, LocalWinT<NE>& S, int base, int cnt)
+// RISKY (layers with a risky edge): every edge of the list takes part,
+// DT-Rule 2 is decided on the trees' TreeIntv, kept in ST (HDP_WORDS words per
+// local tree) and merged with the trees; kq is the criterion's k (a huge
+// value for a pass without the criterion).  Windows then use reservations
+// only: the class-by-class shortcut and the sequential finish assume trees
+// that never join different sets.
+template <bool L2, int NT, int NE, bool RISKY = false>
+__device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, LocalWinT<NE>& S, int base, int cnt,
+                          uint32_t* ST = nullptr, long long kq_in = -1)
 {
     constexpr int LW_PER = NE / NT;
+    const long long kq = RISKY ? kq_in : a.kq;
     const int t = threadIdx.x;
     if (t == 0) {
         S.nroots = 0;
@@ -710,7 +718,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
     }
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k)
-        if ((live >> k & 1u) && !same_set(a, ra[k], rb[k])) live &= ~(1u << k);
+        if (!RISKY && (live >> k & 1u) && !same_set(a, ra[k], rb[k])) live &= ~(1u << k);
     g_find_many<L2, LW_PER>(a.parent, ra, rb, live);
 #pragma unroll
     for (int k = 0; k < LW_PER; ++k) {
@@ -756,7 +764,10 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
                 const int iw = L2 ? __ldcg(a.intw + r) : a.intw[r];
                 S.size[id] = sz;
                 S.intw[id] = iw;
-                S.best[id] = (w0 - iw) * sz > a.kq ? 0u : 0xffffffffu;
+                S.best[id] = (w0 - iw) * sz > kq ? 0u : 0xffffffffu;
+                if (RISKY)
+#pragma unroll
+                    for (int h = 0; h < HDP_WORDS; ++h) ST[id * HDP_WORDS + h] = a.T[(size_t)r * HDP_WORDS + h];
             }
         }
     }
@@ -769,7 +780,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         S.lb[i] = S.rep[cb[k]];
     }
     __syncthreads();
-    if (S.ntrans < LW_CLASS_RUNS) {
+    if (!RISKY && S.ntrans < LW_CLASS_RUNS) {
         // few weight classes (the usual window of a big region): inside a
         // class the trees that pass at its weight keep passing as they merge
         // (Int becomes w) and the others cannot merge, so each class resolves
@@ -835,7 +846,7 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
             const long long ia = S.intw[xa[k]], ib = S.intw[xb[k]];
             // the earliest unresolved edge of a tree sees its final state: if
             // the criterion fails there, the tree is frozen and the edge rejected
-            const bool fa = ha && (w - ia) * sa > a.kq, fb = hb && (w - ib) * sb > a.kq;
+            const bool fa = ha && (w - ia) * sa > kq, fb = hb && (w - ib) * sb > kq;
             if (fa || fb) {
                 if (fa) S.best[xa[k]] = 0u;
                 if (fb) S.best[xb[k]] = 0u;
@@ -843,17 +854,30 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
                 continue;
             }
             if (!ha || !hb) continue;
-            live &= ~(1u << k);                                              // both pass: merge
-            int big = xa[k], small = xb[k];
+            live &= ~(1u << k);
+            if (RISKY) {   // DT-Rule 2: Jaccard ratio of the two TreeIntv at least beta
+                int inter = 0, uni = 0;
+#pragma unroll
+                for (int h = 0; h < HDP_WORDS; ++h) {
+                    const uint32_t ta = ST[xa[k] * HDP_WORDS + h], tb = ST[xb[k] * HDP_WORDS + h];
+                    inter += __popc(ta & tb);
+                    uni += __popc(ta | tb);
+                }
+                if ((long long)inter * a.bden < (long long)a.bnum * uni) continue;
+            }
+            int big = xa[k], small = xb[k];                                  // both pass: merge
             if (sa < sb) { big = xb[k]; small = xa[k]; }
             S.parent[small] = big;
             S.size[big] = (int)(sa + sb);
             S.intw[big] = w;
+            if (RISKY)
+#pragma unroll
+                for (int h = 0; h < HDP_WORDS; ++h) ST[big * HDP_WORDS + h] |= ST[small * HDP_WORDS + h];
             a.in_tree[e] = 1;
         }
         const int lt = __syncthreads_count(live != 0);          // threads still holding edges
         const int rt = __syncthreads_count(live != live0);      // threads that resolved one this round
-        if (lt == 0 || (round >= 1 && rt < LW_SEQ_BELOW)) {
+        if (lt == 0 || (!RISKY && round >= 1 && rt < LW_SEQ_BELOW)) {
             if (lt != 0) {
                 // Few edges resolve per round: the rest wait in chains on a few
                 // big trees, and every further round would re-examine all of
@@ -899,6 +923,9 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         } else {
             a.size[r] = S.size[x];
             a.intw[r] = S.intw[x];
+            if (RISKY)
+#pragma unroll
+                for (int h = 0; h < HDP_WORDS; ++h) a.T[(size_t)r * HDP_WORDS + h] = ST[x * HDP_WORDS + h];
         }
         atomicExch(loc + r, INT_MAX);
     }
@@ -914,6 +941,39 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_local(ForestArgs a, int* l
     if (threadIdx.x == 0) *a.engine = 3;
     for (int base = 0; base < n; base += LW_EDGES)
         lw_window<false, LW_THREADS, LW_EDGES>(a, a.keys, loc, S, base, min(LW_EDGES, n - base));
+}
+
+// Layers with a risky edge (DT-Rule 2 may join different sets, so regions are
+// not independent): every pass over the whole list in one CTA, window by
+// window, with each local tree's TreeIntv in shared memory.
+#define RK_EDGES 1024
+#define RK_THREADS 512
+typedef LocalWinT<RK_EDGES> RiskyWin;
+__host__ __device__ constexpr size_t risky_smem() { return sizeof(RiskyWin) + 2 * RK_EDGES * HDP_WORDS * sizeof(uint32_t); }
+
+__global__ void __launch_bounds__(RK_THREADS, 1) k_fh_risky(ForestArgs a, int* loc)
+{
+    extern __shared__ __align__(16) unsigned char lw_raw[];
+    RiskyWin& S = *reinterpret_cast<RiskyWin*>(lw_raw);
+    uint32_t* ST = reinterpret_cast<uint32_t*>(lw_raw + sizeof(RiskyWin));
+    if (!a.risky || !__ldcg(a.risky)) return;
+    const int n = *a.d_n;
+    if (threadIdx.x == 0) *a.engine = 6;
+    for (int pass = 0; pass < a.passes; ++pass) {
+        const long long kq = a.crit_first && pass == 0 ? a.kq : (1LL << 60);
+        for (int base = 0; base < n; base += RK_EDGES)
+            lw_window<false, RK_THREADS, RK_EDGES, true>(a, a.keys, loc, S, base, min(RK_EDGES, n - base), ST, kq);
+    }
+}
+
+static void launch_risky(ForestArgs& a, Ctx& c)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_fh_risky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)risky_smem());
+        configured = true;
+    }
+    k_fh_risky<<<1, RK_THREADS, risky_smem(), c.s>>>(a, c.rootof);
 }
 
 // Segment-tree first pass for big layers (cooperative, one CTA per SM):
@@ -1200,7 +1260,8 @@ __global__ void k_finish_roots(const int* rootof, const int* minid, int* dtroot,
     int r = rootof[v];
     dtroot[v] = minid[r];
     if (r == v) {
-        bool maintained = pixset != nullptr && *engine == 2;
+        // the reservation engines of risky layers keep the unions themselves
+        bool maintained = pixset != nullptr && (*engine == 2 || *engine == 6);
         if (!maintained) {
             const uint32_t* src = pixset ? table + (size_t)pixset[v] * HDP_WORDS : full_mask;
             for (int k = 0; k < HDP_WORDS; ++k) T[(size_t)v * HDP_WORDS + k] = src[k];
@@ -1298,13 +1359,13 @@ void launch_forest(Ctx& c, int l, int hdp)
     // grids sized by the layer (one block per 4K edges at most, one wave at
     // most): small layers get cheap barriers and batched pairs share the GPU
     const int bor_blocks = cdiv(2 * N, c.tune.boruvka_edges_per_cta);
-    a.dr_if_risky = hdp && !small;
+    a.dr_if_risky = 0;   // risky layers: k_fh_risky below
     if (!st_tree) {
         a.passes = 1;
         a.crit_first = 0;
         a.WIN = small ? 4096 : 16384;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
-        if (hdp && small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
+        if (hdp) launch_risky(a, c);
     } else if (hdp && N < c.tune.region_max_nodes) {
         // HDP layer: regions.  Label the connected same-set regions
         // (lock-free union-find), sort the edges by region, resolve the
@@ -1359,9 +1420,8 @@ void launch_forest(Ctx& c, int l, int hdp)
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = small ? 4096 : 16384;
-        a.dr_if_risky = !small;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
-        if (small) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);
+        launch_risky(a, c);
     } else if (!small) {
         // first pass by weight classes and windows, then the linking pass by Boruvka
         uint32_t* flags = c.sorted == c.keys0 ? c.keys1 : c.keys0;
@@ -1385,6 +1445,7 @@ void launch_forest(Ctx& c, int l, int hdp)
         a.crit_first = 1;
         a.WIN = 16384;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        if (hdp) launch_risky(a, c);
     } else {
         // small layer: the windowed first pass in shared memory, then the
         // linking pass by Boruvka; with risky edges both return at once and
@@ -1401,7 +1462,7 @@ void launch_forest(Ctx& c, int l, int hdp)
         a.passes = 2;
         a.crit_first = 1;
         a.WIN = 4096;
-        if (hdp) k_dr<true><<<1, 1024, 0, c.s>>>(a, 1);   // risky: both passes in one block
+        if (hdp) launch_risky(a, c);   // risky: both passes, windowed, in one CTA
     }
     k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
     k_finish_roots<<<cdiv(N, 256), 256, 0, c.s>>>(c.rootof, c.minid, c.dtroot, c.T, hdp ? c.pixset : nullptr,

@@ -136,15 +136,15 @@ def test_third_size_hdp(tree):
 @pytest.mark.parametrize("tree", ["mst", "st"])
 def test_risky_layers_take_the_reservation_engine(tree):
     # beta = 1/5: DT-Rule 2 joins many different sets, so the lower layers are
-    # "risky" and only the reservation engine is exact there (grid form at the
-    # 463x370 layer, single block below 131072 nodes)
+    # "risky" and only reservations are exact there: the windowed engine with
+    # each local tree's TreeIntv in shared memory (engine 6)
     pair = workload_pair("third")
     hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=3, tree=tree, beta=(1, 5))
     res = _run_layers(hp, pair)
     risky = {l: int(g["info"][5]) for l, (g, o) in res.items()}
     engine = {l: int(g["info"][3]) for l, (g, o) in res.items()}
     assert risky[0] == 1 and risky[1] == 1, risky
-    assert all(engine[l] == 2 for l in risky if risky[l]), engine
+    assert all(engine[l] == 6 for l in risky if risky[l]), engine
     for l, (g, o) in res.items():
         _assert_layer(l, g, o, hp, None)
 
