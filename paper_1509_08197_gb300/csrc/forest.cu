@@ -24,10 +24,13 @@
 //  * Hybrid first pass (big full-range layers): a weight class with many
 //    edges is a Boruvka by edge id over the whole grid, for the same reason;
 //    runs of small classes form windows resolved as above.
-//  * Deterministic reservations over the whole list (general fallback, risky
-//    HDP layers): each round takes a window of the earliest unresolved edges;
-//    an edge that holds the reservation of both its trees is resolved on their
-//    current state, exactly as the sequential algorithm would.
+//  * Windows for risky HDP layers (an edge between different sets whose
+//    Jaccard ratio reaches beta, so DT-Rule 2 may join different sets and
+//    the regions are not independent): every pass over the whole list in one
+//    CTA, window by window, by deterministic reservations in shared memory,
+//    with each local tree's TreeIntv there too.  An edge that holds the
+//    reservation of both its trees is decided on their current state,
+//    exactly as the sequential algorithm decides it.
 #include "hdp_impl.cuh"
 
 #define FOREST_THREADS 512
@@ -61,10 +64,7 @@ struct ForestArgs {
     long long kq;
     uint32_t* T;
     int bnum, bden;
-    int *win, *wtmp, *wra, *wrb, *wst;
-    int WIN;
     int passes, crit_first;
-    int dr_if_risky;     // k_boruvka: run the reservation engine itself when the layer is risky
     int big_class;       // k_fh_hybrid: weight classes with at least this many edges run as a grid Boruvka
     int* stats;          // [2]: reservation rounds and windows of the windowed engines (reported per layer)
     int* engine;
@@ -167,18 +167,12 @@ __device__ bool boruvka_rounds(const ForestArgs& a, int& cur, int& par, bool rec
     return false;
 }
 
-template <bool SINGLE>
-__device__ void dr_run(const ForestArgs& a);
-
 // Minimum spanning forest of the eligible edges (MST, or the linking pass of
 // the segment tree on top of the first pass).  Runs only when no risky edge
 // exists.
 __global__ void k_boruvka(ForestArgs a)
 {
-    if (a.risky && __ldcg(a.risky)) {
-        if (a.dr_if_risky) dr_run<false>(a);   // the general fallback, on the same grid
-        return;
-    }
+    if (a.risky && __ldcg(a.risky)) return;   // k_fh_risky takes the layer
     const int n = *a.d_n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     if (tid == 0 && *a.engine == 0) *a.engine = 1;
@@ -196,177 +190,6 @@ __global__ void k_boruvka(ForestArgs a)
     if (!grid_sync(a.st, gridDim.x)) return;
     int cur = 0, par = 0;
     boruvka_rounds(a, cur, par, false);
-}
-
-__device__ int block_excl_sum(int v, int* smem, int* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    int incl = v;
-    for (int d = 1; d < 32; d <<= 1) {
-        int o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
-    }
-    if (lane == 31) smem[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int x = lane < nw ? smem[lane] : 0;
-        int xi = x;
-        for (int d = 1; d < 32; d <<= 1) {
-            int o = __shfl_up_sync(0xffffffffu, xi, d);
-            if (lane >= d) xi += o;
-        }
-        if (lane < nw) smem[lane] = xi - x;
-        if (lane == nw - 1) smem[32] = xi;
-    }
-    __syncthreads();
-    int r = smem[warp] + incl - v;
-    *total = smem[32];
-    __syncthreads();
-    return r;
-}
-
-// single block: plain (L1-cached) accesses; the block's own writes are visible
-// to it after __syncthreads.  Grid: through L2, which all SMs share.
-template <bool SINGLE> __device__ __forceinline__ int ldv(const int* p) { return SINGLE ? *p : __ldcg(p); }
-template <bool SINGLE> __device__ __forceinline__ uint32_t ldv(const uint32_t* p) { return SINGLE ? *p : __ldcg(p); }
-template <bool SINGLE> __device__ __forceinline__ void stv(int* p, int v) { if (SINGLE) *p = v; else __stcg(p, v); }
-template <bool SINGLE> __device__ __forceinline__ void stv(uint32_t* p, uint32_t v) { if (SINGLE) *p = v; else __stcg(p, v); }
-
-// union-find root for one block (plain loads: the block's own writes are
-// visible to it after __syncthreads)
-template <bool SINGLE>
-__device__ __forceinline__ int uf_find_t(int* parent, int v)
-{
-    if (!SINGLE) return uf_find(parent, v);
-    for (int it = 0; it < (1 << 26); ++it) {
-        int p = parent[v];
-        if (p == v) return v;
-        int gp = parent[p];
-        if (gp == p) return p;
-        parent[v] = gp;
-        v = gp;
-    }
-    return v;
-}
-
-// Deterministic reservations over windows of the sorted list.  ctr[3] = window
-// size, ctr[4] = next fresh list index.  best[] holds window positions.
-template <bool SINGLE>
-__device__ void dr_run(const ForestArgs& a)
-{
-    __shared__ int smem[33];
-    const unsigned nb = gridDim.x;
-    const int n = *a.d_n;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    const bool full = a.pixset == nullptr;
-    if (tid == 0) *a.engine = 2;
-    for (int pass = 0; pass < a.passes; ++pass) {
-        const bool crit = a.crit_first && pass == 0;
-        if (tid == 0) { a.ctr[3] = 0; a.ctr[4] = 0; }
-        if (!grid_sync(a.st, nb)) return;
-        for (long long round = 0;; ++round) {
-            if (round > (1LL << 30)) { dev_fail(a.st, DEV_TIMEOUT, 30); return; }
-            if (blockIdx.x == 0) {
-                int k = ldv<SINGLE>(a.ctr + 3), nx = ldv<SINGLE>(a.ctr + 4);
-                int add = min(a.WIN - k, n - nx);
-                for (int t = threadIdx.x; t < add; t += blockDim.x) a.win[k + t] = nx + t;
-                __syncthreads();
-                if (threadIdx.x == 0) { a.ctr[3] = k + add; a.ctr[4] = nx + add; }
-            }
-            if (!grid_sync(a.st, nb)) return;
-            const int wc = ldv<SINGLE>(a.ctr + 3);
-            if (wc == 0) break;
-            for (int i = tid; i < wc; i += nth) {
-                int idx = ldv<SINGLE>(a.win + i), e, w, p, q;
-                decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
-                int ra = uf_find_t<SINGLE>(a.parent, p), rb = uf_find_t<SINGLE>(a.parent, q);
-                a.wra[i] = ra;
-                a.wrb[i] = rb;
-                if (ra != rb) {
-                    atomicMin(a.best + ra, i);
-                    atomicMin(a.best + rb, i);
-                }
-            }
-            if (!grid_sync(a.st, nb)) return;
-            for (int i = tid; i < wc; i += nth) {
-                int ra = ldv<SINGLE>(a.wra + i), rb = ldv<SINGLE>(a.wrb + i);
-                int done = 1;
-                if (ra != rb) {
-                    if (ldv<SINGLE>(a.best + ra) == i && ldv<SINGLE>(a.best + rb) == i) {
-                        int idx = ldv<SINGLE>(a.win + i), e, w, p, q;
-                        decode(a.keys[idx], a.ebits, a.W, e, w, p, q);
-                        bool ok = true;
-                        if (!full) {
-                            int inter = 0, uni = 0;
-#pragma unroll
-                            for (int k = 0; k < HDP_WORDS; ++k) {
-                                uint32_t ta = ldv<SINGLE>(a.T + (size_t)ra * HDP_WORDS + k);
-                                uint32_t tb = ldv<SINGLE>(a.T + (size_t)rb * HDP_WORDS + k);
-                                inter += __popc(ta & tb);
-                                uni += __popc(ta | tb);
-                            }
-                            ok = (long long)inter * a.bden >= (long long)a.bnum * uni;   // DT-Rule 2
-                        }
-                        long long sa = ldv<SINGLE>(a.size + ra), sb = ldv<SINGLE>(a.size + rb);
-                        if (ok && crit) {
-                            long long ia = ldv<SINGLE>(a.intw + ra), ib = ldv<SINGLE>(a.intw + rb);
-                            ok = (long long)w * sa <= ia * sa + a.kq && (long long)w * sb <= ib * sb + a.kq;
-                        }
-                        if (ok) {
-                            int big = ra, small = rb;
-                            if (sa < sb) { big = rb; small = ra; }
-                            stv<SINGLE>(a.parent + small, big);
-                            stv<SINGLE>(a.size + big, (int)(sa + sb));
-                            stv<SINGLE>(a.intw + big, w);
-                            if (!full) {
-#pragma unroll
-                                for (int k = 0; k < HDP_WORDS; ++k) {
-                                    uint32_t u = ldv<SINGLE>(a.T + (size_t)ra * HDP_WORDS + k) |
-                                                 ldv<SINGLE>(a.T + (size_t)rb * HDP_WORDS + k);
-                                    stv<SINGLE>(a.T + (size_t)big * HDP_WORDS + k, u);
-                                }
-                            }
-                            a.in_tree[e] = 1;
-                        }
-                    } else {
-                        done = 0;
-                    }
-                }
-                a.wst[i] = done;
-            }
-            if (!grid_sync(a.st, nb)) return;
-            for (int i = tid; i < wc; i += nth) {
-                int ra = ldv<SINGLE>(a.wra + i), rb = ldv<SINGLE>(a.wrb + i);
-                if (ra != rb) {
-                    stv<SINGLE>(a.best + ra, INT_MAX);
-                    stv<SINGLE>(a.best + rb, INT_MAX);
-                }
-            }
-            if (blockIdx.x == 0) {
-                // stable compaction of the unresolved window entries
-                const int per = cdiv(wc, (int)blockDim.x);
-                const int b0 = threadIdx.x * per, b1 = min(wc, b0 + per);
-                int cnt = 0;
-                for (int i = b0; i < b1; ++i) cnt += ldv<SINGLE>(a.wst + i) == 0;
-                int tot = 0;
-                int off = block_excl_sum(cnt, smem, &tot);
-                for (int i = b0; i < b1; ++i)
-                    if (ldv<SINGLE>(a.wst + i) == 0) a.wtmp[off++] = ldv<SINGLE>(a.win + i);
-                __syncthreads();
-                for (int i = threadIdx.x; i < tot; i += blockDim.x) a.win[i] = a.wtmp[i];
-                __syncthreads();
-                if (threadIdx.x == 0) a.ctr[3] = tot;
-            }
-            if (!grid_sync(a.st, nb)) return;
-        }
-    }
-}
-
-template <bool SINGLE>
-__global__ void k_dr(ForestArgs a, int only_if_risky)
-{
-    if (only_if_risky && !ldv<SINGLE>(a.risky)) return;
-    dr_run<SINGLE>(a);
 }
 
 // ---- segment-tree first pass, windowed, for one CTA (layers up to
@@ -1331,7 +1154,6 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.T = c.T;
     a.bnum = c.p.beta_num;
     a.bden = c.p.beta_den;
-    a.win = c.win; a.wtmp = c.wtmp; a.wra = c.wra; a.wrb = c.wrb; a.wst = c.wst;
     a.engine = c.ints + IDX_ENGINE;
     a.st = c.st;
     a.stats = c.ints + IDX_DRROUNDS;
@@ -1359,18 +1181,17 @@ void launch_forest(Ctx& c, int l, int hdp)
     // grids sized by the layer (one block per 4K edges at most, one wave at
     // most): small layers get cheap barriers and batched pairs share the GPU
     const int bor_blocks = cdiv(2 * N, c.tune.boruvka_edges_per_cta);
-    a.dr_if_risky = 0;   // risky layers: k_fh_risky below
     if (!st_tree) {
         a.passes = 1;
         a.crit_first = 0;
-        a.WIN = small ? 4096 : 16384;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         if (hdp) launch_risky(a, c);
     } else if (hdp && N < c.tune.region_max_nodes) {
         // HDP layer: regions.  Label the connected same-set regions
         // (lock-free union-find), sort the edges by region, resolve the
-        // first pass region by region, then link by Boruvka.  With risky edges every step but the last returns at once
-        // and the reservation engine runs both passes.
+        // first pass region by region, then link by Boruvka.  With risky
+        // edges every step but the last returns at once and k_fh_risky runs
+        // both passes.
         k_cc_runs<<<cdiv(cdiv(d.W, CC_RUN) * d.H, 256), 256, 0, c.s>>>(a, c.parent);
         k_cc_hook<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.parent);
         k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
@@ -1419,7 +1240,6 @@ void launch_forest(Ctx& c, int l, int hdp)
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
         a.passes = 2;
         a.crit_first = 1;
-        a.WIN = small ? 4096 : 16384;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         launch_risky(a, c);
     } else if (!small) {
@@ -1443,13 +1263,12 @@ void launch_forest(Ctx& c, int l, int hdp)
         cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
         a.passes = 2;
         a.crit_first = 1;
-        a.WIN = 16384;
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         if (hdp) launch_risky(a, c);
     } else {
         // small layer: the windowed first pass in shared memory, then the
         // linking pass by Boruvka; with risky edges both return at once and
-        // the reservation engine runs both passes in one block
+        // k_fh_risky runs both passes
         static bool configured = false;
         if (!configured) {
             cudaFuncSetAttribute(k_fh_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalWin));
@@ -1461,7 +1280,6 @@ void launch_forest(Ctx& c, int l, int hdp)
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
         a.passes = 2;
         a.crit_first = 1;
-        a.WIN = 4096;
         if (hdp) launch_risky(a, c);   // risky: both passes, windowed, in one CTA
     }
     k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
