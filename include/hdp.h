@@ -290,8 +290,16 @@ enum {
     HDP_STAGE_PIX_SET = 12,   /* int32 [N]: row of the table used by each pixel */
     HDP_STAGE_COSTS = 13,     /* float [K]: aggregated cost, pixel-major, labels ascending */
     HDP_STAGE_DISP = 14,      /* int32 [N]: D_l */
-    HDP_STAGE_INFO = 15       /* int64 [16]: K_l, edge count, tree count, engine, ... */
+    HDP_STAGE_INFO = 15       /* int64 [16]: K_l, edge count, tree count, engine, ... (below) */
 };
+/* HDP_STAGE_INFO of the layer whose tree is current: [0] K_l aggregated
+ * entries, [1] edges kept by DT-Rule 1, [2] trees, [3] forest engine (1
+ * Boruvka over the sorted list, 3 windows of the top layer, 4 hybrid
+ * first pass, 5 first pass by regions, 6 windows of a risky layer), [4]
+ * aggregation tiles, [5] 1 if the layer has a risky edge, [6] tour arcs,
+ * [7] weight classes (hybrid) or regions (region engine), [8] light-child
+ * links, [9] and [10] reservation or Boruvka rounds and windows of the
+ * windowed engines; the rest is zero. */
 int64_t hdp_stage_bytes(hdp_ctx* ctx, int level, int what);
 int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, size_t bytes);
 int hdp_set_stage(hdp_ctx* ctx, int level, int what, const void* h_src, size_t bytes);
