@@ -87,7 +87,64 @@ def _sequential(edges, wts, W, par, size, intw, kq, in_tree, crit):
         in_tree[e] = 1
 
 
-def _model_forest(W, H, order, wts, kq, window, max_classes):
+def _dr_window(win, wts, W, par, size, intw, kq, in_tree, switch_below):
+    """Reservation rounds as the kernel runs them (the earliest pending edge of
+    a tree holds its reservation; an edge holding both is decided on the
+    current state; a tree failing the criterion there is frozen), then, once a
+    round resolves fewer than switch_below edges, the rest in window order."""
+    w0 = min(int(wts[e]) for e in win)
+    frozen = set()
+    for e in win:
+        for r in (_find(par, v) for v in _ends(e, W)):
+            if (w0 - intw[r]) * size[r] > kq:
+                frozen.add(r)
+    pos = {e: i for i, e in enumerate(win)}   # reservations go by window position (the strict order)
+    live = list(win)
+    rnd = 0
+    while live:
+        roots, best = {}, {}
+        for e in live:
+            a, b = (_find(par, v) for v in _ends(e, W))
+            if a == b or a in frozen or b in frozen:
+                continue
+            roots[e] = (a, b)
+            best[a] = min(best.get(a, pos[e]), pos[e])
+            best[b] = min(best.get(b, pos[e]), pos[e])
+        done = set(e for e in live if e not in roots)
+        resolved = 0
+        for e, (a, b) in roots.items():
+            ha, hb = best[a] == pos[e], best[b] == pos[e]
+            if not (ha or hb):
+                continue
+            w = int(wts[e])
+            fa = ha and (w - intw[a]) * size[a] > kq
+            fb = hb and (w - intw[b]) * size[b] > kq
+            if fa or fb:
+                if fa:
+                    frozen.add(a)
+                if fb:
+                    frozen.add(b)
+                done.add(e)
+                resolved += 1
+                continue
+            if not (ha and hb):
+                continue
+            if size[a] < size[b]:
+                a, b = b, a
+            par[b] = a
+            size[a] += size[b]
+            intw[a] = w
+            in_tree[e] = 1
+            done.add(e)
+            resolved += 1
+        live = [e for e in live if e not in done]
+        if live and rnd >= 1 and resolved < switch_below:
+            _sequential(live, wts, W, par, size, intw, kq, in_tree, crit=True)
+            return
+        rnd += 1
+
+
+def _model_forest(W, H, order, wts, kq, window, max_classes, switch_below=0):
     N = W * H
     par = list(range(N))
     size = [1] * N
@@ -99,6 +156,8 @@ def _model_forest(W, H, order, wts, kq, window, max_classes):
         if len(set(ws)) <= max_classes:
             for w in sorted(set(ws)):
                 _class_boruvka([e for e in win if wts[e] == w], w, W, par, size, intw, kq, in_tree)
+        elif switch_below:
+            _dr_window(win, wts, W, par, size, intw, kq, in_tree, switch_below)
         else:
             _sequential(win, wts, W, par, size, intw, kq, in_tree, crit=True)
     _sequential([int(e) for e in order], wts, W, par, size, intw, kq, in_tree, crit=False)   # linking pass
@@ -121,3 +180,20 @@ def test_class_by_class_windows_equal_sequential_kruskal(seed):
         for window, max_classes in ((8, 2), (16, 3), (32, 4), (len(order), 64)):
             got = _model_forest(W, H, order, wts, k, window, max_classes)
             assert np.array_equal(got, want), (seed, k, window)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_reservation_rounds_with_sequential_finish_equal_sequential_kruskal(seed):
+    # windows of many weight classes: reservation rounds, then the rest of the
+    # window in order once a round resolves few edges (the sequential finish)
+    rng = np.random.default_rng(100 + seed)
+    W, H = int(rng.integers(14, 24)), int(rng.integers(10, 18))
+    img = rng.integers(0, 64, size=(H, W, 3)).astype(np.int32)
+    wts = oracle.edge_weights(img)
+    order = oracle.sort_edges(wts, W, H)
+    pix = np.tile(oracle.full_set(3), (W * H, 1))
+    for k in (3, 30, 300):
+        want, _, _ = oracle.build_forest(W, H, order, wts, pix, tree="st", st_k=k, level=0)
+        for window, switch_below in ((16, 1), (32, 2), (64, 4), (len(order), 8)):
+            got = _model_forest(W, H, order, wts, k, window, max_classes=0, switch_below=switch_below)
+            assert np.array_equal(got, want), (seed, k, window, switch_below)
