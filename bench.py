@@ -127,13 +127,21 @@ def dist_init():
 
 
 def reduce_max(x, ws):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ws, units_per_rank, max_step_ms):
+    """Whole-job throughput in millions of units per second: every rank's
+    units over the slowest rank's time (replicas, weak scaling)."""
+    return ws * units_per_rank / (max_step_ms / 1000.0) / 1e6
 
 
 def barrier(ws):
@@ -408,7 +416,7 @@ def main():
     step_ms = float(np.sum(head["step_ms"]))
     step_ms = reduce_max(step_ms, ws) / args.steps
     Ktot = sum(head["K"])
-    value = ws * Ktot / (step_ms / 1000.0) / 1e6
+    value = job_value(ws, Ktot, step_ms)
     dims = hdp.Context(None, head_p).dims
     hbm, peak_kind = peaks()
     agg_ms = float(np.mean(head["agg_ms"]))
