@@ -190,6 +190,7 @@ def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=Fa
             clk = ck.stop() if ck else None
             step_ms = [a.elapsed_time(b) for a, b in ev]
             D_dev = out.cpu().numpy()
+            maps = {l: hdp.hdp_get_stage(ctx, l, "disp") for l in range(len(K))}
         e2e = None
         if want_e2e:
             hdp.hdp_set_timing(ctx, False)
@@ -210,7 +211,7 @@ def run_variant(hdp, torch, params, pair, steps, warmup, flush, dev, want_e2e=Fa
                 costs = hdp.hdp_get_stage(ctx, ctx_top, "costs")
         return dict(K=K, step_ms=step_ms, agg_ms=agg_ms, stage_ms=np.mean(stage_ms, 0), n_kernels=n_kernels,
                     costs=costs,
-                    e2e=e2e, clocks=clk, D=D_dev)
+                    e2e=e2e, clocks=clk, D=D_dev, maps=maps)
     finally:
         hdp.hdp_destroy(ctx)
 
@@ -338,7 +339,10 @@ def agg_bytes(K, dims, b):
     return sum(5 * b * k + 32 * (w * h) for k, (w, h, _) in zip(K, dims))
 
 
-def cpu_baseline(pair, params_full_hdp, crop=None):
+GAP_TOL = 1e-6   # a WTA difference is a near tie where the oracle's relative top-two gap is below this
+
+
+def cpu_baseline(pair, params_full_hdp, crop=None, want_recs=False):
     from oracle.pipeline import OracleParams, match
     left, right = pair.left, pair.right
     if crop:
@@ -348,7 +352,31 @@ def cpu_baseline(pair, params_full_hdp, crop=None):
     _, recs = match(np.ascontiguousarray(left), np.ascontiguousarray(right), op, keep=True)
     dt = time.perf_counter() - t0
     K = sum(int(r["agg"]["row_off"][-1]) for r in recs.values())
-    return K, dt
+    return (K, dt, recs) if want_recs else (K, dt)
+
+
+def oracle_agreement(maps, recs):
+    """The GPU's maps of a whole run against the oracle's whole run, layer by layer from the top.
+
+    While every upper layer agrees, a layer sees identical inputs on both sides: its differences must be
+    near ties of the oracle (top-two gap < GAP_TOL).  Below the first layer with any difference the
+    predicted ranges differ, so those layers are counted but not judged."""
+    layers, unexplained = [], 0
+    comparable = True
+    for l in sorted(recs, reverse=True):
+        o = recs[l]["agg"]
+        diff = np.flatnonzero(np.asarray(maps[l]).ravel() != o["wta"])
+        gap = (o["second"][diff] - o["best"][diff]) / np.maximum(np.abs(o["best"][diff]), 1e-30)
+        near = int((gap < GAP_TOL).sum())
+        layers.append({"layer": l, "pixels": int(o["wta"].size), "mismatch": int(diff.size), "near_ties": near,
+                       "max_gap_of_mismatch": float(gap.max()) if diff.size else None,
+                       "inputs_identical": comparable})
+        if comparable:
+            unexplained += int(diff.size) - near
+        if diff.size:
+            comparable = False
+    return {"oracle_mismatch": layers[-1]["mismatch"], "oracle_near_ties": layers[-1]["near_ties"],
+            "unexplained": unexplained, "gap_tol": GAP_TOL, "per_layer": layers}
 
 
 def main():
@@ -464,11 +492,13 @@ def main():
         batch = run_batch(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush, rank)
         grad = run_grad(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush)
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        Kc, tc = cpu_baseline(pair, None)
+        Kc, tc, recs = cpu_baseline(pair, None, want_recs=True)
         cpu = {"value": Kc / tc / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one whole pair (all 5 layers, {Kc} entries) in {tc:.1f} s, FP64, single thread"}
+        if args.variant == "hdp_st_fp32":
+            parity = oracle_agreement(head["maps"], recs)
 
     if rank != 0:
         return
@@ -485,6 +515,7 @@ def main():
                      "traffic": agg_traffic(WORKLOAD) if args.variant == "hdp_st_fp32" else None,
                      "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
         "cpu_baseline": cpu,
+        "oracle_parity": parity,
         "e2e": ({"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                  "ms_per_pair": 1000 * e2e["seconds"]} if e2e else None),
         "bad_pixel_rate": bad_pixels(head["D"], pair),

@@ -20,7 +20,8 @@
  *   - Every call returns an hdp_status and never aborts the process.  Errors
  *     raised asynchronously on the device (including a bounded wait that ran
  *     out, HDP_ERR_TIMEOUT) are reported by the next call that synchronises
- *     (hdp_sync, the *_host calls, hdp_get_stage) or by hdp_destroy.
+ *     (hdp_sync, the *_host calls, hdp_get_stage) or by hdp_destroy;
+ *     hdp_sync clears a device-side error once it has reported it.
  *     hdp_last_error returns a text description of the last failure.
  *   - A context is not thread-safe; distinct contexts are independent.
  */
@@ -190,6 +191,17 @@ int hdp_sync(hdp_ctx* ctx);
 int hdp_destroy(hdp_ctx* ctx);
 const char* hdp_last_error(const hdp_ctx* ctx);
 
+/* Failure-path check (tests and tools; no counterpart in the paper): enqueue
+ * on the context's stream one of the library's bounded device waits, made to
+ * run out after `limit` polls (1..2^24) on something that never arrives -
+ * kind 0 a grid barrier that counts one block more than its grid has, kind 1
+ * a decoupled look-back on a predecessor tile that never publishes.  The
+ * wait gives up, records the timeout and its kernel returns; nothing but the
+ * status block is written.  The next hdp_sync returns HDP_ERR_TIMEOUT and
+ * clears the status, after which the context is usable again.  HDP_ERR_ARG
+ * for another kind or limit. */
+int hdp_wait_probe(hdp_ctx* ctx, int kind, unsigned limit);
+
 /* Device time of each stage, recorded with CUDA events on the context's
  * stream while timing is on.  hdp_get_timings synchronises and writes
  * ms[level * 5 + k] for k = 0 interval prediction, 1 edges + sort, 2 forest,
@@ -251,19 +263,26 @@ int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const 
  * graph-building framework, a real-time loop, a plug-in that owns no
  * allocator).  The paper has no counterpart; this is an interface of this
  * library only.
- *   - The workspace is a fixed 64 MiB device array inside the library
- *     (held by every GPU that loads the library, until the process exits).
- *     Problems whose workspace exceeds it (roughly above 256x256 pixels with
+ *   - The workspace is a fixed 64 MiB device array inside the library.  With
+ *     lazy module loading (the CUDA default) a device reserves it when the
+ *     library's module is first loaded there, which is this call's first
+ *     call on that device; that first call can therefore fail with
+ *     HDP_ERR_OOM or HDP_ERR_CUDA.  Make it once at set-up time, not where
+ *     allocation is forbidden.  The array stays reserved on that device
+ *     until the process exits.
+ *   - Problems whose workspace exceeds it (roughly above 256x256 pixels with
  *     max_disp 63, FP32) are rejected with HDP_ERR_ARG and a message.
  *   - d_left/d_right (interleaved RGB uint8, row pitch `pitch` bytes) and
  *     d_disp_out (int32 [height][width]) are the caller's device buffers;
  *     `stream` is a cudaStream_t (NULL = legacy default stream).
  *   - The first call on a device, with that device current, looks up the
- *     array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.  Each call synchronises the stream once,
- *     after uploading a few hundred bytes of constants, then enqueues the
- *     pipeline and returns; device-side errors surface at the caller's next
- *     synchronisation.
+ *     array's device address (cudaGetSymbolAddress).
+ *   - The call is synchronous: it waits once after uploading a few hundred
+ *     bytes of constants and again after the pipeline, then reads the
+ *     device status, so a bounded device wait that gave up returns
+ *     HDP_ERR_TIMEOUT and an invalid device input HDP_ERR_ARG.  It cannot be
+ *     captured in a CUDA graph: on a stream under capture it returns
+ *     HDP_ERR_STATE and does nothing.
  *   - Every call uses the same array: calls that overlap on the GPU (two
  *     streams, two host threads) race and corrupt each other's results.
  *   - It calls no cudaMalloc, cudaFree or other allocating routine. */

@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
         "hdp_match_host": (I, [P, P, P, P]),
         "hdp_run_level": (I, [P, I]),
         "hdp_sync": (I, [P]),
+        "hdp_wait_probe": (I, [P, I, ctypes.c_uint]),
         "hdp_destroy": (I, [P]),
         "hdp_last_error": (ctypes.c_char_p, [P]),
         "hdp_stage_bytes": (I64, [P, I, I]),
@@ -188,10 +189,37 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _image(t, params):
+    """A device image of this problem: contiguous torch.uint8 (height, width, 3) on a CUDA device."""
+    import torch
+    want = (params.height, params.width, 3)
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or tuple(t.shape) != want:
+        raise TypeError(f"expected a torch.uint8 tensor of shape {want}")
+    return _ptr(t)
+
+
+def _dmap(t, params):
+    """A device disparity map of this problem: contiguous torch.int32 (height, width) on a CUDA device."""
+    import torch
+    want = (params.height, params.width)
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or tuple(t.shape) != want:
+        raise TypeError(f"expected a torch.int32 tensor of shape {want}")
+    return _ptr(t)
+
+
+def _stream(stream):
+    """The cudaStream_t of `stream`; None means torch's current stream."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
 def hdp_create(params: HDPParams, stream=None) -> Context:
+    """A context bound to `stream` (torch's current stream when None)."""
     L = load()
     h = ctypes.c_void_p()
-    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    s = _stream(stream)
     cp = params.to_c()
     rc = L.hdp_create(ctypes.byref(cp), s, ctypes.byref(h))
     if rc != HDP_OK:
@@ -231,7 +259,8 @@ def hdp_autotune(ctx: Context, left, right, reps: int = 2) -> Tuning:
     """Coordinate descent over the launch-shape knobs on this pair (device images)."""
     t = Tuning()
     W = ctx.params.width
-    _check(ctx, load().hdp_autotune(ctx.handle, _ptr(left), _ptr(right), 3 * W, int(reps), ctypes.byref(t)),
+    _check(ctx, load().hdp_autotune(ctx.handle, _image(left, ctx.params), _image(right, ctx.params), 3 * W, int(reps),
+                                    ctypes.byref(t)),
            "hdp_autotune")
     return t
 
@@ -243,20 +272,25 @@ def hdp_workspace_bytes(ctx: Context) -> int:
 def hdp_build_trees(ctx: Context, left, right):
     """left, right: torch.uint8 (H, W, 3) contiguous CUDA tensors."""
     W = ctx.params.width
-    _check(ctx, load().hdp_build_trees(ctx.handle, _ptr(left), _ptr(right), 3 * W), "hdp_build_trees")
+    _check(ctx, load().hdp_build_trees(ctx.handle, _image(left, ctx.params), _image(right, ctx.params), 3 * W),
+           "hdp_build_trees")
 
 
 def hdp_match(ctx: Context, out):
     """out: torch.int32 (H, W) contiguous CUDA tensor."""
-    _check(ctx, load().hdp_match(ctx.handle, _ptr(out)), "hdp_match")
+    _check(ctx, load().hdp_match(ctx.handle, _dmap(out, ctx.params)), "hdp_match")
 
 
 def hdp_match_host(ctx: Context, left: np.ndarray, right: np.ndarray, out: np.ndarray = None) -> np.ndarray:
     H, W = ctx.params.height, ctx.params.width
     left = np.ascontiguousarray(left, np.uint8)
     right = np.ascontiguousarray(right, np.uint8)
+    if left.shape != (H, W, 3) or right.shape != (H, W, 3):
+        raise TypeError(f"expected uint8 images of shape {(H, W, 3)}")
     if out is None:
         out = np.empty((H, W), np.int32)
+    if out.shape != (H, W) or out.dtype != np.int32 or not out.flags.c_contiguous:
+        raise TypeError(f"expected a contiguous int32 output of shape {(H, W)}")
     _check(ctx, load().hdp_match_host(ctx.handle, left.ctypes.data, right.ctypes.data, out.ctypes.data),
            "hdp_match_host")
     return out
@@ -268,6 +302,11 @@ def hdp_run_level(ctx: Context, level: int):
 
 def hdp_sync(ctx: Context):
     _check(ctx, load().hdp_sync(ctx.handle), "hdp_sync")
+
+
+def hdp_wait_probe(ctx: Context, kind: int, limit: int):
+    """Enqueue a bounded device wait made to run out (0: grid barrier, 1: look-back); hdp_sync then raises."""
+    _check(ctx, load().hdp_wait_probe(ctx.handle, int(kind), int(limit)), "hdp_wait_probe")
 
 
 def hdp_destroy(ctx: Context):
@@ -318,8 +357,9 @@ def hdp_get_timings(ctx: Context) -> np.ndarray:
 def hdp_graph_capture(ctx: Context, left, right, out) -> int:
     """Capture build + match on these device buffers as a CUDA graph; returns its kernel count."""
     n = ctypes.c_int(0)
-    _check(ctx, load().hdp_graph_capture(ctx.handle, _ptr(left), _ptr(right), 3 * ctx.params.width, _ptr(out),
-                                         ctypes.byref(n)), "hdp_graph_capture")
+    _check(ctx, load().hdp_graph_capture(ctx.handle, _image(left, ctx.params), _image(right, ctx.params),
+                                         3 * ctx.params.width, _dmap(out, ctx.params), ctypes.byref(n)),
+           "hdp_graph_capture")
     return n.value
 
 
@@ -331,11 +371,15 @@ NOALLOC_BYTES = 64 << 20
 
 
 def hdp_match_noalloc(params: HDPParams, left, right, out, stream=None):
-    """Match without allocating: the workspace is a fixed 64 MiB array inside
-    libhdp.so (see include/hdp.h).  Calls that overlap on the GPU race."""
+    """Match without allocating device memory, for callers that may not
+    allocate: the workspace is a fixed 64 MiB array inside libhdp.so (see
+    include/hdp.h).  Runs on `stream` (torch's current stream when None) and
+    returns when the map is written; raises HDPError with the C status (for
+    example HDP_ERR_TIMEOUT when a bounded device wait gave up).  Calls that
+    overlap on the GPU race, and the call cannot be graph-captured."""
     cp = params.to_c()
-    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
-    rc = load().hdp_match_noalloc(ctypes.byref(cp), _ptr(left), _ptr(right), 3 * params.width, _ptr(out), s)
+    rc = load().hdp_match_noalloc(ctypes.byref(cp), _image(left, params), _image(right, params), 3 * params.width,
+                                  _dmap(out, params), _stream(stream))
     if rc != HDP_OK:
         raise HDPError(f"hdp_match_noalloc failed ({rc})")
 
@@ -367,10 +411,12 @@ def hdp_soft_argmin_l1(ctx: Context, C, gt=None, valid=None, T=1.0, disp=None, l
 def _batch_arrays(ctxs, lefts, rights, outs):
     n = len(ctxs)
     H = (ctypes.c_void_p * n)(*[c.handle for c in ctxs])
-    L = (ctypes.c_void_p * n)(*[t.data_ptr() for t in lefts])
-    R = (ctypes.c_void_p * n)(*[t.data_ptr() for t in rights])
+    if not (len(lefts) == len(rights) == len(outs) == n):
+        raise TypeError("one left image, right image and output per context")
+    L = (ctypes.c_void_p * n)(*[_image(t, c.params).value for t, c in zip(lefts, ctxs)])
+    R = (ctypes.c_void_p * n)(*[_image(t, c.params).value for t, c in zip(rights, ctxs)])
     Pt = (ctypes.c_int * n)(*[3 * c.params.width for c in ctxs])
-    O = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    O = (ctypes.c_void_p * n)(*[_dmap(t, c.params).value for t, c in zip(outs, ctxs)])
     return n, H, L, R, Pt, O
 
 
@@ -395,7 +441,7 @@ def exported_symbols():
     """Names declared in include/hdp.h (for the load/export check)."""
     return ["hdp_default_params", "hdp_create", "hdp_create_own_stream", "hdp_get_stream", "hdp_get_tuning",
             "hdp_set_tuning", "hdp_autotune", "hdp_workspace_bytes", "hdp_build_trees", "hdp_match",
-            "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
+            "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_wait_probe", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
             "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch"]

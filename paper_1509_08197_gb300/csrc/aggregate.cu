@@ -220,9 +220,10 @@ __device__ __forceinline__ int tile_of_row(const AggArgs& a, int r) { return (in
 __device__ __forceinline__ int wait_flag(const AggArgs& a, int* f)
 {
     unsigned it = 0;
+    const unsigned cap = spin_cap(a.st);
     int v;
     while ((v = *(volatile int*)f) == 0) {
-        if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+        if (++it > cap || dev_err(a.st)) {
             dev_fail(a.st, DEV_TIMEOUT, 50);
             return -1;
         }
@@ -235,8 +236,9 @@ __device__ __forceinline__ int wait_flag(const AggArgs& a, int* f)
 __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 {
     unsigned it = 0;
+    const unsigned cap = spin_cap(a.st);
     while (*(volatile int*)f != 2) {
-        if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+        if (++it > cap || dev_err(a.st)) {
             dev_fail(a.st, DEV_TIMEOUT, 52);
             return;
         }
@@ -548,7 +550,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
                 off += 32;                          // 32 aggregates: keep walking
                 continue;
             }
-            if (++it > HDP_SPIN_LIMIT || dev_err(a.st)) {
+            if (++it > spin_cap(a.st) || dev_err(a.st)) {
                 dev_fail(a.st, DEV_TIMEOUT, 51);
                 break;
             }

@@ -22,9 +22,18 @@ struct DevStatus {
     unsigned int bar_gen;
     int err;
     int where;
+    // polls before a grid barrier or a look-back wait gives up; 0 means
+    // HDP_SPIN_LIMIT.  Waits for bulk copies in flight keep HDP_SPIN_LIMIT.
+    unsigned int spin_limit;
 };
 
 __device__ __forceinline__ int dev_err(const DevStatus* st) { return *(volatile const int*)&st->err; }
+
+__device__ __forceinline__ unsigned spin_cap(const DevStatus* st)
+{
+    const unsigned c = *(volatile const unsigned*)&st->spin_limit;
+    return c ? c : HDP_SPIN_LIMIT;
+}
 
 __device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where)
 {
@@ -47,9 +56,10 @@ __device__ __forceinline__ bool grid_sync(DevStatus* st, unsigned nblocks)
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
+            const unsigned cap = spin_cap(st);
             unsigned it = 0;
             while (*vgen == g) {
-                if (++it > HDP_SPIN_LIMIT || dev_err(st)) {
+                if (++it > cap || dev_err(st)) {
                     dev_fail(st, DEV_TIMEOUT, 1);
                     break;
                 }

@@ -184,6 +184,7 @@ static void layout_buffers(Ctx& c)
     c.nfull = carve<float>(c, N0);
     c.ints = carve<int>(c, IDX_COUNT);
     c.st = carve<DevStatus>(c, 1);
+    c.zero64 = carve<unsigned long long>(c, 4);
     c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
     c.tmp = carve<uint32_t>(c, c.tmp_words);
     c.hist = carve<unsigned long long>(c, HDP_MAX_LEVELS * 256);
@@ -329,6 +330,7 @@ extern "C" int hdp_create(const hdp_params* p, void* stream, hdp_ctx** out)
     TRY_CUDA(cudaMemcpy(c.full_mask, hc.fm, sizeof(hc.fm), cudaMemcpyHostToDevice));
     TRY_CUDA(cudaMemset(c.st, 0, sizeof(DevStatus)));
     TRY_CUDA(cudaMemset(c.ints, 0, sizeof(int) * IDX_COUNT));
+    TRY_CUDA(cudaMemset(c.zero64, 0, 4 * sizeof(unsigned long long)));
     c.scan.st = c.st;
     c.scan4.st = c.st;
     TRY_CUDA(cudaMemset(c.scan.state, 0, sizeof(unsigned long long) * c.scan.max_tiles));
@@ -448,9 +450,23 @@ extern "C" int hdp_sync(hdp_ctx* ctx)
     if (c.s2) TRY_CUDA(cudaStreamSynchronize(c.s2));
     DevStatus st;
     TRY_CUDA(cudaMemcpy(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.err == DEV_OK) return HDP_OK;
+    // report once, then clear the status block (error, barrier counter and
+    // generation) so that the next call on this context starts clean
+    TRY_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
+    TRY_CUDA(cudaStreamSynchronize(c.s));
     if (st.err == DEV_TIMEOUT) return fail(ctx, HDP_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(st.where) + ")");
-    if (st.err == DEV_BAD_INPUT) return fail(ctx, HDP_ERR_ARG, "invalid device input (site " + std::to_string(st.where) + ")");
-    return HDP_OK;
+    return fail(ctx, HDP_ERR_ARG, "invalid device input (site " + std::to_string(st.where) + ")");
+}
+
+extern "C" int hdp_wait_probe(hdp_ctx* ctx, int kind, unsigned limit)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    if (kind < 0 || kind > 1 || limit < 1 || limit > HDP_SPIN_LIMIT)
+        return fail(ctx, HDP_ERR_ARG, "hdp_wait_probe: kind must be 0 or 1 and limit in 1..2^24");
+    Ctx& c = ctx->c;
+    launch_wait_probe(kind, limit, c.zero64, c.st, c.s);
+    return check_launch(ctx, "hdp_wait_probe");
 }
 
 // ------------------------------------------------------------ tuning ---
@@ -896,7 +912,16 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
                                  int32_t* d_disp_out, void* stream)
 {
     if (!p || !d_left || !d_right || !d_disp_out) return HDP_ERR_ARG;
-    hdp_ctx local;   // on the stack: no host or device allocation
+    {
+        // the call synchronises its stream twice, which a stream under capture forbids
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            fprintf(stderr, "hdp_match_noalloc: the stream is being captured; this call cannot be captured\n");
+            return HDP_ERR_STATE;
+        }
+    }
+    hdp_ctx local;   // on the stack: no device allocation
     hdp_ctx* ctx = &local;
     Ctx& c = ctx->c;
     c.s = (cudaStream_t)stream;
@@ -948,6 +973,10 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
     TRY_CUDA(cudaStreamSynchronize(c.s));
     int rc = hdp_build_trees(ctx, d_left, d_right, pitch);
     if (!rc) rc = hdp_match(ctx, d_disp_out);
+    // wait for the work and read its device status (a bounded wait that gave
+    // up, an invalid device input): the status block lives in the shared
+    // array, so this call is the only one that can report it
+    if (!rc) rc = hdp_sync(ctx);
     if (rc) {
         fprintf(stderr, "hdp_match_noalloc: %s\n", c.err.c_str());
         return rc;

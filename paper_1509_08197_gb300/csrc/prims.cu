@@ -92,6 +92,7 @@ __device__ __forceinline__ uint32_t lookback_u32(const unsigned long long* stp, 
     const int lane = threadIdx.x & 31;
     uint32_t pre = 0;
     unsigned it = 0;
+    const unsigned cap = spin_cap(st);
     for (int j0 = tile - 1; j0 >= 0;) {
         const int j = j0 - lane;
         const unsigned long long w = j >= 0 ? *(volatile const unsigned long long*)(stp + j) : (2ull << 32);
@@ -100,7 +101,7 @@ __device__ __forceinline__ uint32_t lookback_u32(const unsigned long long* stp, 
         const int k = incl ? __ffs(incl) - 1 : 31;
         const unsigned need = k == 31 ? FULL : (2u << k) - 1u;   // lanes 0..k
         if (none & need) {
-            if (++it > HDP_SPIN_LIMIT || dev_err(st)) {
+            if (++it > cap || dev_err(st)) {
                 if (lane == 0) dev_fail(st, DEV_TIMEOUT, where);
                 break;
             }
@@ -123,6 +124,7 @@ __device__ __forceinline__ I4 lookback_i4(const ScanStateI4& ss, int tile, int w
     const int lane = threadIdx.x & 31;
     I4 pre = I4{0, 0, 0, 0};
     unsigned it = 0;
+    const unsigned cap = spin_cap(ss.st);
     for (int j0 = tile - 1; j0 >= 0;) {
         const int j = j0 - lane;
         const unsigned f = j >= 0 ? *(volatile const unsigned*)(ss.flags + j) : 2u;
@@ -130,7 +132,7 @@ __device__ __forceinline__ I4 lookback_i4(const ScanStateI4& ss, int tile, int w
         const int k = incl ? __ffs(incl) - 1 : 31;
         const unsigned need = k == 31 ? FULL : (2u << k) - 1u;
         if (none & need) {
-            if (++it > HDP_SPIN_LIMIT || dev_err(ss.st)) {
+            if (++it > cap || dev_err(ss.st)) {
                 if (lane == 0) dev_fail(ss.st, DEV_TIMEOUT, where);
                 break;
             }
@@ -364,4 +366,29 @@ void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool
     if (n_max <= 0) return;
     const int nb = (int)cdiv<long long>(n_max, SCAN_TILE);
     k_scan1_u32<<<nb, SCAN_THREADS, 0, s>>>(in, out, d_n, exclusive ? 1 : 0, ss, total);
+}
+
+// ------------------------------------------------------ wait probes ---
+// Drive one of the library's bounded waits into its limit on purpose: kind 0
+// is a grid barrier that counts one block more than the grid has (the
+// missing block never arrives), kind 1 a decoupled look-back on tile 1 whose
+// predecessor's flag (zero[0], which nothing writes) never gets published.
+// Both give up after st->spin_limit polls, record DEV_TIMEOUT and return;
+// nothing is written but the status block.
+__global__ void k_set_spin_limit(DevStatus* st, unsigned v) { st->spin_limit = v; }
+
+__global__ void k_wait_probe(int kind, const unsigned long long* zero, DevStatus* st)
+{
+    if (kind == 0) {
+        grid_sync(st, gridDim.x + 1);
+    } else if (blockIdx.x == 0 && threadIdx.x < 32) {
+        lookback_u32(zero, 1, st, 90);
+    }
+}
+
+void launch_wait_probe(int kind, unsigned limit, const unsigned long long* zero, DevStatus* st, cudaStream_t s)
+{
+    k_set_spin_limit<<<1, 1, 0, s>>>(st, limit);
+    k_wait_probe<<<kind == 0 ? 4 : 1, 32, 0, s>>>(kind, zero, st);
+    k_set_spin_limit<<<1, 1, 0, s>>>(st, 0u);
 }

@@ -206,4 +206,7 @@ void scan_u32(const uint32_t* in, uint32_t* out, const int* d_n, int n_max, bool
               uint32_t* total, cudaStream_t s);
 int scan_state_tiles(int n_max);
 __global__ void k_set_int(int* out, int v);
+// Enqueue a wait that is made to run out after `limit` polls (kind 0: grid
+// barrier, 1: look-back); see prims.cu.  zero: a zeroed device word.
+void launch_wait_probe(int kind, unsigned limit, const unsigned long long* zero, DevStatus* st, cudaStream_t s);
 size_t scan_tmp_words(int n_max);
