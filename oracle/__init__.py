@@ -63,6 +63,8 @@ def _declare(L):
         "orc_cost_mq": (I64, [P, P, P, P, I, I, I, I, I, I, I, I]),
         "orc_edge_weights": (I, [P, I, I, P]),
         "orc_sort_edges": (I, [P, I, I, P]),
+        "orc_splitmix64": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
+        "orc_sort_edges_rt": (I, [P, I, I, ctypes.c_uint64, I, P]),
         "orc_build_forest": (I, [I, I, P, I, P, P, I, I, I, I64, I, P, P, P]),
         "orc_bfs": (I, [I, I, P, P, P, P]),
         "orc_aggregate": (I, [I, I, I, I, P, P, P, P, D, D, D, D, P, P, P, P, P, P, P, P, P]),
@@ -131,6 +133,21 @@ def sort_edges(w: np.ndarray, W: int, H: int) -> np.ndarray:
     w = _c(w, np.int64)
     order = np.empty(2 * W * H, np.int32)
     n = lib().orc_sort_edges(_p(w), W, H, _p(order))
+    return order[:n].copy()
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """The i-th output of SplitMix64 from state `seed` (the random tree's generator)."""
+    return int(lib().orc_splitmix64(seed & (2 ** 64 - 1), i & (2 ** 64 - 1)))
+
+
+def sort_edges_rt(w: np.ndarray, W: int, H: int, seed: int, level: int) -> np.ndarray:
+    """Random-tree order (Sec. 4.1): valid edges by (31-bit SplitMix64 key, id)."""
+    w = _c(w, np.int64)
+    order = np.empty(2 * W * H, np.int32)
+    n = lib().orc_sort_edges_rt(_p(w), W, H, seed & (2 ** 64 - 1), int(level), _p(order))
+    if n < 0:
+        raise MemoryError("orc_sort_edges_rt")
     return order[:n].copy()
 
 

@@ -172,6 +172,54 @@ int orc_sort_edges(const int64_t* w, int W, int H, int32_t* order)
     return n;
 }
 
+/* Random spanning tree, RT (Sec. 4.1): the edges are shuffled at random and
+ * the same union-find construction takes them in that order.  Reading: the
+ * shuffle is the order of a counter-based random key per edge, ties (equal
+ * keys) broken by edge id.  The key of edge e at layer l is the top 31 bits
+ * of the i-th output of SplitMix64 started from state `seed`, with
+ * i = l * 2^32 + e + 1; SplitMix64 is the generator of Steele, Lea and Flood,
+ * "Fast splittable pseudorandom number generators" (OOPSLA 2014): the state
+ * advances by the odd constant 0x9E3779B97F4A7C15 and each output is the
+ * state passed through two xor-shift-multiply rounds and a final xor-shift.  */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static uint32_t rt_key(uint64_t seed, int level, int64_t e)
+{
+    return (uint32_t)(orc_splitmix64(seed, ((uint64_t)level << 32) + (uint64_t)e + 1u) >> 33);
+}
+
+static const uint32_t* g_rt_key;
+static int cmp_rt(const void* A, const void* B)
+{
+    int32_t a = *(const int32_t*)A, b = *(const int32_t*)B;
+    if (g_rt_key[a] != g_rt_key[b]) return g_rt_key[a] < g_rt_key[b] ? -1 : 1;
+    return (a > b) - (a < b);
+}
+
+/* Rule 1 of the random tree: every valid edge in increasing (key, id) order;
+ * returns the number written to `order` (key: scratch of 2*W*H words). */
+int orc_sort_edges_rt(const int64_t* w, int W, int H, uint64_t seed, int level, int32_t* order)
+{
+    const int64_t n2 = 2 * (int64_t)W * H;
+    uint32_t* key = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n2 > 0 ? n2 : 1));
+    if (!key) return -1;
+    int n = 0;
+    for (int64_t e = 0; e < n2; ++e) {
+        key[e] = rt_key(seed, level, e);
+        if (w[e] >= 0) order[n++] = (int32_t)e;
+    }
+    g_rt_key = key;
+    qsort(order, (size_t)n, sizeof(int32_t), cmp_rt);
+    free(key);
+    return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sets of disparity labels (PixelIntv / TreeIntv, Sec. 3.1-3.2) as 256-bit
  * masks; |.| is the number of labels in the set.                            */

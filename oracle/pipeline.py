@@ -18,14 +18,14 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (aggregate, bfs, build_forest, edge_weights, full_set, gradient, pixel_intervals, prior,
-               pyr_down, range_table, sort_edges, to_level0)
+               pyr_down, range_table, sort_edges, sort_edges_rt, to_level0)
 
 
 @dataclass
 class OracleParams:
     max_disp: int
     levels: int = 2                 # number of layers, L + 1
-    tree: str = "mst"               # "mst" | "st"
+    tree: str = "mst"               # "mst" | "st" | "rt" (random spanning tree, Sec. 4.1)
     mode: str = "hdp"               # "hdp" | "full" (single layer, full range)
     gamma: float = 25.5             # Eq. S, 0.1 * 255
     alpha: float = 0.9              # cost weights ([Cost2])
@@ -36,6 +36,13 @@ class OracleParams:
     delta0: float = 0.064           # delta_l = delta0 * 2^l
     gmm: list = field(default_factory=list)   # per predicted layer: [[pi, mu, sd], ...]
     prior: str = "sampled"          # "sampled" | "uniform"
+    rt_seed: int = 0                # seed of the random tree's edge order
+
+    def edge_order(self, w, W, H, level):
+        """Rule 1: (w, id) order for MST and ST; the seeded random order for RT."""
+        if self.tree == "rt":
+            return sort_edges_rt(w, W, H, self.rt_seed, level)
+        return sort_edges(w, W, H)
 
     def gmm_for(self, l):
         if l < len(self.gmm) and self.gmm[l] is not None:
@@ -84,7 +91,7 @@ def match(left: np.ndarray, right: np.ndarray, p: OracleParams, keep: bool = Fal
             pix = pixel_intervals(W, H, D_up, masks)
             rec.update(prior=pw, masks=masks)
         w = edge_weights(L)
-        order = sort_edges(w, W, H)
+        order = p.edge_order(w, W, H, l)
         in_tree, dt_root, tint = build_forest(W, H, order, w, pix, p.beta, p.tree, p.st_k, l)
         bfs_order, parent, depth = bfs(W, H, in_tree)
         agg = aggregate(L, gL, R, gR, l, d[l], bfs_order, parent, w, tint, p.gamma, p.alpha, p.tau_c, p.tau_g,

@@ -67,6 +67,7 @@ class HDPParams:
     prior: str = "sampled"
     gmm: list = field(default_factory=list)   # per predicted layer: [[pi, mu, sd], ...] or None
     storage: str = "fp32"
+    rt_seed: int = 0              # tree="rt": seed of the random edge order (Sec. 4.1)
 
     def to_c(self) -> _Params:
         large = self.width > 640

@@ -166,6 +166,65 @@ def test_forest_matches_naive_replay(tree):
         assert set(np.flatnonzero(in_tree).tolist()) == ref
 
 
+# ---------------------------------------------------------- random tree ---
+def test_splitmix64_known_outputs():
+    # published first outputs of SplitMix64 started from state 0
+    assert [oracle.splitmix64(0, i) for i in (1, 2, 3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                             0x06C45D188009454F]
+
+
+def test_rt_order_is_a_seeded_permutation_of_the_valid_edges():
+    rng = np.random.default_rng(21)
+    img = rng.integers(0, 50, size=(9, 13, 3)).astype(np.int32)
+    w = oracle.edge_weights(img)
+    a = oracle.sort_edges_rt(w, 13, 9, 7, 0)
+    assert sorted(a.tolist()) == np.flatnonzero(w >= 0).tolist()
+    assert np.array_equal(a, oracle.sort_edges_rt(w, 13, 9, 7, 0))           # seeded: reproducible
+    assert not np.array_equal(a, oracle.sort_edges_rt(w, 13, 9, 8, 0))       # another seed
+    assert not np.array_equal(a, oracle.sort_edges_rt(w, 13, 9, 7, 1))       # another layer
+    # the order ignores the weights: same permutation for any image of that size
+    w2 = oracle.edge_weights(rng.integers(0, 50, size=(9, 13, 3)).astype(np.int32))
+    assert np.array_equal(a, oracle.sort_edges_rt(w2, 13, 9, 7, 0))
+
+
+def test_rt_order_is_uncorrelated_with_ids_and_weights():
+    rng = np.random.default_rng(22)
+    img = rng.integers(0, 256, size=(60, 80, 3)).astype(np.int32)
+    w = oracle.edge_weights(img)
+    order = oracle.sort_edges_rt(w, 80, 60, 12345, 0)
+    rank = np.empty(order.size)
+    rank[np.argsort(order)] = np.arange(order.size)
+    ids = np.sort(order)
+    # Spearman correlation of the position with the id and with the weight: near 0 for a shuffle
+    assert abs(np.corrcoef(rank, np.arange(ids.size))[0, 1]) < 0.05
+    assert abs(np.corrcoef(rank, w[ids])[0, 1]) < 0.05
+
+
+def test_rt_forest_is_a_spanning_tree_and_matches_naive_replay():
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    rng = np.random.default_rng(23)
+    for trial in range(8):
+        H, W = int(rng.integers(2, 6)), int(rng.integers(2, 7))
+        img = rng.integers(0, 12, size=(H, W, 3)).astype(np.int32)
+        w = oracle.edge_weights(img)
+        order = oracle.sort_edges_rt(w, W, H, 1000 + trial, 0)
+        # one label set everywhere: a spanning tree of the grid (N - 1 edges, connected)
+        full = np.tile(oracle.full_set(15), (W * H, 1))
+        in_tree, root, _ = oracle.build_forest(W, H, order, w, full, (0, 1), "mst", 0, 0)
+        e = np.flatnonzero(in_tree)
+        assert e.size == W * H - 1
+        p = e >> 1
+        q = np.where(e & 1, p + W, p + 1)
+        g = coo_matrix((np.ones(e.size), (p, q)), shape=(W * H, W * H))
+        assert connected_components(g, directed=False)[0] == 1
+        # with predicted sets and DT-Rule 2: the naive label replay of the same order
+        pix, sets = _random_sets(rng, W * H)
+        beta = [(0, 1), (1, 2), (3, 5), (19, 20)][trial % 4]
+        in_tree, _, _ = oracle.build_forest(W, H, order, w, pix, beta, "mst", 0, 0)
+        assert set(np.flatnonzero(in_tree).tolist()) == brute.naive_forest(W, H, order, w, sets, beta, "mst", 0)
+
+
 def test_forest_hand_2x3_dt_rule1():
     # 0 1 2 / 3 4 5 ; pixels 0,1,3,4 predict {0,1}, pixels 2,5 predict {5,6}
     img = np.zeros((2, 3, 3), np.int32)
