@@ -46,7 +46,7 @@ typedef enum {
     HDP_ERR_STATE = -5     /* calls made in the wrong order */
 } hdp_status;
 
-enum { HDP_TREE_MST = 0, HDP_TREE_ST = 1 };
+enum { HDP_TREE_MST = 0, HDP_TREE_ST = 1, HDP_TREE_RT = 2 };
 enum { HDP_MODE_HDP = 0, HDP_MODE_FULL = 1 };
 enum { HDP_PRIOR_SAMPLED = 0, HDP_PRIOR_UNIFORM = 1 };
 enum { HDP_STORE_FP32 = 0, HDP_STORE_FP16 = 1 };
@@ -60,8 +60,14 @@ enum { HDP_STORE_FP32 = 0, HDP_STORE_FP16 = 1 };
  * 0..max_disp); 1 <= levels <= 8.
  *   levels  number of pyramid layers L+1 (Sec. 2.1, S = 2 fixed, as in Sec. 4.1);
  *           mode HDP_MODE_FULL ignores it and aggregates one full-range layer.
- *   tree    HDP_TREE_MST (the MST of [MST]) or HDP_TREE_ST (segment tree, [ST]):
- *           Kruskal merging w <= Int(C) + st_k/|C| for both trees, then linking.
+ *   tree    HDP_TREE_MST (the MST of [MST]), HDP_TREE_ST (segment tree, [ST]:
+ *           Kruskal merging w <= Int(C) + st_k/|C| for both trees, then
+ *           linking) or HDP_TREE_RT (random spanning tree, Sec. 4.1: the edges
+ *           shuffled, then the same union-find rules; the aggregation still
+ *           uses the edge weights).
+ *   rt_seed seed of the random tree's shuffle: edges in increasing order of
+ *           the top 31 bits of SplitMix64 output number l * 2^32 + e + 1 from
+ *           state rt_seed (edge id e, layer l), ties by edge id.
  *   gamma   Eq. (S): similarity exp(-W/gamma), W in 0..255 intensity units.
  *   alpha, tau_c, tau_g  matching cost of [Cost2] (Sec. 3.3); 20*alpha,
  *           3*tau_c and 6*tau_g must be integers (the cost is evaluated exactly).
@@ -89,6 +95,7 @@ typedef struct {
     int gmm_k[HDP_MAX_LEVELS];
     double gmm[HDP_MAX_LEVELS][HDP_MAX_GMM][3];
     int storage;
+    unsigned long long rt_seed;
 } hdp_params;
 
 /*

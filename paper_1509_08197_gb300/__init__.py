@@ -26,7 +26,7 @@ MAX_LEVELS = 8
 MAX_GMM = 8
 
 HDP_OK, HDP_ERR_ARG, HDP_ERR_CUDA, HDP_ERR_OOM, HDP_ERR_TIMEOUT, HDP_ERR_STATE = 0, -1, -2, -3, -4, -5
-TREE = {"mst": 0, "st": 1}
+TREE = {"mst": 0, "st": 1, "rt": 2}
 MODE = {"hdp": 0, "full": 1}
 PRIOR = {"sampled": 0, "uniform": 1}
 STORAGE = {"fp32": 0, "fp16": 1}
@@ -46,7 +46,7 @@ class _Params(ctypes.Structure):
                 ("beta_den", ctypes.c_int), ("delta0", ctypes.c_double), ("prior", ctypes.c_int),
                 ("gmm_k", ctypes.c_int * MAX_LEVELS),
                 ("gmm", ((ctypes.c_double * 3) * MAX_GMM) * MAX_LEVELS),
-                ("storage", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("rt_seed", ctypes.c_uint64)]
 
 
 @dataclass
@@ -89,6 +89,7 @@ class HDPParams:
             for k, (pi, mu, sd) in enumerate(comp):
                 p.gmm[l][k][0], p.gmm[l][k][1], p.gmm[l][k][2] = pi, mu, sd
         p.storage = STORAGE[self.storage]
+        p.rt_seed = int(self.rt_seed) & (2 ** 64 - 1)
         return p
 
 

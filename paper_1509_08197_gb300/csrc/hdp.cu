@@ -230,7 +230,7 @@ static const char* setup_params(Ctx& c, const hdp_params* p)
     if (p->width >= (1 << 19)) return "width must be below 2^19";   // packed with row data in the aggregation
     if (p->max_disp < 1 || p->max_disp > HDP_MAX_DISP) return "max_disp must be in 1..255";
     if (p->levels < 1 || p->levels > HDP_MAX_LEVELS) return "levels must be in 1..8";
-    if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST) return "unknown tree";
+    if (p->tree != HDP_TREE_MST && p->tree != HDP_TREE_ST && p->tree != HDP_TREE_RT) return "unknown tree";
     if (p->mode != HDP_MODE_HDP && p->mode != HDP_MODE_FULL) return "unknown mode";
     if (!(p->gamma > 0)) return "gamma must be > 0";
     if (!near_int(20.0 * p->alpha, &c.a20) || c.a20 < 0 || c.a20 > 20) return "20*alpha must be an integer in 0..20";

@@ -125,6 +125,42 @@ __global__ void k_edges(const int4* __restrict__ img, int W, int H, int ebits, c
     if (threadIdx.x == 0 && kept) atomicAdd(count, kept);
 }
 
+// Random spanning tree (Sec. 4.1): the edges are shuffled and taken by the
+// same union-find rules.  The shuffle is the order of a counter-based key:
+// the top 31 bits of the i-th output of SplitMix64 (Steele, Lea and Flood,
+// OOPSLA 2014) from state `seed`, i = l * 2^32 + e + 1, ties by edge id.
+__device__ __forceinline__ uint32_t rt_key(unsigned long long seed, int l, int e)
+{
+    unsigned long long z = seed + (((unsigned long long)l << 32) + (unsigned long long)e + 1ull) *
+                                      0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)(z >> 33);
+}
+
+// sort key of every slot: the edge's random key if it survived (packed key
+// not all ones), else all ones (below no survivor); the value is the edge id
+__global__ void k_rt_keys(const uint32_t* __restrict__ packed, int n2, unsigned long long seed, int l, uint32_t* rk,
+                          uint32_t* rv)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n2) return;
+    rk[e] = packed[e] == 0xffffffffu ? 0xffffffffu : rt_key(seed, l, e);
+    rv[e] = (uint32_t)e;
+}
+
+// back to packed (w << ebits | e) keys in the random order, which every
+// forest engine reads (the list position is the order)
+__global__ void k_rt_pack(const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rv,
+                          const int* __restrict__ weights, int n2, int ebits, uint32_t* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    const uint32_t e = rv[i];
+    out[i] = rk[i] == 0xffffffffu ? 0xffffffffu : ((uint32_t)weights[e] << ebits) | e;
+}
+
 void launch_edges(Ctx& c, int l, int hdp)
 {
     const LayerDims& d = c.dim[l];
@@ -140,6 +176,20 @@ void launch_edges(Ctx& c, int l, int hdp)
     // slots (all ones) come after every survivor
     int* slots = c.ints + IDX_ESLOTS;
     k_set_int<<<1, 1, 0, c.s>>>(slots, 2 * d.N);
+    if (c.p.tree == HDP_TREE_RT) {
+        // stable sort of all 2N slots on the full 32-bit random key, ids as
+        // values (ties stay in id order); the dropped slots come last
+        uint32_t* rk = c.keys1;
+        uint32_t* rv = (uint32_t*)c.listA;
+        k_rt_keys<<<cdiv(2 * d.N, 256), 256, 0, c.s>>>(c.keys0, 2 * d.N, c.p.rt_seed, l, rk, rv);
+        int where = radix_sort(rk, rv, c.keys0, (uint32_t*)c.listB, slots, 2 * d.N, 32, c.tmp, c.scan, c.s, 0);
+        const uint32_t* sk = where ? c.keys0 : rk;
+        const uint32_t* sv = where ? (const uint32_t*)c.listB : rv;
+        uint32_t* out = where ? c.keys1 : c.keys0;
+        k_rt_pack<<<cdiv(2 * d.N, 256), 256, 0, c.s>>>(sk, sv, c.weights, 2 * d.N, ebits, out);
+        c.sorted = out;
+        return;
+    }
     int where = radix_sort(c.keys0, nullptr, c.keys1, nullptr, slots, 2 * d.N, 8 + 2 * l, c.tmp, c.scan, c.s, ebits);
     c.sorted = where ? c.keys1 : c.keys0;
 }

@@ -91,6 +91,29 @@ def test_tiny_hdp_mst():
         _assert_layer(l, g, o, hp, None)
 
 
+@pytest.mark.parametrize("case", ["tiny_hdp", "third_hdp", "third_hdp_risky", "third_full"])
+def test_random_tree(case):
+    # HDP+RT (Sec. 4.1): the seeded random edge order through the same engines;
+    # every stage bit-exact, costs within REL_TOL, WTA up to near ties
+    if case == "tiny_hdp":
+        pair = workload_pair("tiny")
+        hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, tree="rt", rt_seed=11)
+    elif case == "third_hdp":
+        pair = workload_pair("third")
+        hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=4, tree="rt", rt_seed=12)
+    elif case == "third_hdp_risky":
+        pair = workload_pair("third")
+        hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=3, tree="rt", rt_seed=13, beta=(1, 5))
+    else:
+        pair = workload_pair("third")
+        hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=1, mode="full", tree="rt", rt_seed=14)
+    res = _run_layers(hp, pair)
+    if case == "third_hdp_risky":
+        assert int(res[0][0]["info"][5]) == 1 and int(res[0][0]["info"][3]) == 6
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
 def test_injected_prior_rebuilds_the_table():
     # the priors and tables of predicted layers run on the context's side
     # stream after hdp_build_trees; a prior set afterwards must win, and the
