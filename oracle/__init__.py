@@ -73,6 +73,9 @@ def _declare(L):
         "orc_range_table": (I, [P, I, I, I, P, D, P, P]),
         "orc_pixel_intervals": (I, [I, I, P, I, P, P]),
         "orc_aggregate_given": (I, [I64, I, P, P, P, P, P, P]),
+        "orc_gt_down": (I, [P, I, I, P]),
+        "orc_offset_hist": (I, [P, I, P, I, I, I, P]),
+        "orc_gmm_em": (I, [P, I, I, I, D, P, P]),
         "orc_aggregate_adjoint": (I, [I64, I, P, P, P, D, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -315,3 +318,34 @@ def soft_argmin(C, T=1.0):
     e = np.exp(z)
     pr = e / e.sum(1, keepdims=True)
     return (pr * np.arange(C.shape[1])[None, :]).sum(1)
+
+
+# ------------------------------------------------------------- GMM by EM ---
+def gt_down(gt: np.ndarray) -> np.ndarray:
+    """Ground truth of the next layer (Sec. 2.2 training data): int32 labels, -1 invalid."""
+    gt = _c(gt, np.int32)
+    H, W = gt.shape
+    up = np.empty(((H + 1) // 2, (W + 1) // 2), np.int32)
+    lib().orc_gt_down(_p(gt), W, H, _p(up))
+    return up
+
+
+def offset_hist(up: np.ndarray, lo: np.ndarray, rng: int, hist: np.ndarray = None) -> np.ndarray:
+    """Add the offsets o = up(P) - floor(lo(c)/2) of valid pixels to hist[o + rng] (int64, 2 rng + 1 bins)."""
+    up = _c(up, np.int32)
+    lo = _c(lo, np.int32)
+    if hist is None:
+        hist = np.zeros(2 * rng + 1, np.int64)
+    H, W = lo.shape
+    lib().orc_offset_hist(_p(up), up.shape[1], _p(lo), W, H, int(rng), _p(hist))
+    return hist
+
+
+def gmm_em(hist: np.ndarray, rng: int, K: int, iters: int, sd_min: float = 0.5, want_ll: bool = False):
+    """EM fit of a K-component GMM to offset histogram data; returns (K, 3) rows of (pi, mu, sd)."""
+    hist = _c(hist, np.int64)
+    out = np.empty(3 * K, np.float64)
+    ll = np.empty(iters + 1, np.float64) if want_ll else None
+    if lib().orc_gmm_em(_p(hist), int(rng), int(K), int(iters), float(sd_min), _p(out), _p(ll)):
+        raise ValueError("orc_gmm_em: empty histogram or K < 1")
+    return (out.reshape(K, 3), ll) if want_ll else out.reshape(K, 3)

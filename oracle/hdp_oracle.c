@@ -660,3 +660,143 @@ int orc_aggregate_adjoint(int64_t N, int X, const int32_t* order, const int32_t*
     free(s); free(Eu); free(Cf); free(gu);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* GMM_l by EM (Sec. 2.2).  The paper models the offset
+ * o = D_{l+1} - floor(D_l / S) of a superpixel's disparity from the mode
+ * given by each of its children, collects o over training pairs with ground
+ * truth, and fits a Gaussian mixture to its distribution by EM.
+ *
+ * Ground truth per layer (reading; the paper does not say how the coarse
+ * ground truth is formed): a map of integer labels, -1 where invalid
+ * (occluded).  The superpixel of a square takes the mean of its valid
+ * children divided by S = 2, rounded half up: floor((sum + n) / (2 n)) for n
+ * valid children; no valid child gives -1.                                  */
+int orc_gt_down(const int32_t* gt, int W, int H, int32_t* up)
+{
+    int Wu = (W + 1) / 2, Hu = (H + 1) / 2;
+    for (int Y = 0; Y < Hu; ++Y)
+        for (int X = 0; X < Wu; ++X) {
+            int64_t sum = 0, n = 0;
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    int x = 2 * X + dx, y = 2 * Y + dy;
+                    if (x >= W || y >= H) continue;
+                    int32_t v = gt[(size_t)y * W + x];
+                    if (v < 0) continue;
+                    sum += v;
+                    n += 1;
+                }
+            up[(size_t)Y * Wu + X] = n ? (int32_t)((sum + n) / (2 * n)) : -1;
+        }
+    return 0;
+}
+
+/* Histogram of o = up(floor(x/2), floor(y/2)) - floor(lo(x, y) / 2) over the
+ * pixels of layer l whose own and superpixel's labels are valid; bin
+ * o + range for |o| <= range (other offsets are not counted).  Adds to hist. */
+int orc_offset_hist(const int32_t* up, int Wu, const int32_t* lo, int W, int H, int range, int64_t* hist)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int32_t a = lo[(size_t)y * W + x], b = up[(size_t)(y / 2) * Wu + x / 2];
+            if (a < 0 || b < 0) continue;
+            int o = b - a / 2;
+            if (o < -range || o > range) continue;
+            hist[o + range] += 1;
+        }
+    return 0;
+}
+
+/* EM for a K-component 1-D Gaussian mixture on histogram data: h[b] points
+ * at o = b - range.  Standard EM (the GMM of Sec. 2.2, trained by the EM of
+ * its citation):
+ *   E-step  r_k(o) = pi_k N(o; mu_k, sd_k) / sum_j pi_j N(o; mu_j, sd_j)
+ *   M-step  n_k = sum_o h(o) r_k(o);  pi_k = n_k / sum h;
+ *           mu_k = sum_o h r_k o / n_k;  sd_k^2 = sum_o h r_k (o - mu_k)^2 / n_k
+ * Readings: the data are integers, so a component could collapse onto one
+ * value; sd_k is floored at sd_min (the constrained maximiser of the
+ * M-step, so the likelihood still never decreases).  Start: every mu_k at
+ * the data mean m, sd_k = max(s, sd_min) * 4^(k - (K-1)/2) with s the data's
+ * standard deviation (a narrow core and wider tails), pi_k = 1/K.  A
+ * component that loses all its points (n_k = 0) keeps its parameters with
+ * pi_k = 0.  The responsibilities are evaluated in the log domain.  Runs
+ * `iters` iterations; out: K rows of (pi, mu, sd); ll (optional, iters + 1
+ * entries): the log-likelihood sum_o h(o) log sum_k pi_k N(o; mu_k, sd_k)
+ * before the first and after every iteration.                           */
+static double em_loglik(const int64_t* h, int range, int K, const double* g)
+{
+    double ll = 0.0;
+    for (int b = 0; b <= 2 * range; ++b) {
+        if (!h[b]) continue;
+        double o = (double)(b - range), lmax = -INFINITY, acc = 0.0;
+        double lp[64];
+        for (int k = 0; k < K && k < 64; ++k) {
+            double z = (o - g[3 * k + 1]) / g[3 * k + 2];
+            lp[k] = g[3 * k] > 0.0 ? log(g[3 * k]) - log(g[3 * k + 2]) - 0.5 * z * z : -INFINITY;
+            if (lp[k] > lmax) lmax = lp[k];
+        }
+        for (int k = 0; k < K && k < 64; ++k) acc += exp(lp[k] - lmax);
+        ll += (double)h[b] * (lmax + log(acc) - 0.91893853320467274178);   /* - log sqrt(2 pi) */
+    }
+    return ll;
+}
+
+int orc_gmm_em(const int64_t* h, int range, int K, int iters, double sd_min, double* out, double* ll)
+{
+    const int nb = 2 * range + 1;
+    double tot = 0.0, m = 0.0, s2 = 0.0;
+    for (int b = 0; b < nb; ++b) { tot += (double)h[b]; m += (double)h[b] * (double)(b - range); }
+    if (tot <= 0.0 || K < 1 || K > 64) return -1;
+    m /= tot;
+    for (int b = 0; b < nb; ++b) s2 += (double)h[b] * ((double)(b - range) - m) * ((double)(b - range) - m);
+    double s = sqrt(s2 / tot);
+    if (s < sd_min) s = sd_min;
+    for (int k = 0; k < K; ++k) {
+        out[3 * k] = 1.0 / K;
+        out[3 * k + 1] = m;
+        out[3 * k + 2] = s * pow(4.0, (double)k - 0.5 * (K - 1));
+        if (out[3 * k + 2] < sd_min) out[3 * k + 2] = sd_min;
+    }
+    double* r = (double*)malloc(sizeof(double) * (size_t)nb * K);
+    if (!r) return -1;
+    if (ll) ll[0] = em_loglik(h, range, K, out);
+    for (int it = 0; it < iters; ++it) {
+        /* E-step */
+        for (int b = 0; b < nb; ++b) {
+            double o = (double)(b - range), lmax = -INFINITY;
+            for (int k = 0; k < K; ++k) {
+                double pi = out[3 * k], mu = out[3 * k + 1], sd = out[3 * k + 2];
+                double z = (o - mu) / sd;
+                double lp = pi > 0.0 ? log(pi) - log(sd) - 0.5 * z * z : -INFINITY;
+                r[(size_t)b * K + k] = lp;
+                if (lp > lmax) lmax = lp;
+            }
+            double den = 0.0;
+            for (int k = 0; k < K; ++k) den += exp(r[(size_t)b * K + k] - lmax);
+            for (int k = 0; k < K; ++k) r[(size_t)b * K + k] = exp(r[(size_t)b * K + k] - lmax) / den;
+        }
+        /* M-step: weights and means first, then spreads about the new means */
+        for (int k = 0; k < K; ++k) {
+            double nk = 0.0, sx = 0.0;
+            for (int b = 0; b < nb; ++b) {
+                double w = (double)h[b] * r[(size_t)b * K + k];
+                nk += w;
+                sx += w * (double)(b - range);
+            }
+            if (nk <= 0.0) { out[3 * k] = 0.0; continue; }
+            double mu = sx / nk, sv = 0.0;
+            for (int b = 0; b < nb; ++b) {
+                double d = (double)(b - range) - mu;
+                sv += (double)h[b] * r[(size_t)b * K + k] * d * d;
+            }
+            double sd = sqrt(sv / nk);
+            out[3 * k] = nk / tot;
+            out[3 * k + 1] = mu;
+            out[3 * k + 2] = sd < sd_min ? sd_min : sd;
+        }
+        if (ll) ll[it + 1] = em_loglik(h, range, K, out);
+    }
+    free(r);
+    return 0;
+}

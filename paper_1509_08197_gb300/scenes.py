@@ -184,3 +184,16 @@ def workload_pair(name: str, index: int = 0, **over) -> StereoPair:
     kw = dict(WORKLOADS[name])
     kw.update(over)
     return make_pair(seed=(order.index(name) + 1) * 1000 + index, **kw)
+
+
+def integer_gt(pair: StereoPair) -> np.ndarray:
+    """The pair's ground truth as integer labels: floor(gt + 1/2) clipped to
+    0..max_disp, -1 at occluded pixels (int32, (H, W))."""
+    d = np.clip(np.floor(pair.gt.astype(np.float64) + 0.5), 0, pair.max_disp).astype(np.int32)
+    d[pair.occluded] = -1
+    return d
+
+
+def training_pairs(name: str, count: int, first_index: int = 100):
+    """Seeded training scenes of a recipe (pair indices first_index.., disjoint from the evaluated pairs)."""
+    return [workload_pair(name, index=first_index + i) for i in range(count)]

@@ -647,3 +647,115 @@ def test_soft_argmin_closed_forms():
     # two equal minima, far below the rest: the midpoint
     C[0, 2] = 0.0
     assert oracle.soft_argmin(C)[0] == pytest.approx(4.0)
+
+
+# ------------------------------------------------------------- GMM by EM ---
+def test_gt_down_hand():
+    gt = np.array([[4, 5, 7],
+                   [6, -1, 9],
+                   [-1, -1, 2]], np.int32)
+    up = oracle.gt_down(gt)
+    # (4 + 5 + 6) / 3 = 5 -> 2.5 -> 3 (half up); (7 + 9) / 2 = 8 -> 4; no valid child -> -1; 2 -> 1
+    assert up.tolist() == [[3, 4], [-1, 1]]
+    assert oracle.gt_down(np.full((2, 2), 4, np.int32)).tolist() == [[2]]
+    assert oracle.gt_down(np.array([[3, 4]], np.int32)).tolist() == [[2]]       # 3.5 / 2 = 1.75 -> 2
+
+
+def test_offset_hist_hand():
+    up = np.array([[3, -1]], np.int32)
+    lo = np.array([[5, 6, 9, 9],
+                   [-1, 2, 0, 0]], np.int32)
+    h = oracle.offset_hist(up, lo, 4)
+    # children of 3: 5 -> 3 - 2 = 1, 6 -> 0, 2 -> 2 (the -1 child is skipped); the -1 superpixel counts nothing
+    want = np.zeros(9, np.int64)
+    want[[4 + 1, 4 + 0, 4 + 2]] = 1
+    assert np.array_equal(h, want)
+    h2 = oracle.offset_hist(up, lo, 4, h.copy())   # accumulates
+    assert np.array_equal(h2, 2 * want)
+
+
+def _norm_ll(hist, rng, g):
+    from scipy.special import logsumexp
+    from scipy.stats import norm
+    o = np.arange(-rng, rng + 1, dtype=np.float64)
+    lp = np.stack([np.log(max(pi, 1e-300)) + norm.logpdf(o, mu, sd) for pi, mu, sd in g])
+    return float((hist * logsumexp(lp, axis=0)).sum())
+
+
+def test_em_one_component_is_the_weighted_mean_and_spread():
+    rng = np.random.default_rng(31)
+    h = rng.integers(0, 50, size=41).astype(np.int64)
+    o = np.arange(-20, 21, dtype=np.float64)
+    g = oracle.gmm_em(h, 20, 1, 1)
+    m = np.average(o, weights=h)
+    s = np.sqrt(np.average((o - m) ** 2, weights=h))
+    assert g[0, 0] == pytest.approx(1.0)
+    assert g[0, 1] == pytest.approx(m, rel=1e-12)
+    assert g[0, 2] == pytest.approx(s, rel=1e-12)
+    # a single value: the spread is floored
+    h1 = np.zeros(41, np.int64)
+    h1[23] = 10
+    assert np.allclose(oracle.gmm_em(h1, 20, 1, 5), [[1.0, 3.0, 0.5]])
+
+
+def test_em_likelihood_never_decreases_and_matches_scipy():
+    rng = np.random.default_rng(32)
+    x = np.concatenate([rng.normal(0.3, 0.8, 30000), rng.normal(-1.0, 5.0, 8000)])
+    o = np.clip(np.rint(x), -30, 30).astype(int)
+    h = np.bincount(o + 30, minlength=61).astype(np.int64)
+    for K in (1, 2, 3):
+        g, ll = oracle.gmm_em(h, 30, K, 60, want_ll=True)
+        assert np.all(np.diff(ll) >= -1e-9 * abs(ll[-1]))
+        assert ll[-1] == pytest.approx(_norm_ll(h, 30, g), rel=1e-10)
+        assert g[:, 0].sum() == pytest.approx(1.0)
+
+
+def test_em_recovers_a_known_mixture():
+    # a narrow core and a wide tail, sampled, rounded to integers: the fit
+    # recovers the weights and means; the spreads grow by the rounding
+    # variance 1/12 (Sheppard)
+    rng = np.random.default_rng(33)
+    n = 400000
+    core = rng.random(n) < 0.7
+    x = np.where(core, rng.normal(0.0, 1.5, n), rng.normal(1.0, 7.0, n))
+    o = np.clip(np.rint(x), -60, 60).astype(int)
+    h = np.bincount(o + 60, minlength=121).astype(np.int64)
+    g = oracle.gmm_em(h, 60, 2, 300)
+    g = g[np.argsort(g[:, 2])]
+    assert g[0, 0] == pytest.approx(0.7, abs=0.02) and g[1, 0] == pytest.approx(0.3, abs=0.02)
+    assert g[0, 1] == pytest.approx(0.0, abs=0.05) and g[1, 1] == pytest.approx(1.0, abs=0.2)
+    assert g[0, 2] == pytest.approx(np.sqrt(1.5 ** 2 + 1 / 12), rel=0.03)
+    assert g[1, 2] == pytest.approx(np.sqrt(7.0 ** 2 + 1 / 12), rel=0.03)
+
+
+def test_em_translation_and_scale_invariance():
+    rng = np.random.default_rng(34)
+    h = np.zeros(81, np.int64)
+    h[30:50] = rng.integers(1, 400, size=20)
+    g = oracle.gmm_em(h, 40, 2, 50)
+    gs = oracle.gmm_em(np.roll(h, 7), 40, 2, 50)         # every offset + 7
+    assert np.allclose(gs[:, 1], g[:, 1] + 7, atol=1e-9)
+    assert np.allclose(gs[:, [0, 2]], g[:, [0, 2]], atol=1e-9)
+    assert np.allclose(oracle.gmm_em(3 * h, 40, 2, 50), g, atol=1e-9)
+
+
+def test_em_first_step_by_hand():
+    # one textbook EM step from the documented start (means at the data mean m,
+    # spreads s/2 and 2s, equal weights), with scipy's normal density
+    from scipy.stats import norm
+    rng = np.random.default_rng(35)
+    h = rng.integers(0, 30, size=31).astype(np.int64)
+    h[12:16] += 200
+    o = np.arange(-15, 16, dtype=np.float64)
+    m = np.average(o, weights=h)
+    s = np.sqrt(np.average((o - m) ** 2, weights=h))
+    g0 = [(0.5, m, s / 2), (0.5, m, 2 * s)]
+    p = np.stack([pi * norm.pdf(o, mu, sd) for pi, mu, sd in g0])
+    r = p / p.sum(0)
+    want = []
+    for k in range(2):
+        nk = (h * r[k]).sum()
+        mu = (h * r[k] * o).sum() / nk
+        sd = np.sqrt((h * r[k] * (o - mu) ** 2).sum() / nk)
+        want.append((nk / h.sum(), mu, max(sd, 0.5)))
+    assert np.allclose(oracle.gmm_em(h, 15, 2, 1), want, rtol=1e-10, atol=1e-12)
