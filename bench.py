@@ -319,6 +319,69 @@ def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
             hdp.hdp_destroy(c)
 
 
+def fit_gmm_on_training(hdp, torch, dev, n_pairs=6, K=2, iters=200):
+    """GMM_l of every predicted layer fitted by EM (Sec. 2.2) on the ground truth of seeded training scenes
+    of the full-size recipe (pair indices 100..105, disjoint from the benchmarked pair), on the GPU."""
+    from paper_1509_08197_gb300.scenes import integer_gt, training_pairs
+    maps = [integer_gt(p) for p in training_pairs("full", n_pairs)]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    gmm = hdp.fit_gmm(maps, D, LEVELS, K=K, iters=iters, device=dev)
+    torch.cuda.synchronize(dev)
+    return {"gmm": gmm, "fit_ms": 1000 * (time.perf_counter() - t0), "training_pairs": n_pairs, "K": K,
+            "iters": iters, "sd_min": 0.5}
+
+
+def injected_layers(hdp, torch, dev, params, pair, recs):
+    """Every layer of params on the GPU with the oracle's upper-layer map injected (identical inputs per layer):
+    {l: (costs, disparities)}."""
+    ctx = hdp.hdp_create(params)
+    try:
+        left = torch.from_numpy(pair.left).to(dev).contiguous()
+        right = torch.from_numpy(pair.right).to(dev).contiguous()
+        hdp.hdp_build_trees(ctx, left, right)
+        out = {}
+        for l in range(ctx.top, -1, -1):
+            if l < ctx.top:
+                hdp.hdp_set_stage(ctx, l + 1, "disp", recs[l + 1]["D"].astype(np.int32).ravel())
+            hdp.hdp_run_level(ctx, l)
+            out[l] = (hdp.hdp_get_stage(ctx, l, "costs"), hdp.hdp_get_stage(ctx, l, "disp"))
+        return out
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def eager_map(hdp, torch, dev, params, pair):
+    ctx = hdp.hdp_create(params)
+    try:
+        out = torch.empty((params.height, params.width), dtype=torch.int32, device=dev)
+        hdp.hdp_build_trees(ctx, torch.from_numpy(pair.left).to(dev), torch.from_numpy(pair.right).to(dev))
+        hdp.hdp_match(ctx, out)
+        hdp.hdp_sync(ctx)
+        return out.cpu().numpy()
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def precision_report(hdp, torch, dev, p16, pair, recs, D32=None):
+    """FP16 storage against the FP64 oracle: max relative cost error and WTA flip rate per layer on identical
+    inputs, and the change in bad-pixel rate of the whole FP16 run against the whole FP32 run."""
+    inj = injected_layers(hdp, torch, dev, p16, pair, recs)
+    layers = []
+    for l in sorted(inj, reverse=True):
+        costs, disp = inj[l]
+        o = recs[l]["agg"]
+        layers.append({"layer": l, "max_rel_err_vs_fp64": max_rel_err(costs, o["costs"]),
+                       "wta_flip_rate_vs_fp64": float((disp != o["wta"]).mean())})
+    p32 = hdp.HDPParams(**{**p16.__dict__, "storage": "fp32"})
+    D16 = eager_map(hdp, torch, dev, p16, pair)
+    D32 = eager_map(hdp, torch, dev, p32, pair) if D32 is None else D32
+    return {"max_rel_err_vs_fp64": max(x["max_rel_err_vs_fp64"] for x in layers),
+            "wta_flip_rate_vs_fp64": max(x["wta_flip_rate_vs_fp64"] for x in layers),
+            "bad_pixel_rate_fp32": bad_pixels(D32, pair), "bad_pixel_rate_fp16": bad_pixels(D16, pair),
+            "delta_bad_pixel_rate": bad_pixels(D16, pair) - bad_pixels(D32, pair), "per_layer": layers}
+
+
 def bad_pixels(D, pair, thr=1.0):
     """Fraction of non-occluded pixels whose disparity is off the synthetic ground truth by more than thr."""
     ok = ~pair.occluded
@@ -349,10 +412,28 @@ def cpu_baseline(pair, params_full_hdp, crop=None, want_recs=False):
         left, right = left[:crop[1], :crop[0]], right[:crop[1], :crop[0]]
     op = OracleParams(max_disp=D, levels=LEVELS, tree="st", beta=(95, 100), delta0=0.004)
     t0 = time.perf_counter()
-    _, recs = match(np.ascontiguousarray(left), np.ascontiguousarray(right), op, keep=True)
+    _, recs = match(np.ascontiguousarray(left), np.ascontiguousarray(right), op, keep=True, want_costs=want_recs)
     dt = time.perf_counter() - t0
     K = sum(int(r["agg"]["row_off"][-1]) for r in recs.values())
     return (K, dt, recs) if want_recs else (K, dt)
+
+
+def oracle_precision_reports(hdp, torch, dev, pair, recs, D32):
+    """FP16 storage against FP64 on the headline pair (HDP+ST, 1390x1110, d = 255) and on a 463x370, d = 79,
+    4-layer pair with MST and with ST (the oracle's runs are the FP64 reference)."""
+    from oracle.pipeline import OracleParams, match
+    from paper_1509_08197_gb300.scenes import workload_pair
+    rep = {"1390x1110 HDP+ST": precision_report(hdp, torch, dev, hdp.HDPParams(width=W, height=H, max_disp=D,
+                                                                                levels=LEVELS, tree="st",
+                                                                                storage="fp16"),
+                                                pair, recs, D32)}
+    third = workload_pair("third")
+    for tree in ("mst", "st"):
+        op = OracleParams(max_disp=79, levels=4, tree=tree, beta=(3, 5), delta0=0.064)
+        _, r3 = match(third.left, third.right, op, keep=True, want_costs=True)
+        p16 = hdp.HDPParams(width=463, height=370, max_disp=79, levels=4, tree=tree, storage="fp16")
+        rep[f"463x370 HDP+{tree.upper()}"] = precision_report(hdp, torch, dev, p16, third, r3)
+    return rep
 
 
 def oracle_agreement(maps, recs):
@@ -457,7 +538,10 @@ def main():
 
     variants = {}
     runs = {}
+    gmm_fit = None
     if not args.no_variants:
+        gmm_fit = fit_gmm_on_training(hdp, torch, dev)
+        specs["hdp_st_fp32_em"] = dict(base, gmm=gmm_fit["gmm"])
         for name, kw in specs.items():
             if name == args.variant:
                 continue
@@ -494,13 +578,15 @@ def main():
         batch = run_batch(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush, rank)
         grad = run_grad(hdp, torch, dev, max(3, args.steps // 2), args.warmup, flush)
 
-    cpu = parity = None
+    cpu = parity = precision = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         Kc, tc, recs = cpu_baseline(pair, None, want_recs=True)
         cpu = {"value": Kc / tc / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one whole pair (all 5 layers, {Kc} entries) in {tc:.1f} s, FP64, single thread"}
         if args.variant == "hdp_st_fp32":
             parity = oracle_agreement(head["maps"], recs)
+            if not args.no_variants:
+                precision = oracle_precision_reports(hdp, torch, dev, pair, recs, head["D"])
 
     if rank != 0:
         return
@@ -518,6 +604,8 @@ def main():
                      "algorithmic_bytes": abytes, "aggregation_ms": agg_ms},
         "cpu_baseline": cpu,
         "oracle_parity": parity,
+        "fp16_vs_fp64": precision,
+        "gmm_em": gmm_fit,
         "e2e": ({"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                  "ms_per_pair": 1000 * e2e["seconds"]} if e2e else None),
         "bad_pixel_rate": bad_pixels(head["D"], pair),

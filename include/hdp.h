@@ -296,6 +296,39 @@ int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const 
 int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, const uint8_t* d_right, int pitch,
                       int32_t* d_disp_out, void* stream);
 
+/* GMM_l by EM (Sec. 2.2; the trained GMM the paper uses is not published, so
+ * it is fitted here on ground truth the caller supplies).  The paper models
+ * the offset o = D_{l+1} - floor(D_l / 2) of a superpixel's disparity from
+ * the mode each of its children gives, collects o over training pairs with
+ * ground truth and fits a Gaussian mixture by EM; the result goes into
+ * hdp_params.gmm_k / gmm.  Context-free calls, enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); all pointers are device
+ * pointers owned by the caller.
+ *   hdp_gt_down: ground truth of the next layer.  d_gt int32 [height][width]
+ *     labels (-1 = invalid, e.g. occluded) -> d_gt_up int32
+ *     [ceil(height/2)][ceil(width/2)]: the mean of the valid children divided
+ *     by 2, rounded half up, floor((sum + n) / (2 n)); -1 without a valid
+ *     child.  width * height <= 2^23.
+ *   hdp_offset_hist: adds, for every pixel (x, y) of the lower map d_lo
+ *     (int32 [height][width]) with d_lo >= 0 and a superpixel
+ *     u = d_up[y/2][x/2] >= 0 (d_up as written by hdp_gt_down), one count to
+ *     d_hist[o + range] with o = u - floor(d_lo / 2), |o| <= range <= 255
+ *     (2 range + 1 uint64 bins, zeroed by the caller; counts accumulate over
+ *     calls, so several pairs can be summed).  Exact.
+ *   hdp_gmm_em: K (1..8) components fitted to the histogram by `iters`
+ *     iterations of EM, FP32: start with every mean at the data mean m,
+ *     spreads max(s, sd_min) * 4^(k - (K-1)/2) (s the data's spread) and
+ *     equal weights; E-step responsibilities in the log domain; M-step
+ *     weights and means, then spreads about the new means, floored at
+ *     sd_min > 0 (the offsets are integers: no component may collapse onto
+ *     one value).  d_out: float [K][3] = (pi, mu, sd) per component.
+ * HDP_ERR_ARG on a bad size or pointer; HDP_ERR_CUDA if a launch fails. */
+int hdp_gt_down(const int32_t* d_gt, int width, int height, int32_t* d_gt_up, void* stream);
+int hdp_offset_hist(const int32_t* d_up, const int32_t* d_lo, int width, int height, int range,
+                    unsigned long long* d_hist, void* stream);
+int hdp_gmm_em(const unsigned long long* d_hist, int range, int K, int iters, float sd_min, float* d_out,
+               void* stream);
+
 /* Per-stage inspection and injection for tests.  `what` selects one of the
  * HDP_STAGE_* buffers of layer `level`; `bytes` must equal its size exactly
  * (query it with hdp_stage_bytes).  hdp_get_stage synchronises the stream.

@@ -130,6 +130,9 @@ def load(path: str = LIB_PATH):
         "hdp_graph_capture": (I, [P, P, P, I, P, P]),
         "hdp_graph_launch": (I, [P]),
         "hdp_match_noalloc": (I, [P, P, P, I, P, P]),
+        "hdp_gt_down": (I, [P, I, I, P, P]),
+        "hdp_offset_hist": (I, [P, P, I, I, I, P, P]),
+        "hdp_gmm_em": (I, [P, I, I, I, ctypes.c_float, P, P]),
         "hdp_aggregate_fwd": (I, [P, P, P]),
         "hdp_aggregate_bwd": (I, [P, P, P, P, P, P]),
         "hdp_set_gamma": (I, [P, ctypes.c_float]),
@@ -386,6 +389,65 @@ def hdp_match_noalloc(params: HDPParams, left, right, out, stream=None):
         raise HDPError(f"hdp_match_noalloc failed ({rc})")
 
 
+def _raw(rc, what):
+    if rc != HDP_OK:
+        raise HDPError(f"{what} failed ({rc})")
+
+
+def hdp_gt_down(gt, stream=None):
+    """Ground truth of the next layer: gt int32 (H, W) CUDA tensor (-1 invalid) -> int32 (ceil(H/2), ceil(W/2))."""
+    import torch
+    if not isinstance(gt, torch.Tensor) or gt.dtype != torch.int32 or gt.dim() != 2:
+        raise TypeError("expected an int32 (H, W) CUDA tensor")
+    H, W = gt.shape
+    up = torch.empty(((H + 1) // 2, (W + 1) // 2), dtype=torch.int32, device=gt.device)
+    _raw(load().hdp_gt_down(_ptr(gt), W, H, _ptr(up), _stream(stream)), "hdp_gt_down")
+    return up
+
+
+def hdp_offset_hist(up, lo, rng: int, hist, stream=None):
+    """Add the offsets up(P) - floor(lo(c)/2) of lo's valid pixels to hist (int64 (2 rng + 1,) CUDA tensor)."""
+    import torch
+    H, W = lo.shape
+    if lo.dtype != torch.int32 or up.dtype != torch.int32 or tuple(up.shape) != ((H + 1) // 2, (W + 1) // 2):
+        raise TypeError("expected int32 maps, up of shape (ceil(H/2), ceil(W/2))")
+    if hist.dtype != torch.int64 or hist.numel() != 2 * rng + 1:
+        raise TypeError("expected an int64 histogram of 2 * range + 1 bins")
+    _raw(load().hdp_offset_hist(_ptr(up), _ptr(lo), W, H, int(rng), _ptr(hist), _stream(stream)), "hdp_offset_hist")
+
+
+def hdp_gmm_em(hist, rng: int, K: int, iters: int, sd_min: float = 0.5, out=None, stream=None):
+    """EM fit of K components to the histogram on the GPU; returns the float32 (K, 3) CUDA tensor (pi, mu, sd)."""
+    import torch
+    if out is None:
+        out = torch.empty((K, 3), dtype=torch.float32, device=hist.device)
+    _raw(load().hdp_gmm_em(_ptr(hist), int(rng), int(K), int(iters), float(sd_min), _ptr(out), _stream(stream)),
+         "hdp_gmm_em")
+    return out
+
+
+def fit_gmm(gt_maps, max_disp: int, levels: int, K: int = 2, iters: int = 200, sd_min: float = 0.5, device=None):
+    """GMM_l of every predicted layer (l = 0 .. levels-2) fitted by EM on ground-truth maps (Sec. 2.2).
+
+    gt_maps: int32 (H, W) numpy label maps (-1 invalid) at layer 0, one per training pair, all of range
+    0..max_disp.  Every step runs in the CUDA library; returns the per-layer [[pi, mu, sd], ...] lists
+    for HDPParams.gmm."""
+    import torch
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    d = [max_disp]
+    for _ in range(levels - 1):
+        d.append(d[-1] // 2)
+    hists = [torch.zeros(2 * d[l + 1] + 1, dtype=torch.int64, device=dev) for l in range(levels - 1)]
+    for g in gt_maps:
+        lo = torch.from_numpy(np.ascontiguousarray(g, np.int32)).to(dev)
+        for l in range(levels - 1):
+            up = hdp_gt_down(lo)
+            hdp_offset_hist(up, lo, d[l + 1], hists[l])
+            lo = up
+    return [hdp_gmm_em(hists[l], d[l + 1], K, iters, sd_min).cpu().numpy().astype(np.float64).tolist()
+            for l in range(levels - 1)]
+
+
 def _optr(t):
     return None if t is None else _ptr(t)
 
@@ -446,4 +508,5 @@ def exported_symbols():
             "hdp_match_host", "hdp_run_level", "hdp_sync", "hdp_wait_probe", "hdp_destroy", "hdp_last_error", "hdp_stage_bytes",
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
-            "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch"]
+            "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch",
+            "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em"]

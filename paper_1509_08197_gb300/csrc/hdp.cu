@@ -984,6 +984,47 @@ extern "C" int hdp_match_noalloc(const hdp_params* p, const uint8_t* d_left, con
     return HDP_OK;
 }
 
+// ---------------------------------------------------------- GMM by EM ---
+static int stream_error(const char* where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "%s: %s\n", where, cudaGetErrorString(e));
+        return HDP_ERR_CUDA;
+    }
+    return HDP_OK;
+}
+
+extern "C" int hdp_gt_down(const int32_t* d_gt, int width, int height, int32_t* d_gt_up, void* stream)
+{
+    if (!d_gt || !d_gt_up || width < 1 || height < 1 || (long long)width * height > (1 << 23)) return HDP_ERR_ARG;
+    launch_gt_down(d_gt, width, height, d_gt_up, (cudaStream_t)stream);
+    return stream_error("hdp_gt_down");
+}
+
+extern "C" int hdp_offset_hist(const int32_t* d_up, const int32_t* d_lo, int width, int height, int range,
+                               unsigned long long* d_hist, void* stream)
+{
+    if (!d_up || !d_lo || !d_hist || width < 1 || height < 1 || (long long)width * height > (1 << 23) ||
+        range < 0 || range > HDP_MAX_DISP)
+        return HDP_ERR_ARG;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HDP_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    launch_offset_hist(d_up, d_lo, width, height, range, d_hist, sms, (cudaStream_t)stream);
+    return stream_error("hdp_offset_hist");
+}
+
+extern "C" int hdp_gmm_em(const unsigned long long* d_hist, int range, int K, int iters, float sd_min, float* d_out,
+                          void* stream)
+{
+    if (!d_hist || !d_out || range < 0 || range > HDP_MAX_DISP || K < 1 || K > HDP_MAX_GMM || iters < 0 ||
+        iters > 100000 || !(sd_min > 0.f))
+        return HDP_ERR_ARG;
+    launch_gmm_em(d_hist, range, K, iters, sd_min, d_out, (cudaStream_t)stream);
+    return stream_error("hdp_gmm_em");
+}
+
 // ------------------------------------------------------ differentiable path ---
 static int grad_ready(hdp_ctx* ctx)
 {

@@ -188,6 +188,13 @@ void launch_aggregate(Ctx& c, int l);
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down);
 
 // grad.cu
+// GMM_l by EM (gmm.cu)
+void launch_gt_down(const int* gt, int W, int H, int* up, cudaStream_t s);
+void launch_offset_hist(const int* up, const int* lo, int W, int H, int range, unsigned long long* hist,
+                        int num_sms, cudaStream_t s);
+void launch_gmm_em(const unsigned long long* hist, int range, int K, int iters, float sd_min, float* out,
+                   cudaStream_t s);
+
 int grad_forward(Ctx& c, const float* E, float* C);
 int grad_backward(Ctx& c, const float* E, const float* gC, float* gE, float* gw, float* ggamma);
 void launch_set_gamma(Ctx& c, float gamma);
