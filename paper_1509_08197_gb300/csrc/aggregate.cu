@@ -18,7 +18,10 @@
 // neighbouring tile of the same path with a decoupled look-back: a tile
 // publishes its affine aggregate (A, M), then its inclusive boundary value; the
 // carry is evaluated innermost-first, so the rounding does not depend on
-// timing.  Light levels run one launch each (deepest first for the up pass).
+// timing.  Each pass is one launch over all tiles of the layer: tiles take
+// tickets deepest light level first (up) or shallowest first (down), and a
+// tile whose rows read another level's rows (a light child's U, a parent's
+// C) waits for that tile's done flag, set once its stores have completed.
 #include "hdp_impl.cuh"
 
 #define AGG_WARPS 4
@@ -43,8 +46,6 @@ struct AggArgs {
     const int* kp;
     const int* tbeg;
     const int* d_ntiles;
-    const int* lvl_first;
-    const int* lvl_count;
     float* vol;          // up-pass values U (and the down pass input)
     float* vout;         // down-pass output C (== vol for in-place aggregation)
     const float* Ein;    // optional dense cost volume [N][X] (all labels) instead of the matching cost
@@ -54,10 +55,10 @@ struct AggArgs {
     float* nd;
     int* tickets;
     int* tflags;
+    int* dflags;         // per tile and pass: 1 once the tile's rows are final in global memory
     float* aggA;
     float* inclA;
     float* aggM;
-    int level;
     int32_t* disp;
     DevStatus* st;
 };
@@ -246,6 +247,24 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
     }
 }
 
+// a light child's U (up pass) or a parent's C (down pass) lives in another
+// tile, with an earlier ticket: wait until that tile has published its rows
+// (bounded; on timeout the value read may be stale and the device status
+// reports DEV_TIMEOUT)
+__device__ __forceinline__ void wait_tile(const AggArgs& a, const int* dflags, int t)
+{
+    if (*(volatile const int*)(dflags + t)) return;
+    unsigned it = 0;
+    const unsigned cap = spin_cap(a.st);
+    while (*(volatile const int*)(dflags + t) == 0) {
+        if (++it > cap || dev_err(a.st)) {
+            dev_fail(a.st, DEV_TIMEOUT, 54);
+            return;
+        }
+        __nanosleep(32);
+    }
+}
+
 template <bool FP16, bool UP, int TF>
 __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P, float* PT, float* Q,
                           float4* CIN, int* CO, float* CS, uint64_t* bar, uint32_t& bar_phase)
@@ -267,6 +286,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     const uint32_t mqe = qe > 1 ? (uint32_t)((0x100000000ull + qe - 1) / qe) : 0u;
     const uint32_t mq = q > 1 ? (uint32_t)((0x100000000ull + q - 1) / q) : 0u;
     int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
+    int* dflags = a.dflags + (UP ? 0 : (size_t)ntiles);
     int* Pi = (int*)P;
     int* PTi = (int*)PT;
     int* Qi = (int*)Q;
@@ -338,6 +358,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
             const bool top = signbit(s);
             const float sv = fabsf(s), w = 1.f - sv * sv;
             const int pr = top ? a.prow[row] : -1;
+            if (pr >= 0) wait_tile(a, dflags, tile_of_row(a, pr));
             Pi[r] = pr >= 0 ? (int)a.roff[pr] : -1;
             PT[r] = pr >= 0 ? sv * (FP16 ? __ldcg(a.nd + pr) : 1.f) : 0.f;
             Q[r] = FP16 ? w * a.nup[row] : w;
@@ -379,6 +400,7 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         if (UP) {
             for (int k = lane; k < cn; k += 32) {
                 const int cr = a.lcrow[cc + k];
+                wait_tile(a, dflags, tile_of_row(a, cr));
                 CO[k] = (int)a.roff[cr];
                 CS[k] = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
             }
@@ -721,6 +743,16 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
         }
         if (lane == 0) bulk_store(a.volh + base, X, (uint32_t)(n * kp * 2));
     }
+    // the tile's rows (and masses) are final once its stores have completed:
+    // the bulk stores of lane 0 (async proxy) and every lane's plain stores,
+    // each ordered before the flag by a fence
+    if (lane == 0 && (tma16 || !FP16)) {
+        bulk_store_complete();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(dflags + u, 1);
 }
 
 // per warp: X (TF floats) | M, P, PT, Q (tile_rows_max(TF) each) | CIN (80 float4) | CO, CS (AGG_CHUNK each)
@@ -732,9 +764,8 @@ __global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? 4 : 5) k_agg(
 {
     constexpr int RM = tile_rows_max(TF);
     extern __shared__ float4 smem[];
-    const int cnt = a.lvl_count[a.level];
+    const int cnt = *a.d_ntiles;
     if (cnt == 0) return;
-    const int first = a.lvl_first[a.level];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* X = smem + (size_t)warp * agg_warp_f4<TF>();
     float* M = (float*)(X + TF / 4);
@@ -749,15 +780,19 @@ __global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? 4 : 5) k_agg(
     uint32_t bar_phase = 0;
     if (lane == 0) mbar_init(bar);
     __syncwarp();
-    int* tk = a.tickets + (UP ? 0 : MAX_LIGHT_LEVELS) + a.level;
+    int* tk = a.tickets + (UP ? 0 : MAX_LIGHT_LEVELS);
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(tk, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= cnt) break;
-        // up: bottom tiles first (carries flow upwards); down: top tiles first.
-        // A tile only waits on tiles with earlier tickets, so the waits end.
-        const int u = UP ? first + cnt - 1 - t : first + t;
+        // Tiles are numbered by light level, then position.  Up: the deepest
+        // level first and, inside a level, bottom tiles first (carries flow
+        // upwards, light children are deeper); down: the reverse.  A tile
+        // only waits on tiles with earlier tickets (its path neighbours, the
+        // tiles of its light children or of its parents), which were handed
+        // to running warps, so every wait ends.
+        const int u = UP ? cnt - 1 - t : t;
         tile_pass<FP16, UP, TF>(a, u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
     }
     if (lane == 0) bulk_store_complete();
@@ -824,8 +859,6 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.tstart = c.ustart_flag;
     a.tid = c.uid;
     a.d_ntiles = c.ints + IDX_NUNITS;
-    a.lvl_first = c.lvl_first;
-    a.lvl_count = c.lvl_count;
     a.vol = vol_up ? vol_up : c.vol;
     a.vout = vol_down ? vol_down : a.vol;
     a.Ein = Ein;
@@ -840,24 +873,23 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.aggM = c.aggM;
     a.disp = c.disp[l];
     a.st = c.st;
-    // light depth is at most floor(log2 N): one launch per possible level
-    int levels = 1;
-    while ((1 << levels) <= d.N) ++levels;
-    if (levels > MAX_LIGHT_LEVELS) levels = MAX_LIGHT_LEVELS;
+    // one launch per pass over every tile of the layer, in dependency order
+    // (look-back flags and done flags of both passes are cleared together)
+    a.dflags = c.tflags + 2 * c.max_tiles;
     cudaMemsetAsync(c.tickets, 0, sizeof(int) * 2 * MAX_LIGHT_LEVELS, c.s);
-    cudaMemsetAsync(c.tflags, 0, sizeof(int) * 2 * c.max_tiles, c.s);
+    cudaMemsetAsync(c.tflags, 0, sizeof(int) * 4 * c.max_tiles, c.s);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
-    const bool small_tiles = layer_tile_floats(c, l) == TILE_FLOATS_HDP;
+    const int tf = layer_tile_floats(c, l);
     const int cap = c.tune.agg_ctas_per_sm;
-    for (int lv = levels - 1; lv >= 0; --lv) {
-        a.level = lv;
-        if (small_tiles) launch_level_s<true, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
-        else launch_level_s<true, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
-    }
-    for (int lv = 0; lv < levels; ++lv) {
-        a.level = lv;
-        if (small_tiles) launch_level_s<false, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
-        else launch_level_s<false, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
+    if (tf == TILE_FLOATS_SMALL) {
+        launch_level_s<true, TILE_FLOATS_SMALL>(a, fp16, c.num_sms, cap, c.s);
+        launch_level_s<false, TILE_FLOATS_SMALL>(a, fp16, c.num_sms, cap, c.s);
+    } else if (tf == TILE_FLOATS_HDP) {
+        launch_level_s<true, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
+        launch_level_s<false, TILE_FLOATS_HDP>(a, fp16, c.num_sms, cap, c.s);
+    } else {
+        launch_level_s<true, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
+        launch_level_s<false, TILE_FLOATS>(a, fp16, c.num_sms, cap, c.s);
     }
 }
 

@@ -214,7 +214,7 @@ static void layout_buffers(Ctx& c)
     }
     c.vol_elems = K;
     c.max_tiles = tiles + 2 * 2048 + 16;   // + one partial tile per (light level, width) run
-    c.tflags = carve<int>(c, 2 * c.max_tiles);
+    c.tflags = carve<int>(c, 4 * c.max_tiles);   // look-back flags, then done flags, of both passes
     c.aggA = carve<float>(c, c.max_tiles * SCR_STRIDE);
     c.inclA = carve<float>(c, c.max_tiles * SCR_STRIDE);
     c.aggM = carve<float>(c, c.max_tiles);

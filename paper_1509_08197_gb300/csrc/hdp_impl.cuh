@@ -19,6 +19,13 @@
 // ms with 1024.
 #define TILE_FLOATS 2048
 #define TILE_FLOATS_HDP 1024
+// layers of fewer nodes than this are latency-bound (a chain of light levels,
+// one tile deep each): they take tiles of TILE_FLOATS_SMALL costs, so a
+// warp's share of a tile is short.  TILE_FLOATS_SMALL >= 256 + 4 (the widest
+// FP16 row with its mass column).
+#define TILE_FLOATS_SMALL 512
+#define SMALL_TILE_NODES (1 << 17)       // layers with one label set (full range, the top layer)
+#define SMALL_TILE_NODES_HDP (1 << 19)   // predicted layers (the 1390x1110 pair: layers 1-3)
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
 // rows per tile at most: tf / 8 (the narrowest rows, kp = 4, fill half a tile)
 __host__ __device__ __forceinline__ constexpr int tile_rows_max(int tf) { return tf / 8; }
@@ -163,7 +170,9 @@ enum {
 // the aggregation tile size of layer l (see TILE_FLOATS_HDP)
 inline int layer_tile_floats(const Ctx& c, int l)
 {
-    return (c.p.mode == HDP_MODE_FULL || l == c.top) ? TILE_FLOATS : TILE_FLOATS_HDP;
+    const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.top;
+    if (c.dim[l].N < (one_set ? SMALL_TILE_NODES : SMALL_TILE_NODES_HDP)) return TILE_FLOATS_SMALL;
+    return one_set ? TILE_FLOATS : TILE_FLOATS_HDP;
 }
 
 void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch);
