@@ -251,8 +251,12 @@ __device__ __noinline__ void wait_done(const AggArgs& a, int* f)
 // tile, with an earlier ticket: wait until that tile has published its rows
 // (bounded; on timeout the value read may be stale and the device status
 // reports DEV_TIMEOUT)
-__device__ __forceinline__ void wait_tile(const AggArgs& a, const int* dflags, int t)
+__device__ __forceinline__ void wait_tile(const AggArgs& a, const int* dflags, int t, int ntiles)
 {
+    if ((unsigned)t >= (unsigned)ntiles) {   // a corrupt layout: record it, read nothing
+        dev_fail(a.st, DEV_BAD_INPUT, 55);
+        return;
+    }
     if (*(volatile const int*)(dflags + t)) return;
     unsigned it = 0;
     const unsigned cap = spin_cap(a.st);
@@ -352,17 +356,29 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
             M[r] = m;
         }
     } else {
+        // parent row of a path top, -1 otherwise; CIN (320 floats >= the
+        // rows of any tile) is unused until phase 3 (P, PT, Q, M hold the
+        // row inputs: Pi aliases P)
+        int* Pr = (int*)CIN;
         for (int r = lane; r < n; r += 32) {
             const int row = b + r;
             const float s = a.rs[row];
             const bool top = signbit(s);
             const float sv = fabsf(s), w = 1.f - sv * sv;
             const int pr = top ? a.prow[row] : -1;
-            if (pr >= 0) wait_tile(a, dflags, tile_of_row(a, pr));
+            Pr[r] = pr;
             Pi[r] = pr >= 0 ? (int)a.roff[pr] : -1;
-            PT[r] = pr >= 0 ? sv * (FP16 ? __ldcg(a.nd + pr) : 1.f) : 0.f;
+            PT[r] = pr >= 0 ? sv : 0.f;
             Q[r] = FP16 ? w * a.nup[row] : w;
             M[r] = top ? 0.f : s;
+        }
+        // only now wait for the parents' tiles (their C and, in FP16, their
+        // masses), with this tile's own loads already in flight
+        for (int r = lane; r < n; r += 32) {
+            const int pr = Pr[r];
+            if (pr < 0) continue;
+            wait_tile(a, dflags, tile_of_row(a, pr), ntiles);
+            if (FP16) PT[r] *= __ldcg(a.nd + pr);
         }
     }
     __syncwarp();
@@ -393,83 +409,95 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
     }
 
     // ---- phase 1b: the affine inputs of every (row, column) of the tile.  Up:
-    // E plus the light children's U, in child order, the children taken in
-    // chunks of AGG_CHUNK whose row offsets and weights are staged first
-    for (int cc = c_base, first = 1; first || cc < c_end; cc += AGG_CHUNK, first = 0) {
-        const int cn = UP ? min(AGG_CHUNK, c_end - cc) : 0;
-        if (UP) {
-            for (int k = lane; k < cn; k += 32) {
-                const int cr = a.lcrow[cc + k];
-                wait_tile(a, dflags, tile_of_row(a, cr));
-                CO[k] = (int)a.roff[cr];
-                CS[k] = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
-            }
-            __syncwarp();
-        }
-        // no unrolling: the kernel is bound by instruction fetch and latency,
-        // not by the loop overhead (1390x1110 full range: 6.9 ms unrolled 4
-        // times, 6.0 ms not unrolled)
+    // E first (it needs no other tile, so it runs before any wait), then the
+    // light children's U added in child order, the children taken in chunks of
+    // AGG_CHUNK whose row offsets and weights are staged (after waiting for
+    // their tiles) first.  Down: (1 - s^2) U plus s C(parent) at path tops.
+    // No unrolling: the kernel is bound by instruction fetch and latency, not
+    // by the loop overhead (1390x1110 full range: 6.9 ms unrolled 4 times,
+    // 6.0 ms not unrolled)
+    if (UP) {
 #pragma unroll 1
         for (int idx = lane; idx < n * qe; idx += 32) {
             const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe, row = b + r;
             float4 x;
-            if (UP) {
+            if (j < q) {
                 const uint32_t qi = (uint32_t)Qi[r];
-                const int cb = PTi[r], ce = cb + (int)((qi >> 19) & 3u);
-                const int lo = max(cb, cc) - cc, hi = min(ce, cc + cn) - cc;
-                if (j < q) {
-                    if (first) {
-                        const int v = Pi[r];
-                        float t[4];
-                        if (a.Ein) {
-                            const float* er = a.Ein + (size_t)v * a.X;
+                const int v = Pi[r];
+                float t[4];
+                if (a.Ein) {
+                    const float* er = a.Ein + (size_t)v * a.X;
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
-                        } else {
-                            int lab[4];
-                            if (qi & (1u << 21)) {   // one interval: slot s holds label lo + s
-                                const int lo = (int)(qi >> 24), k = kp - (int)((qi >> 22) & 3u);
+                    for (int i = 0; i < 4; ++i) t[i] = 4 * j + i < a.X ? er[4 * j + i] : 0.f;
+                } else {
+                    int lab[4];
+                    if (qi & (1u << 21)) {   // one interval: slot s holds label lo + s
+                        const int lo = (int)(qi >> 24), k = kp - (int)((qi >> 22) & 3u);
 #pragma unroll
-                                for (int i = 0; i < 4; ++i) lab[i] = 4 * j + i < k ? lo + 4 * j + i : -1;
-                            } else {
-                                slot_labels(a, row, j, lab, nullptr);
-                            }
-                            const int px = (int)(qi & 0x7ffffu);
-                            const int4 Lp = a.imL[v];
-                            const int4* Rrow = a.imR + (size_t)(v - px);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
-                        }
-                        x = make_float4(t[0], t[1], t[2], t[3]);
+                        for (int i = 0; i < 4; ++i) lab[i] = 4 * j + i < k ? lo + 4 * j + i : -1;
                     } else {
-                        x = X[idx];
+                        slot_labels(a, row, j, lab, nullptr);
                     }
-                    for (int k = lo; k < hi; ++k) x = fma4(CS[k], load_row4_cg<FP16>(a, (size_t)CO[k] + 4 * j), x);
-                } else {
-                    float mass = first ? 1.f : X[idx].x;
-                    for (int k = lo; k < hi; ++k) mass += CS[k];
-                    x = make_float4(mass, 0.f, 0.f, 0.f);
+                    const int px = (int)(qi & 0x7ffffu);
+                    const int4 Lp = a.imL[v];
+                    const int4* Rrow = a.imR + (size_t)(v - px);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
                 }
+                x = make_float4(t[0], t[1], t[2], t[3]);
             } else {
-                const int po = Pi[r];
-                const float cw = Q[r];
-                if (j < q) {
-                    const float4 U = (!FP16 || tma16) ? X[idx] : load_row4<FP16>(a, base + (size_t)r * kp + 4 * j);
-                    x = make_float4(cw * U.x, cw * U.y, cw * U.z, cw * U.w);
-                    if (po >= 0) {
-                        const float4 cp = FP16 ? load_row4_cg<FP16>(a, (size_t)po + 4 * j)
-                                               : __ldcg((const float4*)(a.vout + po + 4 * j));
-                        x = fma4(PT[r], cp, x);
-                    }
-                } else {
-                    x = make_float4(cw + PT[r], 0.f, 0.f, 0.f);
-                }
+                x = make_float4(1.f, 0.f, 0.f, 0.f);   // FP16: the support mass starts at 1
             }
             X[idx] = x;
         }
         __syncwarp();
-        if (!UP) break;
+        for (int cc = c_base; cc < c_end; cc += AGG_CHUNK) {
+            const int cn = min(AGG_CHUNK, c_end - cc);
+            for (int k = lane; k < cn; k += 32) {
+                const int cr = a.lcrow[cc + k];
+                wait_tile(a, dflags, tile_of_row(a, cr), ntiles);
+                CO[k] = (int)a.roff[cr];
+                CS[k] = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int idx = lane; idx < n * qe; idx += 32) {
+                const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe;
+                const uint32_t qi = (uint32_t)Qi[r];
+                const int cb = PTi[r], ce = cb + (int)((qi >> 19) & 3u);
+                const int lo = max(cb, cc) - cc, hi = min(ce, cc + cn) - cc;
+                if (lo >= hi) continue;
+                float4 x = X[idx];
+                if (j < q) {
+                    for (int k = lo; k < hi; ++k) x = fma4(CS[k], load_row4_cg<FP16>(a, (size_t)CO[k] + 4 * j), x);
+                } else {
+                    for (int k = lo; k < hi; ++k) x.x += CS[k];
+                }
+                X[idx] = x;
+            }
+            __syncwarp();
+        }
+    } else {
+#pragma unroll 1
+        for (int idx = lane; idx < n * qe; idx += 32) {
+            const int r = qe > 1 ? (int)__umulhi((uint32_t)idx, mqe) : idx, j = idx - r * qe;
+            const int po = Pi[r];
+            const float cw = Q[r];
+            float4 x;
+            if (j < q) {
+                const float4 U = (!FP16 || tma16) ? X[idx] : load_row4<FP16>(a, base + (size_t)r * kp + 4 * j);
+                x = make_float4(cw * U.x, cw * U.y, cw * U.z, cw * U.w);
+                if (po >= 0) {
+                    const float4 cp = FP16 ? load_row4_cg<FP16>(a, (size_t)po + 4 * j)
+                                           : __ldcg((const float4*)(a.vout + po + 4 * j));
+                    x = fma4(PT[r], cp, x);
+                }
+            } else {
+                x = make_float4(cw + PT[r], 0.f, 0.f, 0.f);
+            }
+            X[idx] = x;
+        }
+        __syncwarp();
     }
 
     // ---- phase 2: scan in recurrence order t (row = n-1-t going up, t going down)
@@ -760,7 +788,9 @@ template <int TF>
 __host__ __device__ constexpr int agg_warp_f4() { return TF / 4 + tile_rows_max(TF) + 80 + AGG_CHUNK / 2; }
 
 template <bool FP16, bool UP, int TF>
-__global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? 4 : 5) k_agg(AggArgs a)
+__global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? AGG_MINB_2048 : TF == TILE_FLOATS_HDP ? AGG_MINB_1024
+                                                                                                    : AGG_MINB_512)
+    k_agg(AggArgs a)
 {
     constexpr int RM = tile_rows_max(TF);
     extern __shared__ float4 smem[];

@@ -472,7 +472,7 @@ extern "C" int hdp_wait_probe(hdp_ctx* ctx, int kind, unsigned limit)
 // ------------------------------------------------------------ tuning ---
 static const char* tuning_error(const hdp_tuning& t)
 {
-    if (t.agg_ctas_per_sm < 1 || t.agg_ctas_per_sm > 5) return "agg_ctas_per_sm out of 1..5";
+    if (t.agg_ctas_per_sm < 1 || t.agg_ctas_per_sm > 8) return "agg_ctas_per_sm out of 1..8";
     if (t.region_ctas_per_sm < 1 || t.region_ctas_per_sm > 4) return "region_ctas_per_sm out of 1..4";
     if (t.big_class_edges < 64 || t.big_class_edges > 4096) return "big_class_edges out of 64..4096";
     if (t.one_cta_nodes < 1024 || t.one_cta_nodes > (1 << 24)) return "one_cta_nodes out of 1024..1<<24";

@@ -24,6 +24,12 @@
 // warp's share of a tile is short.  TILE_FLOATS_SMALL >= 256 + 4 (the widest
 // FP16 row with its mass column).
 #define TILE_FLOATS_SMALL 512
+// aggregation CTAs (4 warps) per SM: launch bounds of the three tile sizes
+// and the default cap (occupancy limits each kernel below the cap)
+#define AGG_MINB_2048 4
+#define AGG_MINB_1024 5
+#define AGG_MINB_512 5
+#define AGG_CTAS_DEFAULT 5
 #define SMALL_TILE_NODES (1 << 17)       // layers with one label set (full range, the top layer)
 #define SMALL_TILE_NODES_HDP (1 << 19)   // predicted layers (the 1390x1110 pair: layers 1-3)
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
@@ -50,7 +56,7 @@ struct CostK {
 
 struct Ctx {
     hdp_params p;
-    hdp_tuning tune = {5, 4, 2048, 131072, 4096, 1 << 24};
+    hdp_tuning tune = {AGG_CTAS_DEFAULT, 4, 2048, 131072, 4096, 1 << 24};
     cudaStream_t s = nullptr;
     // side stream: the priors and interval tables of the predicted layers need
     // only that layer's images, so they run beside the coarser layers' work
