@@ -103,7 +103,7 @@ typedef struct {
  * same results bit for bit (the forest engines are exact, and the carries of
  * the aggregation are evaluated in a fixed order); only the speed changes.
  * Defaults in brackets; hdp_set_tuning rejects values outside the ranges.
- *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..5 [5] (the
+ *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..8 [5] (the
  *                          kernels of full-range layers fit 4, those of
  *                          predicted layers 5)
  *   region_ctas_per_sm     first-pass CTAs per SM on HDP layers, 1..4 [4]
