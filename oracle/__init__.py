@@ -62,6 +62,7 @@ def _declare(L):
         "orc_cost_m": (D, [P, P, P, P, I, I, I, I, I, D, D, D]),
         "orc_cost_mq": (I64, [P, P, P, P, I, I, I, I, I, I, I, I]),
         "orc_edge_weights": (I, [P, I, I, P]),
+        "orc_median3": (I, [P, I, I, P]),
         "orc_sort_edges": (I, [P, I, I, P]),
         "orc_splitmix64": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
         "orc_sort_edges_rt": (I, [P, I, I, ctypes.c_uint64, I, P]),
@@ -122,6 +123,15 @@ def cost_m(L, gL, R, gR, level, px, py, x, alpha=0.9, tau_c=7.0, tau_g=2.0):
 def cost_mq(L, gL, R, gR, level, px, py, x, a20=18, tc3=21, tg6=12):
     H, W, _ = L.shape
     return lib().orc_cost_mq(_p(L), _p(gL), _p(R), _p(gR), W, level, px, py, x, a20, tc3, tg6)
+
+
+def median3(img: np.ndarray) -> np.ndarray:
+    """3 x 3 per-channel median with replicated borders (the M+* prefilter, Sec. 4.1)."""
+    img = _c(img, np.int32)
+    H, W, _ = img.shape
+    out = np.empty_like(img)
+    lib().orc_median3(_p(img), W, H, _p(out))
+    return out
 
 
 def edge_weights(img: np.ndarray) -> np.ndarray:

@@ -125,6 +125,37 @@ static int64_t cost_mq_right(const int32_t* L, const int32_t* gL, const int32_t*
 }
 
 /* ------------------------------------------------------------------------ */
+/* M+* variants (Sec. 4.1): the cited MST and ST methods median-filter the
+ * image before building their trees; the paper removes that filter and
+ * names the versions that keep it M+*.  Reading: a 3 x 3 median per colour
+ * channel (border pixels replicated) of the layer's image, used for the edge
+ * weights (Eq. weight) only; the matching cost keeps the unfiltered images.
+ * The median of the nine values is the fifth smallest.                     */
+static int cmp_i32(const void* A, const void* B)
+{
+    int32_t a = *(const int32_t*)A, b = *(const int32_t*)B;
+    return (a > b) - (a < b);
+}
+
+int orc_median3(const int32_t* img, int W, int H, int32_t* out)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int c = 0; c < 3; ++c) {
+                int32_t v[9];
+                int n = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int yy = imin(imax(y + dy, 0), H - 1), xx = imin(imax(x + dx, 0), W - 1);
+                        v[n++] = img[3 * ((size_t)yy * W + xx) + c];
+                    }
+                qsort(v, 9, sizeof(int32_t), cmp_i32);
+                out[3 * ((size_t)y * W + x) + c] = v[4];
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. (weight): w(p, q) = |I(p) - I(q)| on the 4-connected grid.  Reading for
  * colour images: the largest per-channel absolute difference, as in the
  * cited MST method.  Edge id e = 2*(y*W + x) + o: o = 0 joins (x, y) and

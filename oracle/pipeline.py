@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (aggregate, bfs, build_forest, edge_weights, full_set, gradient, pixel_intervals, prior,
-               pyr_down, range_table, sort_edges, sort_edges_rt, to_level0)
+               median3, pyr_down, range_table, sort_edges, sort_edges_rt, to_level0)
 
 
 @dataclass
@@ -37,6 +37,11 @@ class OracleParams:
     gmm: list = field(default_factory=list)   # per predicted layer: [[pi, mu, sd], ...]
     prior: str = "sampled"          # "sampled" | "uniform"
     rt_seed: int = 0                # seed of the random tree's edge order
+    prefilter: str = "none"         # "none" | "median3" (the M+* variants, Sec. 4.1)
+
+    def tree_weights(self, L):
+        """Eq. (weight) on the layer's image, median-filtered first for the M+* variants."""
+        return edge_weights(median3(L) if self.prefilter == "median3" else L)
 
     def edge_order(self, w, W, H, level):
         """Rule 1: (w, id) order for MST and ST; the seeded random order for RT."""
@@ -90,7 +95,7 @@ def match(left: np.ndarray, right: np.ndarray, p: OracleParams, keep: bool = Fal
             masks = range_table(pw, d[l], d[l + 1], p.gmm_for(l), p.delta0 * (2 ** l))
             pix = pixel_intervals(W, H, D_up, masks)
             rec.update(prior=pw, masks=masks)
-        w = edge_weights(L)
+        w = p.tree_weights(L)
         order = p.edge_order(w, W, H, l)
         in_tree, dt_root, tint = build_forest(W, H, order, w, pix, p.beta, p.tree, p.st_k, l)
         bfs_order, parent, depth = bfs(W, H, in_tree)

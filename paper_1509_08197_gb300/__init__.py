@@ -68,6 +68,7 @@ class HDPParams:
     gmm: list = field(default_factory=list)   # per predicted layer: [[pi, mu, sd], ...] or None
     storage: str = "fp32"
     rt_seed: int = 0              # tree="rt": seed of the random edge order (Sec. 4.1)
+    prefilter: str = "none"       # "median3": the M+* variants (Sec. 4.1), tree weights from a 3x3 median
 
     def to_c(self) -> _Params:
         large = self.width > 640

@@ -17,7 +17,7 @@ def oracle_params(hp) -> OracleParams:
     delta0 = hp.delta0 if hp.delta0 is not None else (0.004 if large else 0.064)
     return OracleParams(max_disp=hp.max_disp, levels=hp.levels, tree=hp.tree, mode=hp.mode, gamma=hp.gamma,
                         alpha=hp.alpha, tau_c=hp.tau_c, tau_g=hp.tau_g, st_k=hp.st_k, beta=beta, delta0=delta0,
-                        gmm=hp.gmm, prior=hp.prior, rt_seed=hp.rt_seed)
+                        gmm=hp.gmm, prior=hp.prior, rt_seed=hp.rt_seed, prefilter=hp.prefilter)
 
 
 def oracle_layer(op: OracleParams, L, R, l, top, d_l, d_up, D_up, want_costs=True):
@@ -34,7 +34,7 @@ def oracle_layer(op: OracleParams, L, R, l, top, d_l, d_up, D_up, want_costs=Tru
         masks = oracle.range_table(pw, d_l, d_up, op.gmm_for(l), op.delta0 * 2 ** l)
         pix = oracle.pixel_intervals(W, H, D_up, masks)
         rec.update(prior=pw, table=masks, pix_set=D_up[np.arange(H)[:, None] // 2, np.arange(W)[None, :] // 2].ravel())
-    w = oracle.edge_weights(L)
+    w = op.tree_weights(L)
     order = op.edge_order(w, W, H, l)
     in_tree, dt_root, tint = oracle.build_forest(W, H, order, w, pix, op.beta, op.tree, op.st_k, l)
     bo, parent, depth = oracle.bfs(W, H, in_tree)

@@ -759,3 +759,30 @@ def test_em_first_step_by_hand():
         sd = np.sqrt((h * r[k] * (o - mu) ** 2).sum() / nk)
         want.append((nk / h.sum(), mu, max(sd, 0.5)))
     assert np.allclose(oracle.gmm_em(h, 15, 2, 1), want, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------- M+* prefilter ---
+def test_median3_equals_scipy_and_hand_cases():
+    from scipy.ndimage import median_filter
+    rng = np.random.default_rng(51)
+    for (H, W) in [(7, 9), (1, 5), (4, 1), (2, 2)]:
+        img = rng.integers(0, 1000, size=(H, W, 3)).astype(np.int32)
+        want = np.stack([median_filter(img[..., c], size=3, mode="nearest") for c in range(3)], -1)
+        assert np.array_equal(oracle.median3(img), want)
+    # an impulse is removed, a constant image is unchanged, a step edge keeps its place
+    img = np.zeros((5, 5, 3), np.int32)
+    img[2, 2] = 255
+    assert not oracle.median3(img).any()
+    step = np.zeros((4, 6, 3), np.int32)
+    step[:, 3:] = 90
+    assert np.array_equal(oracle.median3(step), step)
+
+
+def test_prefilter_changes_only_the_tree_weights():
+    from oracle.pipeline import OracleParams
+    rng = np.random.default_rng(52)
+    img = rng.integers(0, 255, size=(6, 8, 3)).astype(np.int32)
+    plain = OracleParams(max_disp=15)
+    med = OracleParams(max_disp=15, prefilter="median3")
+    assert np.array_equal(plain.tree_weights(img), oracle.edge_weights(img))
+    assert np.array_equal(med.tree_weights(img), oracle.edge_weights(oracle.median3(img)))
