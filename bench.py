@@ -471,7 +471,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", default="hdp_st_fp32",
                     choices=["hdp_st_fp32", "hdp_st_fp16", "full_st_fp32", "full_st_fp16", "hdp_mst_fp32",
-                             "hdp_rt_fp32"],
+                             "hdp_rt_fp32", "m_hdp_st_fp32", "m_full_st_fp32"],
                     help="configuration of the timed headline (profiling runs); the reported metric is hdp_st_fp32")
     args = ap.parse_args()
     rank, ws = dist_init()
@@ -519,7 +519,9 @@ def main():
              "full_st_fp32": dict(base, mode="full", levels=1),
              "full_st_fp16": dict(base, mode="full", levels=1, storage="fp16"),
              "hdp_mst_fp32": dict(base, tree="mst"),
-             "hdp_rt_fp32": dict(base, tree="rt", rt_seed=1)}
+             "hdp_rt_fp32": dict(base, tree="rt", rt_seed=1),
+             "m_hdp_st_fp32": dict(base, prefilter="median3"),
+             "m_full_st_fp32": dict(base, mode="full", levels=1, prefilter="median3")}
     head_p = hdp.HDPParams(**specs[args.variant])
     barrier(ws)
     head = run_variant(hdp, torch, head_p, pair, args.steps, args.warmup, flush, dev, want_e2e=not args.no_e2e,

@@ -50,6 +50,7 @@ enum { HDP_TREE_MST = 0, HDP_TREE_ST = 1, HDP_TREE_RT = 2 };
 enum { HDP_MODE_HDP = 0, HDP_MODE_FULL = 1 };
 enum { HDP_PRIOR_SAMPLED = 0, HDP_PRIOR_UNIFORM = 1 };
 enum { HDP_STORE_FP32 = 0, HDP_STORE_FP16 = 1 };
+enum { HDP_PREFILTER_NONE = 0, HDP_PREFILTER_MEDIAN3 = 1 };
 
 #define HDP_MAX_LEVELS 8
 #define HDP_MAX_GMM 8
@@ -65,6 +66,10 @@ enum { HDP_STORE_FP32 = 0, HDP_STORE_FP16 = 1 };
  *           linking) or HDP_TREE_RT (random spanning tree, Sec. 4.1: the edges
  *           shuffled, then the same union-find rules; the aggregation still
  *           uses the edge weights).
+ *   prefilter HDP_PREFILTER_MEDIAN3 gives the M+* variants of Sec. 4.1: the
+ *           edge weights (Eq. weight) of every layer come from that layer's
+ *           image after a 3x3 median per colour channel (borders replicated);
+ *           the matching cost keeps the unfiltered images.  Default NONE.
  *   rt_seed seed of the random tree's shuffle: edges in increasing order of
  *           the top 31 bits of SplitMix64 output number l * 2^32 + e + 1 from
  *           state rt_seed (edge id e, layer l), ties by edge id.
@@ -96,6 +101,7 @@ typedef struct {
     double gmm[HDP_MAX_LEVELS][HDP_MAX_GMM][3];
     int storage;
     unsigned long long rt_seed;
+    int prefilter;
 } hdp_params;
 
 /*

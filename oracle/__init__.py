@@ -75,6 +75,8 @@ def _declare(L):
         "orc_pixel_intervals": (I, [I, I, P, I, P, P]),
         "orc_aggregate_given": (I, [I64, I, P, P, P, P, P, P]),
         "orc_gt_down": (I, [P, I, I, P]),
+        "orc_lr_check": (I, [P, P, I, I, P]),
+        "orc_refine_aggregate": (I, [I, I, I, I, D, P, P, P, P, P, P, P, P, P, P]),
         "orc_offset_hist": (I, [P, I, P, I, I, I, P]),
         "orc_gmm_em": (I, [P, I, I, I, D, P, P]),
         "orc_aggregate_adjoint": (I, [I64, I, P, P, P, D, P, P, P, P, P]),
@@ -359,3 +361,33 @@ def gmm_em(hist: np.ndarray, rng: int, K: int, iters: int, sd_min: float = 0.5, 
     if lib().orc_gmm_em(_p(hist), int(rng), int(K), int(iters), float(sd_min), _p(out), _p(ll)):
         raise ValueError("orc_gmm_em: empty histogram or K < 1")
     return (out.reshape(K, 3), ll) if want_ll else out.reshape(K, 3)
+
+
+# ------------------------------------------------------------- refinement ---
+def lr_check(DL: np.ndarray, DR: np.ndarray) -> np.ndarray:
+    """refD = D_L where the left-right check passes (D_R(x - D_L, y) = D_L), else -1."""
+    DL = _c(DL, np.int32)
+    DR = _c(DR, np.int32)
+    H, W = DL.shape
+    out = np.empty((H, W), np.int32)
+    lib().orc_lr_check(_p(DL), _p(DR), W, H, _p(out))
+    return out
+
+
+def refine_aggregate(W, H, level, d_l, order, parent, w, tree_intv, refD, gamma=25.5, want_costs=True):
+    """Eq. C for the refinement cost |x - refD(p)| (0 where refD < 0) over the forest; dict like aggregate()."""
+    N = W * H
+    tint = _c(tree_intv, np.uint32).reshape(N, WORDS)
+    k = set_sizes(tint)
+    row_off = np.zeros(N + 1, np.int64)
+    np.cumsum(k, out=row_off[1:])
+    costs = np.empty(int(row_off[-1]), np.float64) if want_costs else None
+    wta = np.empty(N, np.int32)
+    best = np.empty(N, np.float64)
+    second = np.empty(N, np.float64)
+    rc = lib().orc_refine_aggregate(W, H, level, d_l, float(gamma), _p(_c(order, np.int32)), _p(_c(parent, np.int32)),
+                                    _p(_c(w, np.int64)), _p(tint), _p(_c(refD, np.int32).reshape(-1)), _p(row_off),
+                                    _p(costs), _p(wta), _p(best), _p(second))
+    if rc:
+        raise MemoryError("orc_refine_aggregate")
+    return dict(costs=costs, row_off=row_off, wta=wta, best=best, second=second)

@@ -831,3 +831,84 @@ int orc_gmm_em(const int64_t* h, int range, int K, int iters, double sd_min, dou
     free(r);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tree-based refinement (Sec. 3.3, last paragraph: the refinement of the
+ * cited MST/ST methods integrated at a layer).  Readings:
+ *   - D_R, the disparity map of the right view, is the method run with the
+ *     views' roles exchanged; a left pixel (x, y) with disparity D_L is
+ *     stable iff x - D_L >= 0 and D_R(x - D_L, y) = D_L (left-right check);
+ *     refD(p) = D_L(p) for a stable pixel, -1 otherwise.
+ *   - The new cost is E'(p, x) = |x - D_L(p)| at a stable pixel and 0 at an
+ *     unstable one, for x in TreeIntv(DT(p)); it is aggregated over the same
+ *     forest (Eq. C, same two passes as orc_aggregate) and the refined map is
+ *     its WTA (ties to the lowest label).                                     */
+int orc_lr_check(const int32_t* DL, const int32_t* DR, int W, int H, int32_t* refD)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int32_t d = DL[(size_t)y * W + x];
+            int xr = x - d;
+            refD[(size_t)y * W + x] = (xr >= 0 && DR[(size_t)y * W + xr] == d) ? d : -1;
+        }
+    return 0;
+}
+
+int orc_refine_aggregate(int W, int H, int level, int d_l, double gamma, const int32_t* order,
+                         const int32_t* parent, const int64_t* w, const uint32_t* tree_intv, const int32_t* refD,
+                         const int64_t* row_off, double* C_out, int32_t* wta, double* best, double* second)
+{
+    int64_t N = (int64_t)W * H;
+    double* s = (double*)malloc(sizeof(double) * N);
+    double* U = (double*)malloc(sizeof(double) * N);
+    double* C = (double*)malloc(sizeof(double) * N);
+    double* b1 = (double*)malloc(sizeof(double) * N);
+    double* b2 = (double*)malloc(sizeof(double) * N);
+    int32_t* arg = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* slot = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+    if (!s || !U || !C || !b1 || !b2 || !arg || !slot) return -1;
+    double sc = (double)scale4(level);
+    for (int64_t v = 0; v < N; ++v) {
+        int32_t p = parent[v];
+        s[v] = 0.0;
+        if (p >= 0) {
+            int64_t e;
+            if (p == v - 1) e = 2 * (int64_t)p;
+            else if (p == v + 1) e = 2 * v;
+            else if (p == v - W) e = 2 * (int64_t)p + 1;
+            else e = 2 * v + 1;
+            s[v] = exp(-((double)w[e] / sc) / gamma);
+        }
+        b1[v] = INFINITY; b2[v] = INFINITY; arg[v] = -1;
+    }
+    for (int x = 0; x <= d_l; ++x) {
+        for (int64_t v = 0; v < N; ++v) {
+            U[v] = 0.0;
+            if (set_has(tree_intv + ORC_WORDS * v, x) && refD[v] >= 0) U[v] = fabs((double)(x - refD[v]));
+        }
+        for (int64_t i = N - 1; i >= 0; --i) {      /* leaf to root */
+            int32_t v = order[i];
+            if (parent[v] >= 0 && set_has(tree_intv + ORC_WORDS * (int64_t)v, x))
+                U[parent[v]] += s[v] * U[v];
+        }
+        for (int64_t i = 0; i < N; ++i) {           /* root to leaf */
+            int32_t v = order[i];
+            if (!set_has(tree_intv + ORC_WORDS * (int64_t)v, x)) continue;
+            C[v] = parent[v] < 0 ? U[v] : s[v] * C[parent[v]] + (1.0 - s[v] * s[v]) * U[v];
+        }
+        for (int64_t v = 0; v < N; ++v) {
+            if (!set_has(tree_intv + ORC_WORDS * v, x)) continue;
+            if (C_out) C_out[row_off[v] + slot[v]] = C[v];
+            slot[v]++;
+            if (C[v] < b1[v]) { b2[v] = b1[v]; b1[v] = C[v]; arg[v] = x; }
+            else if (C[v] < b2[v]) b2[v] = C[v];
+        }
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        if (wta) wta[v] = arg[v];
+        if (best) best[v] = b1[v];
+        if (second) second[v] = b2[v];
+    }
+    free(s); free(U); free(C); free(b1); free(b2); free(arg); free(slot);
+    return 0;
+}

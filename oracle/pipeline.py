@@ -109,3 +109,21 @@ def match(left: np.ndarray, right: np.ndarray, p: OracleParams, keep: bool = Fal
             recs[l] = rec
         D_up = D
     return D_up, recs
+
+
+def refine(left: np.ndarray, right: np.ndarray, p: OracleParams, want_costs: bool = False):
+    """Tree-based refinement at layer 0 (Sec. 3.3, last paragraph; readings in hdp_oracle.c).
+
+    The right view's map is the method run with the views exchanged, which is
+    the left-reference method on both images mirrored left-right.  Returns
+    (refined D_0, record with D_L, D_R, refD and the refinement aggregation)."""
+    from . import lr_check, refine_aggregate
+    D_L, recs = match(left, right, p, keep=True)
+    D_Rm, _ = match(np.ascontiguousarray(right[:, ::-1]), np.ascontiguousarray(left[:, ::-1]), p)
+    D_R = np.ascontiguousarray(D_Rm[:, ::-1])
+    refD = lr_check(D_L, D_R)
+    r0 = recs[0]
+    agg = refine_aggregate(r0["W"], r0["H"], 0, r0["d"], r0["bfs"], r0["parent"], r0["w"], r0["tree_intv"], refD,
+                           p.gamma, want_costs=want_costs)
+    D = agg["wta"].reshape(r0["H"], r0["W"])
+    return D, dict(D_L=D_L, D_R=D_R, refD=refD, agg=agg, rec0=r0)

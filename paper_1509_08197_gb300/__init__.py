@@ -30,6 +30,7 @@ TREE = {"mst": 0, "st": 1, "rt": 2}
 MODE = {"hdp": 0, "full": 1}
 PRIOR = {"sampled": 0, "uniform": 1}
 STORAGE = {"fp32": 0, "fp16": 1}
+PREFILTER = {"none": 0, "median3": 1}
 STAGE = dict(pyr_left=0, pyr_right=1, weights=2, edges=3, in_tree=4, dt_root=5, tree_intv=6, bfs=7, parent=8,
              depth=9, prior=10, table=11, pix_set=12, costs=13, disp=14, info=15)
 _STAGE_DTYPE = dict(pyr_left=np.int32, pyr_right=np.int32, weights=np.int32, edges=np.int32, in_tree=np.uint8,
@@ -46,7 +47,7 @@ class _Params(ctypes.Structure):
                 ("beta_den", ctypes.c_int), ("delta0", ctypes.c_double), ("prior", ctypes.c_int),
                 ("gmm_k", ctypes.c_int * MAX_LEVELS),
                 ("gmm", ((ctypes.c_double * 3) * MAX_GMM) * MAX_LEVELS),
-                ("storage", ctypes.c_int), ("rt_seed", ctypes.c_uint64)]
+                ("storage", ctypes.c_int), ("rt_seed", ctypes.c_uint64), ("prefilter", ctypes.c_int)]
 
 
 @dataclass
@@ -91,6 +92,7 @@ class HDPParams:
                 p.gmm[l][k][0], p.gmm[l][k][1], p.gmm[l][k][2] = pi, mu, sd
         p.storage = STORAGE[self.storage]
         p.rt_seed = int(self.rt_seed) & (2 ** 64 - 1)
+        p.prefilter = PREFILTER[self.prefilter]
         return p
 
 

@@ -104,6 +104,7 @@ static void layout_buffers(Ctx& c)
         c.table[l] = carve<uint32_t>(c, 256 * HDP_WORDS);
         c.canon[l] = carve<int>(c, 256);
     }
+    c.imF = carve<int4>(c, c.p.prefilter == HDP_PREFILTER_MEDIAN3 ? N0 : 1);
     c.pk0[0] = carve<uint2>(c, N0);
     c.pk0[1] = carve<uint2>(c, N0);
     c.stage_l = carve<uint8_t>(c, 3 * (size_t)N0);
@@ -241,6 +242,7 @@ static const char* setup_params(Ctx& c, const hdp_params* p)
     if (!(p->delta0 >= 0.0) || p->delta0 >= 1.0) return "delta0 must be in [0, 1)";
     if (p->prior != HDP_PRIOR_SAMPLED && p->prior != HDP_PRIOR_UNIFORM) return "unknown prior";
     if (p->storage != HDP_STORE_FP32 && p->storage != HDP_STORE_FP16) return "unknown storage";
+    if (p->prefilter != HDP_PREFILTER_NONE && p->prefilter != HDP_PREFILTER_MEDIAN3) return "unknown prefilter";
     for (int l = 0; l < HDP_MAX_LEVELS; ++l) {
         if (p->gmm_k[l] < 0 || p->gmm_k[l] > HDP_MAX_GMM) return "gmm_k out of range";
         for (int k = 0; k < p->gmm_k[l]; ++k)

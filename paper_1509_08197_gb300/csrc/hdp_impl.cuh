@@ -158,6 +158,7 @@ struct Ctx {
     uint32_t* tmp = nullptr;   // scan / sort scratch
     size_t tmp_words = 0;
     DevStatus* st = nullptr;
+    int4* imF = nullptr;   // median-filtered layer image (M+* variants)
     unsigned long long* zero64 = nullptr;   // a word nothing writes (the wait probes read it)
 
     int tree_level = -1;       // layer whose forest/layout is in the work buffers

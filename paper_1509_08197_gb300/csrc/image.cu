@@ -161,13 +161,52 @@ __global__ void k_rt_pack(const uint32_t* __restrict__ rk, const uint32_t* __res
     out[i] = rk[i] == 0xffffffffu ? 0xffffffffu : ((uint32_t)weights[e] << ebits) | e;
 }
 
+// M+* variants (Sec. 4.1): the tree is built on the layer's image after a
+// 3x3 median per colour channel (border pixels replicated); the matching
+// cost keeps the unfiltered image.  The median of nine is the middle element
+// after an odd-even transposition sort (nine rounds of compare-exchange).
+__device__ __forceinline__ int median9(int v[9])
+{
+#pragma unroll
+    for (int round = 0; round < 9; ++round)
+#pragma unroll
+        for (int i = round & 1; i + 1 < 9; i += 2) {
+            const int a = v[i], b = v[i + 1];
+            v[i] = min(a, b);
+            v[i + 1] = max(a, b);
+        }
+    return v[4];
+}
+
+__global__ void k_median3(const int4* __restrict__ img, int W, int H, int4* __restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= W * H) return;
+    const int x = p % W, y = p / W;
+    int r[9], g[9], b[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int xx = min(max(x + k % 3 - 1, 0), W - 1), yy = min(max(y + k / 3 - 1, 0), H - 1);
+        const int4 v = img[yy * W + xx];
+        r[k] = v.x;
+        g[k] = v.y;
+        b[k] = v.z;
+    }
+    out[p] = make_int4(median9(r), median9(g), median9(b), img[p].w);
+}
+
 void launch_edges(Ctx& c, int l, int hdp)
 {
     const LayerDims& d = c.dim[l];
     int ebits = edge_bits(d.N);
+    const int4* wimg = c.imL[l];   // the image the tree's weights come from
+    if (c.p.prefilter == HDP_PREFILTER_MEDIAN3) {
+        k_median3<<<cdiv(d.N, 256), 256, 0, c.s>>>(c.imL[l], d.W, d.H, c.imF);
+        wimg = c.imF;
+    }
     cudaMemsetAsync(c.ints + IDX_NEDGES, 0, sizeof(int), c.s);
     cudaMemsetAsync(c.ints + IDX_RISKY, 0, sizeof(int), c.s);
-    k_edges<<<cdiv(2 * d.N, 256), 256, 0, c.s>>>(c.imL[l], d.W, d.H, ebits, hdp ? c.pixset : nullptr,
+    k_edges<<<cdiv(2 * d.N, 256), 256, 0, c.s>>>(wimg, d.W, d.H, ebits, hdp ? c.pixset : nullptr,
                                                    hdp ? c.table[l] : nullptr, hdp ? c.canon[l] : nullptr,
                                                    c.p.beta_num, c.p.beta_den, c.keys0, c.ints + IDX_NEDGES,
                                                    c.weights, c.ints + IDX_RISKY);

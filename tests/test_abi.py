@@ -43,7 +43,7 @@ def test_default_params(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("max_disp", 0), ("max_disp", 256), ("levels", 0), ("levels", 9), ("width", 1), ("alpha", 0.93),
-    ("tau_c", 7.1), ("beta_num", 7), ("delta0", 1.5), ("tree", 5), ("storage", 3),
+    ("tau_c", 7.1), ("beta_num", 7), ("delta0", 1.5), ("tree", 5), ("storage", 3), ("prefilter", 2),
 ])
 def test_invalid_params_rejected(lib, field, value):
     p = hdp._Params()

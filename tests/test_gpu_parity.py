@@ -114,6 +114,24 @@ def test_random_tree(case):
         _assert_layer(l, g, o, hp, None)
 
 
+@pytest.mark.parametrize("case", ["tiny_hdp_mst", "third_hdp_st", "third_full_st"])
+def test_median_prefilter(case):
+    # M+* variants (Sec. 4.1): tree weights from the 3x3 median-filtered layer image
+    if case == "tiny_hdp_mst":
+        pair = workload_pair("tiny")
+        hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, prefilter="median3")
+    elif case == "third_hdp_st":
+        pair = workload_pair("third")
+        hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=4, tree="st", prefilter="median3")
+    else:
+        pair = workload_pair("third")
+        hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=1, mode="full", tree="st",
+                           prefilter="median3")
+    res = _run_layers(hp, pair)
+    for l, (g, o) in res.items():
+        _assert_layer(l, g, o, hp, None)
+
+
 def test_injected_prior_rebuilds_the_table():
     # the priors and tables of predicted layers run on the context's side
     # stream after hdp_build_trees; a prior set afterwards must win, and the

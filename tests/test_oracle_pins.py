@@ -786,3 +786,61 @@ def test_prefilter_changes_only_the_tree_weights():
     med = OracleParams(max_disp=15, prefilter="median3")
     assert np.array_equal(plain.tree_weights(img), oracle.edge_weights(img))
     assert np.array_equal(med.tree_weights(img), oracle.edge_weights(oracle.median3(img)))
+
+
+# ------------------------------------------------------------- refinement ---
+def test_lr_check_hand():
+    DL = np.array([[0, 1, 1, 3]], np.int32)
+    DR = np.array([[0, 1, 9, 3]], np.int32)
+    # x=0: 0-0=0, DR[0]=0 ok; x=1: 1-1=0, DR[0]=0 != 1; x=2: 2-1=1, DR[1]=1 ok; x=3: 3-3=0, DR[0]=0 != 3
+    assert oracle.lr_check(DL, DR).tolist() == [[0, -1, 1, -1]]
+    # a match left of the image is never stable
+    assert oracle.lr_check(np.array([[2, 0]], np.int32), np.array([[2, 0]], np.int32)).tolist() == [[-1, 0]]
+
+
+def test_refinement_aggregation_equals_brute_force():
+    rng = np.random.default_rng(61)
+    for (H, W, d) in [(4, 5, 7), (3, 6, 15), (1, 9, 5)]:
+        c = _agg_case(rng, H, W, d)
+        refD = np.array([rng.choice(oracle.labels_of(c["tint"][v])) if rng.random() < 0.7 else -1
+                         for v in range(W * H)], np.int32)
+        agg = oracle.refine_aggregate(W, H, 0, d, c["bfs"], c["parent"], c["w"], c["tint"], refD)
+        E = np.full((W * H, d + 1), np.nan)
+        for v in range(W * H):
+            for x in oracle.labels_of(c["tint"][v]):
+                E[v, x] = abs(x - refD[v]) if refD[v] >= 0 else 0.0
+        ref = brute.brute_aggregate(W, H, c["in_tree"], c["w"].astype(float), E, 25.5)
+        C = _dense(agg, c["tint"], d)
+        assert np.allclose(C, ref, rtol=1e-12, atol=1e-12, equal_nan=True)
+        # WTA: lowest label on ties, taken from the brute-force costs
+        for v in range(W * H):
+            labs = oracle.labels_of(c["tint"][v])
+            assert agg["wta"][v] == labs[int(np.argmin(ref[v, labs]))]
+
+
+def test_refinement_special_cases():
+    rng = np.random.default_rng(62)
+    H, W, d = 4, 6, 9
+    c = _agg_case(rng, H, W, d, pix=np.tile(oracle.full_set(9), (24, 1)))
+    # one tree, every pixel stable at the same disparity: the refined map keeps it
+    agg = oracle.refine_aggregate(W, H, 0, d, c["bfs"], c["parent"], c["w"], c["tint"], np.full(24, 6, np.int32))
+    assert (agg["wta"] == 6).all()
+    # no stable pixel: every cost is 0 and the lowest label wins
+    agg = oracle.refine_aggregate(W, H, 0, d, c["bfs"], c["parent"], c["w"], c["tint"], np.full(24, -1, np.int32))
+    assert (agg["wta"] == 0).all() and (agg["costs"] == 0).all()
+
+
+def test_refine_right_view_by_mirroring():
+    # the right view's map is the method with the views exchanged: mirroring
+    # both images of a mirror-symmetric pair (right = mirror of left, left =
+    # mirror of right) gives back the left map, mirrored
+    from oracle.pipeline import OracleParams, match, refine
+    from paper_1509_08197_gb300.scenes import workload_pair
+    pair = workload_pair("tiny")
+    p = OracleParams(max_disp=15, levels=2, beta=(3, 5), delta0=0.064)
+    L, R = pair.left, pair.right
+    D, rec = refine(L, R, p)
+    D_R_direct, _ = match(np.ascontiguousarray(R[:, ::-1]), np.ascontiguousarray(L[:, ::-1]), p)
+    assert np.array_equal(rec["D_R"], D_R_direct[:, ::-1])
+    assert np.array_equal(rec["refD"], oracle.lr_check(rec["D_L"], rec["D_R"]))
+    assert D.shape == L.shape[:2] and (D >= 0).all() and (D <= 15).all()
