@@ -332,6 +332,36 @@ def fit_gmm_on_training(hdp, torch, dev, n_pairs=6, K=2, iters=200):
             "iters": iters, "sd_min": 0.5}
 
 
+def run_refine(hdp, torch, params, pair, steps, warmup, flush, dev):
+    """Tree-based refinement at layer 0 (right view, left-right check, re-aggregation over the forest),
+    launched eagerly (about twice the launches of one match), timed with CUDA events on its stream."""
+    stream = torch.cuda.Stream(device=dev)
+    ctx = hdp.hdp_create(params, stream)
+    try:
+        L = torch.from_numpy(pair.left).to(dev).contiguous()
+        R = torch.from_numpy(pair.right).to(dev).contiguous()
+        out = torch.empty((params.height, params.width), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                hdp.hdp_refine(ctx, L, R, out)
+            stream.synchronize()
+            times = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hdp.hdp_refine(ctx, L, R, out)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            D = out.cpu().numpy()
+            refD = hdp.hdp_get_stage(ctx, 0, "ref_d")
+        return {"ms_per_pair_eager": float(np.mean(times)), "bad_pixel_rate": bad_pixels(D, pair),
+                "stable_fraction": float((refD >= 0).mean())}
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
 def injected_layers(hdp, torch, dev, params, pair, recs):
     """Every layer of params on the GPU with the oracle's upper-layer map injected (identical inputs per layer):
     {l: (costs, disparities)}."""
@@ -562,6 +592,9 @@ def main():
                      "disparity_agreement_with_headline": float((r["D"] == head["D"]).mean()),
                      "bad_pixel_rate": bad_pixels(r["D"], pair)}
             variants[name] = entry
+        for name in ("hdp_st_fp32", "full_st_fp32"):
+            variants[name.replace("_fp32", "_fp32_refined")] = run_refine(
+                hdp, torch, hdp.HDPParams(**specs[name]), pair, max(3, args.steps // 2), args.warmup, flush, dev)
         if "full_st_fp32" in variants and args.variant == "hdp_st_fp32":
             variants["speedup_hdp_over_full_st_fp32"] = variants["full_st_fp32"]["ms_per_pair"] / step_ms
         if args.variant == "hdp_st_fp32" and "hdp_st_fp16" in runs:

@@ -185,6 +185,24 @@ int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right,
  * int32 [height][width], to d_disp_out.  Requires hdp_build_trees first. */
 int hdp_match(hdp_ctx* ctx, int32_t* d_disp_out);
 
+/* Tree-based refinement (Sec. 3.3, last paragraph: the refinement of the
+ * cited MST and ST methods integrated at layer 0).  On the caller's device
+ * images (as for hdp_build_trees):
+ *   1. the right view's map D_R: the whole method on the pair mirrored
+ *      left-right with the views exchanged (which is the right-reference
+ *      method), read back mirrored;
+ *   2. the left view's map D_L (hdp_build_trees + hdp_match);
+ *   3. the left-right check: (x, y) is stable iff x - D_L >= 0 and
+ *      D_R(x - D_L, y) = D_L;
+ *   4. the cost |x - D_L(p)| at stable pixels and 0 elsewhere, for x in
+ *      TreeIntv(DT(p)), aggregated over layer 0's forest (Eq. C), and its
+ *      WTA (ties to the lowest label), written to d_disp_out (int32
+ *      [height][width]).
+ * Afterwards HDP_STAGE_DISP of layer 0 and HDP_STAGE_COSTS hold the refined
+ * map and the refinement's aggregated costs, HDP_STAGE_REF_D and
+ * HDP_STAGE_DISP_R the checked map and D_R.  Enqueued on the context's stream. */
+int hdp_refine(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch, int32_t* d_disp_out);
+
 /* hdp_build_trees + hdp_match on host buffers: copies h_left/h_right (tightly
  * packed RGB uint8) to the device, runs, copies the disparity map back into
  * h_disp_out (int32 [height][width]) and synchronises the stream. */
@@ -355,7 +373,9 @@ enum {
     HDP_STAGE_PIX_SET = 12,   /* int32 [N]: row of the table used by each pixel */
     HDP_STAGE_COSTS = 13,     /* float [K]: aggregated cost, pixel-major, labels ascending */
     HDP_STAGE_DISP = 14,      /* int32 [N]: D_l */
-    HDP_STAGE_INFO = 15       /* int64 [16]: K_l, edge count, tree count, engine, ... (below) */
+    HDP_STAGE_INFO = 15,      /* int64 [16]: K_l, edge count, tree count, engine, ... (below) */
+    HDP_STAGE_REF_D = 16,     /* int32 [N], layer 0 after hdp_refine: D_L where the left-right check passes, else -1 */
+    HDP_STAGE_DISP_R = 17     /* int32 [N], layer 0 after hdp_refine: the right view's map, in its own frame */
 };
 /* HDP_STAGE_INFO of the layer whose tree is current: [0] K_l aggregated
  * entries, [1] edges kept by DT-Rule 1, [2] trees, [3] forest engine (1

@@ -32,11 +32,11 @@ PRIOR = {"sampled": 0, "uniform": 1}
 STORAGE = {"fp32": 0, "fp16": 1}
 PREFILTER = {"none": 0, "median3": 1}
 STAGE = dict(pyr_left=0, pyr_right=1, weights=2, edges=3, in_tree=4, dt_root=5, tree_intv=6, bfs=7, parent=8,
-             depth=9, prior=10, table=11, pix_set=12, costs=13, disp=14, info=15)
+             depth=9, prior=10, table=11, pix_set=12, costs=13, disp=14, info=15, ref_d=16, disp_r=17)
 _STAGE_DTYPE = dict(pyr_left=np.int32, pyr_right=np.int32, weights=np.int32, edges=np.int32, in_tree=np.uint8,
                     dt_root=np.int32, tree_intv=np.uint32, bfs=np.int32, parent=np.int32, depth=np.int32,
                     prior=np.int64, table=np.uint32, pix_set=np.int32, costs=np.float32, disp=np.int32,
-                    info=np.int64)
+                    info=np.int64, ref_d=np.int32, disp_r=np.int32)
 
 
 class _Params(ctypes.Structure):
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         "hdp_build_trees": (I, [P, P, P, I]),
         "hdp_match": (I, [P, P]),
         "hdp_match_host": (I, [P, P, P, P]),
+        "hdp_refine": (I, [P, P, P, I, P]),
         "hdp_run_level": (I, [P, I]),
         "hdp_sync": (I, [P]),
         "hdp_wait_probe": (I, [P, I, ctypes.c_uint]),
@@ -287,6 +288,14 @@ def hdp_build_trees(ctx: Context, left, right):
 def hdp_match(ctx: Context, out):
     """out: torch.int32 (H, W) contiguous CUDA tensor."""
     _check(ctx, load().hdp_match(ctx.handle, _dmap(out, ctx.params)), "hdp_match")
+
+
+def hdp_refine(ctx: Context, left, right, out):
+    """Tree-based refinement at layer 0 (right view by mirroring, left-right check, re-aggregation): the
+    refined map into out (torch.int32 (H, W) CUDA tensor); left/right as for hdp_build_trees."""
+    W = ctx.params.width
+    _check(ctx, load().hdp_refine(ctx.handle, _image(left, ctx.params), _image(right, ctx.params), 3 * W,
+                                  _dmap(out, ctx.params)), "hdp_refine")
 
 
 def hdp_match_host(ctx: Context, left: np.ndarray, right: np.ndarray, out: np.ndarray = None) -> np.ndarray:
@@ -512,4 +521,4 @@ def exported_symbols():
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
             "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch",
-            "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em"]
+            "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em", "hdp_refine"]

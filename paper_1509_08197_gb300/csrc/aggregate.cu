@@ -49,6 +49,7 @@ struct AggArgs {
     float* vol;          // up-pass values U (and the down pass input)
     float* vout;         // down-pass output C (== vol for in-place aggregation)
     const float* Ein;    // optional dense cost volume [N][X] (all labels) instead of the matching cost
+    const int* refD;     // optional refinement cost |x - refD[v]| (0 where refD[v] < 0) instead of the matching cost
     int X;
     __half* volh;
     float* nup;
@@ -438,11 +439,18 @@ __device__ void tile_pass(const AggArgs& a, int u, float4* X, float* M, float* P
                     } else {
                         slot_labels(a, row, j, lab, nullptr);
                     }
-                    const int px = (int)(qi & 0x7ffffu);
-                    const int4 Lp = a.imL[v];
-                    const int4* Rrow = a.imR + (size_t)(v - px);
+                    if (a.refD) {   // refinement: distance to the pixel's checked disparity
+                        const int rd = a.refD[v];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
+                        for (int i = 0; i < 4; ++i) t[i] = lab[i] >= 0 && rd >= 0 ? (float)abs(lab[i] - rd) : 0.f;
+                    } else {
+                        const int px = (int)(qi & 0x7ffffu);
+                        const int4 Lp = a.imL[v];
+                        const int4* Rrow = a.imR + (size_t)(v - px);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            t[i] = lab[i] >= 0 ? cost_m(Lp, Rrow[max(px - lab[i], 0)], a.ck) : 0.f;
+                    }
                 }
                 x = make_float4(t[0], t[1], t[2], t[3]);
             } else {
@@ -892,6 +900,7 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.vol = vol_up ? vol_up : c.vol;
     a.vout = vol_down ? vol_down : a.vol;
     a.Ein = Ein;
+    a.refD = c.agg_refD;
     a.X = d.d + 1;
     a.volh = c.volh;
     a.nup = c.nup;

@@ -110,6 +110,9 @@ static void layout_buffers(Ctx& c)
     c.stage_l = carve<uint8_t>(c, 3 * (size_t)N0);
     c.stage_r = carve<uint8_t>(c, 3 * (size_t)N0);
     c.disp_host_stage = carve<int32_t>(c, N0);
+    c.dispRm = carve<int>(c, N0);
+    c.refD = carve<int>(c, N0);
+    c.refR = carve<int>(c, N0);
     c.gmm = carve<double>(c, HDP_MAX_LEVELS * HDP_MAX_GMM * 3);
     c.gmm_k = carve<int>(c, HDP_MAX_LEVELS);
     c.full_mask = carve<uint32_t>(c, HDP_MAX_LEVELS * HDP_WORDS);
@@ -436,6 +439,7 @@ extern "C" int hdp_match(hdp_ctx* ctx, int32_t* d_disp_out)
     if (!ctx || !d_disp_out) return HDP_ERR_ARG;
     Ctx& c = ctx->c;
     if (!c.built) return fail(ctx, HDP_ERR_STATE, "hdp_build_trees has not been called");
+    c.refined = 0;
     for (int l = c.top; l >= 0; --l) {
         int rc = hdp_run_level(ctx, l);
         if (rc) return rc;
@@ -569,6 +573,33 @@ extern "C" int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* 
     return HDP_OK;
 }
 
+extern "C" int hdp_refine(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch, int32_t* d_disp_out)
+{
+    if (!ctx || !d_left || !d_right || !d_disp_out) return HDP_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (pitch < 3 * c.p.width) return fail(ctx, HDP_ERR_ARG, "bad pitch");
+    const int W = c.p.width, H = c.p.height;
+    // the right view's map: the method on the mirrored, exchanged pair (the
+    // staging buffers are free: hdp_build_trees waits for earlier side work)
+    for (int l = 0; l < HDP_MAX_LEVELS; ++l)
+        if (c.side_pending[l]) {
+            TRY_CUDA(cudaStreamWaitEvent(c.s, c.ev_side[l], 0));
+            c.side_pending[l] = 0;
+        }
+    launch_mirror(d_right, pitch, W, H, c.stage_l, c.s);
+    launch_mirror(d_left, pitch, W, H, c.stage_r, c.s);
+    int rc = hdp_build_trees(ctx, c.stage_l, c.stage_r, 3 * W);
+    if (!rc) rc = hdp_match(ctx, c.dispRm);
+    // the left view's map, which leaves layer 0's forest loaded
+    if (!rc) rc = hdp_build_trees(ctx, d_left, d_right, pitch);
+    if (!rc) rc = hdp_match(ctx, d_disp_out);
+    if (rc) return rc;
+    launch_refine(c);
+    TRY_CUDA(cudaMemcpyAsync(d_disp_out, c.disp[0], sizeof(int32_t) * c.dim[0].N, cudaMemcpyDeviceToDevice, c.s));
+    c.refined = 1;
+    return check_launch(ctx, "hdp_refine");
+}
+
 extern "C" int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, int32_t* h_disp_out)
 {
     if (!ctx || !h_left || !h_right || !h_disp_out) return HDP_ERR_ARG;
@@ -698,6 +729,8 @@ extern "C" int64_t hdp_stage_bytes(hdp_ctx* ctx, int level, int what)
         return 4 * K;
     }
     case HDP_STAGE_INFO: return 8 * 16;
+    case HDP_STAGE_REF_D:
+    case HDP_STAGE_DISP_R: return level == 0 && c.refined ? 4 * N : HDP_ERR_STATE;
     default: return HDP_ERR_ARG;
     }
 }
@@ -749,6 +782,8 @@ extern "C" int hdp_get_stage(hdp_ctx* ctx, int level, int what, void* h_dst, siz
     case HDP_STAGE_TABLE: TRY_CUDA(cudaMemcpy(h_dst, c.table[level], bytes, cudaMemcpyDeviceToHost)); break;
     case HDP_STAGE_PIX_SET: TRY_CUDA(cudaMemcpy(h_dst, c.pixset, bytes, cudaMemcpyDeviceToHost)); break;
     case HDP_STAGE_DISP: TRY_CUDA(cudaMemcpy(h_dst, c.disp[level], bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_REF_D: TRY_CUDA(cudaMemcpy(h_dst, c.refD, bytes, cudaMemcpyDeviceToHost)); break;
+    case HDP_STAGE_DISP_R: TRY_CUDA(cudaMemcpy(h_dst, c.refR, bytes, cudaMemcpyDeviceToHost)); break;
     case HDP_STAGE_COSTS: {
         std::vector<int> rowof(N), rdt(N);
         std::vector<uint32_t> roff(N + 1), T((size_t)N * HDP_WORDS);

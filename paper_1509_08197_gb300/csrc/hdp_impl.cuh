@@ -159,6 +159,13 @@ struct Ctx {
     size_t tmp_words = 0;
     DevStatus* st = nullptr;
     int4* imF = nullptr;   // median-filtered layer image (M+* variants)
+    // refinement (refine.cu): the right view's map as computed on mirrored
+    // views, the checked left map (refD) and the right map in its own frame
+    int* dispRm = nullptr;
+    int* refD = nullptr;
+    int* refR = nullptr;
+    const int* agg_refD = nullptr;   // set only while the refinement pass is enqueued
+    int refined = 0;                 // the refinement stages hold the last hdp_refine
     unsigned long long* zero64 = nullptr;   // a word nothing writes (the wait probes read it)
 
     int tree_level = -1;       // layer whose forest/layout is in the work buffers
@@ -210,6 +217,10 @@ void launch_offset_hist(const int* up, const int* lo, int W, int H, int range, u
                         int num_sms, cudaStream_t s);
 void launch_gmm_em(const unsigned long long* hist, int range, int K, int iters, float sd_min, float* out,
                    cudaStream_t s);
+
+// refinement (refine.cu)
+void launch_mirror(const uint8_t* src, int pitch, int W, int H, uint8_t* dst, cudaStream_t s);
+void launch_refine(Ctx& c);
 
 int grad_forward(Ctx& c, const float* E, float* C);
 int grad_backward(Ctx& c, const float* E, const float* gC, float* gE, float* gw, float* ggamma);
