@@ -491,6 +491,7 @@ def oracle_agreement(maps, recs):
 
 
 def main():
+    global W, H, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -503,7 +504,13 @@ def main():
                     choices=["hdp_st_fp32", "hdp_st_fp16", "full_st_fp32", "full_st_fp16", "hdp_mst_fp32",
                              "hdp_rt_fp32", "m_hdp_st_fp32", "m_full_st_fp32"],
                     help="configuration of the timed headline (profiling runs); the reported metric is hdp_st_fp32")
+    ap.add_argument("--pair", default="full", choices=["full", "third"],
+                    help="profiling captures: 'third' runs a 463x370 pair with the same range and layers, a small "
+                         "case of the same kernels; the reported metric is quoted on 'full'")
     args = ap.parse_args()
+    if args.pair == "third":
+        W, H = 463, 370
+        WORKLOAD = "463x370 RGB pair, disparity 0-255, 5 layers, HDP + segment tree (profiling case)"
     rank, ws = dist_init()
 
     from paper_1509_08197_gb300.scenes import workload_pair
@@ -542,7 +549,7 @@ def main():
         from paper_1509_08197_gb300 import build
         build.build()
         hdp.load()
-    pair = workload_pair("full", index=rank)
+    pair = workload_pair("full", index=rank) if args.pair == "full" else workload_pair("third", index=rank, max_disp=D)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     base = dict(width=W, height=H, max_disp=D, levels=LEVELS, tree="st")
     specs = {"hdp_st_fp32": dict(base), "hdp_st_fp16": dict(base, storage="fp16"),
