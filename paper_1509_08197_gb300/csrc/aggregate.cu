@@ -839,6 +839,320 @@ __global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? AGG_MINB_2048
 template <int TF>
 static size_t agg_smem() { return (size_t)AGG_WARPS * agg_warp_f4<TF>() * sizeof(float4); }
 
+// ---- column kernel: one-label-set layers with wide rows -----------------------
+// On a full-range layer (or a big top layer) every row holds the same kp
+// labels.  A CTA takes one tile (the same tiles, tickets, flags and look-back
+// scratch as k_agg) and a thread owns one label column x of all its rows: the
+// cost E(v, x) reads the right image at (px - x), so the threads of a row read
+// consecutive pixels; the recurrence along the rows is sequential per column
+// (no cross-thread scan); children's, parents' and the tile's own rows are
+// read and written row by row, coalesced.  FP16 storage adds a column (thread
+// kp) for the support mass.  Used on the layers whose tiles hold
+// TILE_FLOATS_COL floats (kp >= COL_MIN_KP), so a tile has at most
+// TILE_FLOATS_COL / COL_MIN_KP rows.
+#define COL_MAX_ROWS (TILE_FLOATS_COL / COL_MIN_KP)
+#define COL_THREADS_MAX 288   // 256 label columns + the mass column, in warps
+#define COL_CHUNK 256         // light children staged per chunk
+
+template <bool FP16>
+__device__ __forceinline__ float col_load(const AggArgs& a, const float* v32, size_t off)
+{
+    if (FP16) return __half2float(__ldcg(a.volh + off));
+    return __ldcg(v32 + off);
+}
+
+template <bool FP16, bool UP>
+__global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
+{
+    extern __shared__ float Xs[];                 // the tile: n rows of S floats
+    __shared__ int sV[COL_MAX_ROWS];              // up: node; down: parent row offset (-1: none)
+    __shared__ int sR[COL_MAX_ROWS];              // up: first light child; down: parent row (-1: none)
+    __shared__ int sNC[COL_MAX_ROWS];             // up: light children
+    __shared__ float sM[COL_MAX_ROWS];            // multiplier to the previous row in recurrence order
+    __shared__ float sP[COL_MAX_ROWS];            // coefficient of the carry
+    __shared__ float sW[COL_MAX_ROWS];            // down: 1 - s^2 (x the up-pass mass in FP16)
+    __shared__ float sPW[COL_MAX_ROWS];           // down: s (x the parent's mass in FP16)
+    __shared__ float sMass[COL_MAX_ROWS];
+    __shared__ float sBest[COL_MAX_ROWS][COL_THREADS_MAX / 32];
+    __shared__ int sSlot[COL_MAX_ROWS][COL_THREADS_MAX / 32];
+    __shared__ int sCR[COL_CHUNK];                // staged light children: row in the tile,
+    __shared__ int sCO[COL_CHUNK];                // row offset,
+    __shared__ float sCS[COL_CHUNK];              // weight (x mass in FP16)
+    __shared__ int s_t, s_D;
+    const int x = threadIdx.x, lane = x & 31, warp = x >> 5, nwarps = blockDim.x >> 5;
+    const int S = kp + (FP16 ? 1 : 0);            // floats per row in shared memory
+    const bool col = x < S;                       // owns a column (label slot, or the mass at x == kp)
+    const int K = a.dl + 1;                       // labels 0..dl; slots K..kp-1 are padding
+    const int ntiles = *a.d_ntiles;
+    int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
+    int* dflags = a.dflags + (UP ? 0 : (size_t)ntiles);
+    int* tk = a.tickets + (UP ? 0 : MAX_LIGHT_LEVELS);
+    float* const vdst = UP ? a.vol : a.vout;
+    for (;;) {
+        __syncthreads();   // the previous tile is done with the shared arrays
+        if (x == 0) s_t = atomicAdd(tk, 1);
+        __syncthreads();
+        const int t = s_t;
+        if (t >= ntiles) break;
+        // same order as k_agg: every wait is on an earlier ticket
+        const int u = UP ? ntiles - 1 - t : t;
+        const int b = a.tbeg[u];
+        int e = b + tile_rows_of(kp, FP16 ? 4 : 0, TILE_FLOATS_COL);
+        if (u + 1 < ntiles) e = min(e, a.tbeg[u + 1]);
+        e = min(e, a.N);
+        const int n = min(e - b, COL_MAX_ROWS);
+        const size_t base = a.roff[b];
+
+        // ---- per-row inputs, one thread per row (a tile may have more rows than the CTA threads)
+        for (int r = x; r < n; r += blockDim.x) {
+            const int row = b + r;
+            if (UP) {
+                const int v = a.lay[row];
+                const int c0 = (int)a.lcoff[row];
+                sV[r] = v;
+                sR[r] = c0;
+                sNC[r] = (int)a.lcoff[row + 1] - c0;
+                float m = 0.f;
+                if (row + 1 < a.N) {
+                    const float s1 = a.rs[row + 1];
+                    m = signbit(s1) ? 0.f : s1;
+                }
+                sM[r] = m;
+            } else {
+                const float s = a.rs[row];
+                const bool top = signbit(s);
+                const float sv = fabsf(s), w = 1.f - sv * sv;
+                const int pr = top ? a.prow[row] : -1;
+                sR[r] = pr;
+                sV[r] = pr >= 0 ? (int)a.roff[pr] : -1;
+                sPW[r] = pr >= 0 ? sv : 0.f;
+                sW[r] = FP16 ? w * a.nup[row] : w;
+                sM[r] = top ? 0.f : s;
+            }
+        }
+        __syncthreads();
+        if (x == 0) {   // carry coefficients: products of the multipliers in recurrence order
+            float acc = 1.f;
+            for (int k = 0; k < n; ++k) {
+                const int r = UP ? n - 1 - k : k;
+                acc *= sM[r];
+                sP[r] = acc;
+            }
+        }
+        if (x == 0 && e - b > COL_MAX_ROWS) dev_fail(a.st, DEV_BAD_INPUT, 56);   // a layout this kernel cannot hold
+
+        // ---- the affine inputs of every (row, column)
+        if (UP) {
+            // E (no other tile needed), then the light children's U in child order
+            if (col) {
+#pragma unroll 4
+                for (int r = 0; r < n; ++r) {
+                    float val = 1.f;   // the mass column starts at 1
+                    if (x < kp) {
+                        const int v = sV[r];
+                        const int lab = x < K ? x : -1;   // full range: slot x holds label x
+                        if (a.Ein) {
+                            val = x < a.X ? __ldg(a.Ein + (size_t)v * a.X + x) : 0.f;
+                        } else if (a.refD) {
+                            const int rd = __ldg(a.refD + v);
+                            val = lab >= 0 && rd >= 0 ? (float)abs(lab - rd) : 0.f;
+                        } else {
+                            const int px = v % a.W;
+                            val = lab >= 0 ? cost_m(__ldg(a.imL + v), __ldg(a.imR + (v - px) + max(px - lab, 0)), a.ck)
+                                           : 0.f;
+                        }
+                    }
+                    Xs[r * S + x] = val;
+                }
+            }
+            // the children in chunks: one thread per child waits for its tile and
+            // stages (row, offset, weight); then every column adds them in child
+            // order (children of a row are consecutive), the loads of a chunk
+            // in flight together
+            const int cb = (int)a.lcoff[b], ce = (int)a.lcoff[b + n];
+            for (int cc = cb; cc < ce; cc += COL_CHUNK) {
+                const int cn = min(COL_CHUNK, ce - cc);
+                __syncthreads();   // the previous chunk's staging is consumed
+                for (int k = x; k < cn; k += blockDim.x) {
+                    const int cr = a.lcrow[cc + k];
+                    wait_tile(a, dflags, tile_of_row(a, cr), ntiles);
+                    // the child's parent row is in this tile: find it among the rows' child ranges
+                    int lo = 0, hi = n - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sR[mid] <= cc + k) lo = mid; else hi = mid - 1;
+                    }
+                    sCR[k] = lo;
+                    sCO[k] = (int)a.roff[cr];
+                    sCS[k] = fabsf(a.rs[cr]) * (FP16 ? __ldcg(a.nup + cr) : 1.f);
+                }
+                __syncthreads();
+                if (col) {
+#pragma unroll 8
+                    for (int k = 0; k < cn; ++k) {
+                        const int r = sCR[k];
+                        const float cs = sCS[k];
+                        const float cv = x < kp ? col_load<FP16>(a, a.vol, (size_t)sCO[k] + x) : 1.f;
+                        Xs[r * S + x] = fmaf(cs, cv, Xs[r * S + x]);
+                    }
+                }
+            }
+        } else {
+            // (1 - s^2) U first (the tile's own rows), then s C(parent) at path tops
+            if (col) {
+#pragma unroll 4
+                for (int r = 0; r < n; ++r)
+                    Xs[r * S + x] = x < kp ? sW[r] * col_load<FP16>(a, a.vol, base + (size_t)r * kp + x) : sW[r];
+            }
+            for (int r = x; r < n; r += blockDim.x) {
+                if (sR[r] < 0) continue;
+                wait_tile(a, dflags, tile_of_row(a, sR[r]), ntiles);
+                if (FP16) sPW[r] *= __ldcg(a.nd + sR[r]);
+            }
+            __syncthreads();
+            if (col) {
+                for (int r = 0; r < n; ++r) {
+                    const int po = sV[r];
+                    if (po < 0) continue;
+                    Xs[r * S + x] = x < kp ? fmaf(sPW[r], col_load<FP16>(a, a.vout, (size_t)po + x), Xs[r * S + x])
+                                           : Xs[r * S + x] + sPW[r];
+                }
+            }
+        }
+        // ---- the recurrence along the rows, per column
+        if (col) {
+            float acc = 0.f;
+            for (int k = 0; k < n; ++k) {
+                const int r = UP ? n - 1 - k : k;
+                acc = fmaf(sM[r], acc, Xs[r * S + x]);
+                Xs[r * S + x] = acc;
+            }
+        }
+        __syncthreads();
+        // ---- carry from the neighbouring tile of the same path (the protocol of
+        // k_agg: publish the aggregate unless the neighbour's inclusive value is
+        // out, walk back to the nearest inclusive value, apply the carry tile by
+        // tile from it outwards, so the rounding does not depend on timing)
+        const int rfirst = UP ? n - 1 : 0, rlast = UP ? 0 : n - 1;
+        const int dir = UP ? 1 : -1;
+        float cin = 0.f;
+        if (sM[rfirst] != 0.f) {
+            if (x == 0) {
+                const int j1 = u + dir;
+                const int f1 = (j1 >= 0 && j1 < ntiles) ? *(volatile int*)(flags + j1) : 3;
+                s_D = f1 >= 2 ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_D == 0) {
+                if (col) a.aggA[(size_t)u * SCR_STRIDE + x] = Xs[rlast * S + x];
+                if (x == 0) a.aggM[u] = sP[rlast];
+                __threadfence();
+                __syncthreads();
+                if (x == 0) atomicExch(flags + u, 1);
+                if (warp == 0) {
+                    unsigned it = 0;
+                    int D = 0;
+                    for (int off = 0; D == 0;) {
+                        const int jt = u + dir * (off + lane + 1);
+                        const int f = (jt >= 0 && jt < ntiles) ? *(volatile int*)(flags + jt) : 3;
+                        const unsigned incl = __ballot_sync(0xffffffffu, f >= 2);
+                        const unsigned none = __ballot_sync(0xffffffffu, f == 0);
+                        if (incl) {
+                            const int k = __ffs(incl);
+                            const unsigned before = k == 1 ? 0u : (0xffffffffu >> (33 - k));
+                            if (!(none & before)) { D = off + k; break; }
+                        } else if (!none) {
+                            off += 32;
+                            continue;
+                        }
+                        if (++it > spin_cap(a.st) || dev_err(a.st)) {
+                            if (lane == 0) dev_fail(a.st, DEV_TIMEOUT, 57);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    if (lane == 0) s_D = D;
+                }
+                __syncthreads();
+            }
+            __threadfence();
+            const int D = s_D;
+            if (col && D > 0) {
+                const int jI = u + dir * D;
+                cin = (jI >= 0 && jI < ntiles) ? __ldcg(a.inclA + (size_t)jI * SCR_STRIDE + x) : 0.f;
+                for (int k1 = D - 1; k1 >= 1; k1 -= 8) {   // 8 loads in flight, then the fma chain
+                    float av[8], mv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k1 - i;
+                        const int j = u + dir * k;
+                        const bool ok = k >= 1 && j >= 0 && j < ntiles;
+                        av[i] = ok ? __ldcg(a.aggA + (size_t)j * SCR_STRIDE + x) : 0.f;
+                        mv[i] = ok ? __ldcg(a.aggM + j) : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (k1 - i >= 1) cin = fmaf(mv[i], cin, av[i]);
+                }
+            }
+        }
+        // ---- final values, stores, the inclusive value for the next tile
+        if (col)
+            for (int r = 0; r < n; ++r) Xs[r * S + x] = fmaf(sP[r], cin, Xs[r * S + x]);
+        if (FP16) {
+            if (x == kp)
+                for (int r = 0; r < n; ++r) {
+                    sMass[r] = Xs[r * S + kp];
+                    (UP ? a.nup : a.nd)[b + r] = sMass[r];
+                }
+            __syncthreads();
+            if (x < kp)
+                for (int r = 0; r < n; ++r)
+                    a.volh[base + (size_t)r * kp + x] = __float2half_rn(Xs[r * S + x] * (1.f / sMass[r]));
+        } else if (x < kp) {
+            for (int r = 0; r < n; ++r) vdst[base + (size_t)r * kp + x] = Xs[r * S + x];
+        }
+        bool linked;
+        if (UP) linked = !signbit(a.rs[b]) && u > 0;
+        else linked = u + 1 < ntiles && !signbit(a.rs[a.tbeg[u + 1]]);
+        if (linked) {
+            if (col) a.inclA[(size_t)u * SCR_STRIDE + x] = Xs[rlast * S + x];
+            __threadfence();
+            __syncthreads();
+            if (x == 0) atomicExch(flags + u, 2);
+        }
+        // ---- WTA (down pass): lowest slot on ties, per row over the block
+        if (!UP) {
+            for (int r = 0; r < n; ++r) {
+                float bv = x < K ? Xs[r * S + x] : INFINITY;
+                int bs = x < K ? x : INT_MAX;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+                    if (ov < bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
+                }
+                if (lane == 0) {
+                    sBest[r][warp] = bv;
+                    sSlot[r][warp] = bs;
+                }
+            }
+            __syncthreads();
+            for (int r = x; r < n; r += blockDim.x) {
+                float bv = INFINITY;
+                int bs = INT_MAX;
+                for (int w = 0; w < nwarps; ++w)
+                    if (sBest[r][w] < bv || (sBest[r][w] == bv && sSlot[r][w] < bs)) { bv = sBest[r][w]; bs = sSlot[r][w]; }
+                a.disp[a.lay[b + r]] = bs;   // full range: the slot is the label
+            }
+        }
+        // ---- the tile's rows are final: done
+        __threadfence();
+        __syncthreads();
+        if (x == 0) atomicExch(dflags + u, 1);
+    }
+}
+
 CostK cost_consts(const Ctx& c, int l)
 {
     CostK k;
@@ -870,6 +1184,29 @@ static void launch_level_s(const AggArgs& a, bool fp16, int num_sms, int max_per
 {
     if (fp16) launch_level<true, UP, TF>(a, num_sms, max_per_sm, s);
     else launch_level<false, UP, TF>(a, num_sms, max_per_sm, s);
+}
+
+template <bool FP16, bool UP>
+static void launch_col_t(const AggArgs& a, int kp, int num_sms, cudaStream_t s)
+{
+    const int threads = (kp + (FP16 ? 1 : 0) + 31) / 32 * 32;
+    const size_t smem = TILE_FLOATS_COL * sizeof(float);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_agg_col<FP16, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg_col<FP16, UP>, threads, smem);
+    per_sm = max(1, min(per_sm, 8));
+    k_agg_col<FP16, UP><<<num_sms * per_sm, threads, smem, s>>>(a, kp);
+}
+
+template <bool UP>
+static void launch_col(const AggArgs& a, bool fp16, int kp, int num_sms, cudaStream_t s)
+{
+    if (fp16) launch_col_t<true, UP>(a, kp, num_sms, s);
+    else launch_col_t<false, UP>(a, kp, num_sms, s);
 }
 
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
@@ -920,6 +1257,13 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
     const int tf = layer_tile_floats(c, l);
     const int cap = c.tune.agg_ctas_per_sm;
+    const int kp = (d.d + 1 + 3) / 4 * 4;
+    if (tf == TILE_FLOATS_COL) {
+        // one label set, wide rows: a CTA per tile, a thread per label column
+        launch_col<true>(a, fp16, kp, c.num_sms, c.s);
+        launch_col<false>(a, fp16, kp, c.num_sms, c.s);
+        return;
+    }
     if (tf == TILE_FLOATS_SMALL) {
         launch_level_s<true, TILE_FLOATS_SMALL>(a, fp16, c.num_sms, cap, c.s);
         launch_level_s<false, TILE_FLOATS_SMALL>(a, fp16, c.num_sms, cap, c.s);

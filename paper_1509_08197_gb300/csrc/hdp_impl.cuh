@@ -24,6 +24,10 @@
 // warp's share of a tile is short.  TILE_FLOATS_SMALL >= 256 + 4 (the widest
 // FP16 row with its mass column).
 #define TILE_FLOATS_SMALL 512
+// big layers with one label set and rows of at least COL_MIN_KP labels: the
+// column kernel (a CTA per tile, a thread per label column), taller tiles
+#define TILE_FLOATS_COL 8192
+#define COL_MIN_KP 64
 // aggregation CTAs (4 warps) per SM: launch bounds of the three tile sizes
 // and the default cap (occupancy limits each kernel below the cap)
 #define AGG_MINB_2048 4
@@ -186,6 +190,7 @@ inline int layer_tile_floats(const Ctx& c, int l)
 {
     const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.top;
     if (c.dim[l].N < (one_set ? SMALL_TILE_NODES : SMALL_TILE_NODES_HDP)) return TILE_FLOATS_SMALL;
+    if (one_set && (c.dim[l].d + 1 + 3) / 4 * 4 >= COL_MIN_KP) return TILE_FLOATS_COL;
     return one_set ? TILE_FLOATS : TILE_FLOATS_HDP;
 }
 
