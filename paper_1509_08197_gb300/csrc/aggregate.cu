@@ -841,30 +841,30 @@ static size_t agg_smem() { return (size_t)AGG_WARPS * agg_warp_f4<TF>() * sizeof
 
 // ---- column kernel: one-label-set layers with wide rows -----------------------
 // On a full-range layer (or a big top layer) every row holds the same kp
-// labels.  A CTA takes one tile (the same tiles, tickets, flags and look-back
-// scratch as k_agg) and a thread owns one label column x of all its rows: the
-// cost E(v, x) reads the right image at (px - x), so the threads of a row read
-// consecutive pixels; the recurrence along the rows is sequential per column
-// (no cross-thread scan); children's, parents' and the tile's own rows are
-// read and written row by row, coalesced.  FP16 storage adds a column (thread
-// kp) for the support mass.  Used on the layers whose tiles hold
-// TILE_FLOATS_COL floats (kp >= COL_MIN_KP), so a tile has at most
+// labels.  A CTA takes one tile (the same tickets, flags and look-back scratch
+// as k_agg; tiles of TILE_FLOATS_COL floats) and a thread owns two adjacent
+// label columns 2x, 2x+1 of all its rows: the cost E(v, x) reads the right
+// image at (px - x), so the threads of a row read consecutive pixels; the
+// recurrence along the rows is sequential per column (no cross-thread scan);
+// children's, parents' and the tile's own rows move as float2 (FP32) or half2
+// (FP16) per thread, coalesced.  FP16 storage adds thread kp/2 for the support
+// mass (scratch slot kp).  Used when kp >= COL_MIN_KP, so a tile has at most
 // TILE_FLOATS_COL / COL_MIN_KP rows.
 #define COL_MAX_ROWS (TILE_FLOATS_COL / COL_MIN_KP)
-#define COL_THREADS_MAX 288   // 256 label columns + the mass column, in warps
+#define COL_THREADS_MAX 160   // 128 column pairs + the mass thread, in warps
 #define COL_CHUNK 256         // light children staged per chunk
 
 template <bool FP16>
-__device__ __forceinline__ float col_load(const AggArgs& a, const float* v32, size_t off)
+__device__ __forceinline__ float2 col_ld2(const AggArgs& a, const float* v32, size_t off)
 {
-    if (FP16) return __half2float(__ldcg(a.volh + off));
-    return __ldcg(v32 + off);
+    if (FP16) return __half22float2(__ldcg((const __half2*)(a.volh + off)));
+    return __ldcg((const float2*)(v32 + off));
 }
 
 template <bool FP16, bool UP>
 __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
 {
-    extern __shared__ float Xs[];                 // the tile: n rows of S floats
+    extern __shared__ float2 X2[];                // the tile: n rows of S2 column pairs
     __shared__ int sV[COL_MAX_ROWS];              // up: node; down: parent row offset (-1: none)
     __shared__ int sR[COL_MAX_ROWS];              // up: first light child; down: parent row (-1: none)
     __shared__ int sNC[COL_MAX_ROWS];             // up: light children
@@ -880,8 +880,10 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
     __shared__ float sCS[COL_CHUNK];              // weight (x mass in FP16)
     __shared__ int s_t, s_D;
     const int x = threadIdx.x, lane = x & 31, warp = x >> 5, nwarps = blockDim.x >> 5;
-    const int S = kp + (FP16 ? 1 : 0);            // floats per row in shared memory
-    const bool col = x < S;                       // owns a column (label slot, or the mass at x == kp)
+    const int P2 = kp >> 1;                       // column pairs of a row
+    const int S2 = P2 + (FP16 ? 1 : 0);           // pairs per row in shared memory (FP16: + the mass)
+    const bool col = x < S2;                      // owns a pair (or the mass at x == P2)
+    const bool lab2 = x < P2;                     // owns label slots 2x, 2x+1
     const int K = a.dl + 1;                       // labels 0..dl; slots K..kp-1 are padding
     const int ntiles = *a.d_ntiles;
     int* flags = a.tflags + (UP ? 0 : (size_t)ntiles);
@@ -902,6 +904,7 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
         e = min(e, a.N);
         const int n = min(e - b, COL_MAX_ROWS);
         const size_t base = a.roff[b];
+        if (x == 0 && e - b > COL_MAX_ROWS) dev_fail(a.st, DEV_BAD_INPUT, 56);   // a layout this kernel cannot hold
 
         // ---- per-row inputs, one thread per row (a tile may have more rows than the CTA threads)
         for (int r = x; r < n; r += blockDim.x) {
@@ -939,36 +942,40 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
                 sP[r] = acc;
             }
         }
-        if (x == 0 && e - b > COL_MAX_ROWS) dev_fail(a.st, DEV_BAD_INPUT, 56);   // a layout this kernel cannot hold
 
-        // ---- the affine inputs of every (row, column)
+        // ---- the affine inputs of every (row, column pair)
         if (UP) {
             // E (no other tile needed), then the light children's U in child order
             if (col) {
+                const int c0 = 2 * x, c1 = 2 * x + 1;
+                const int l0 = lab2 && c0 < K ? c0 : -1, l1 = lab2 && c1 < K ? c1 : -1;
 #pragma unroll 4
                 for (int r = 0; r < n; ++r) {
-                    float val = 1.f;   // the mass column starts at 1
-                    if (x < kp) {
+                    float2 val = make_float2(1.f, 0.f);   // the mass pair starts at (1, 0)
+                    if (lab2) {
                         const int v = sV[r];
-                        const int lab = x < K ? x : -1;   // full range: slot x holds label x
                         if (a.Ein) {
-                            val = x < a.X ? __ldg(a.Ein + (size_t)v * a.X + x) : 0.f;
+                            val.x = c0 < a.X ? __ldg(a.Ein + (size_t)v * a.X + c0) : 0.f;
+                            val.y = c1 < a.X ? __ldg(a.Ein + (size_t)v * a.X + c1) : 0.f;
                         } else if (a.refD) {
                             const int rd = __ldg(a.refD + v);
-                            val = lab >= 0 && rd >= 0 ? (float)abs(lab - rd) : 0.f;
+                            val.x = l0 >= 0 && rd >= 0 ? (float)abs(l0 - rd) : 0.f;
+                            val.y = l1 >= 0 && rd >= 0 ? (float)abs(l1 - rd) : 0.f;
                         } else {
                             const int px = v % a.W;
-                            val = lab >= 0 ? cost_m(__ldg(a.imL + v), __ldg(a.imR + (v - px) + max(px - lab, 0)), a.ck)
-                                           : 0.f;
+                            const int4 Lp = __ldg(a.imL + v);
+                            const int4* Rrow = a.imR + (v - px);
+                            val.x = l0 >= 0 ? cost_m(Lp, __ldg(Rrow + max(px - l0, 0)), a.ck) : 0.f;
+                            val.y = l1 >= 0 ? cost_m(Lp, __ldg(Rrow + max(px - l1, 0)), a.ck) : 0.f;
                         }
                     }
-                    Xs[r * S + x] = val;
+                    X2[r * S2 + x] = val;
                 }
             }
             // the children in chunks: one thread per child waits for its tile and
-            // stages (row, offset, weight); then every column adds them in child
-            // order (children of a row are consecutive), the loads of a chunk
-            // in flight together
+            // stages (row, offset, weight); then every column pair adds them in
+            // child order (children of a row are consecutive), the loads of a
+            // chunk in flight together
             const int cb = (int)a.lcoff[b], ce = (int)a.lcoff[b + n];
             for (int cc = cb; cc < ce; cc += COL_CHUNK) {
                 const int cn = min(COL_CHUNK, ce - cc);
@@ -976,7 +983,7 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
                 for (int k = x; k < cn; k += blockDim.x) {
                     const int cr = a.lcrow[cc + k];
                     wait_tile(a, dflags, tile_of_row(a, cr), ntiles);
-                    // the child's parent row is in this tile: find it among the rows' child ranges
+                    // the row of this tile whose child range holds child cc + k
                     int lo = 0, hi = n - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
@@ -992,8 +999,11 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
                     for (int k = 0; k < cn; ++k) {
                         const int r = sCR[k];
                         const float cs = sCS[k];
-                        const float cv = x < kp ? col_load<FP16>(a, a.vol, (size_t)sCO[k] + x) : 1.f;
-                        Xs[r * S + x] = fmaf(cs, cv, Xs[r * S + x]);
+                        const float2 cv = lab2 ? col_ld2<FP16>(a, a.vol, (size_t)sCO[k] + 2 * x) : make_float2(1.f, 0.f);
+                        float2 v = X2[r * S2 + x];
+                        v.x = fmaf(cs, cv.x, v.x);
+                        v.y = fmaf(cs, cv.y, v.y);
+                        X2[r * S2 + x] = v;
                     }
                 }
             }
@@ -1001,8 +1011,15 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
             // (1 - s^2) U first (the tile's own rows), then s C(parent) at path tops
             if (col) {
 #pragma unroll 4
-                for (int r = 0; r < n; ++r)
-                    Xs[r * S + x] = x < kp ? sW[r] * col_load<FP16>(a, a.vol, base + (size_t)r * kp + x) : sW[r];
+                for (int r = 0; r < n; ++r) {
+                    const float w = sW[r];
+                    if (lab2) {
+                        const float2 U = col_ld2<FP16>(a, a.vol, base + (size_t)r * kp + 2 * x);
+                        X2[r * S2 + x] = make_float2(w * U.x, w * U.y);
+                    } else {
+                        X2[r * S2 + x] = make_float2(w, 0.f);
+                    }
+                }
             }
             for (int r = x; r < n; r += blockDim.x) {
                 if (sR[r] < 0) continue;
@@ -1011,21 +1028,33 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
             }
             __syncthreads();
             if (col) {
+#pragma unroll 4
                 for (int r = 0; r < n; ++r) {
                     const int po = sV[r];
                     if (po < 0) continue;
-                    Xs[r * S + x] = x < kp ? fmaf(sPW[r], col_load<FP16>(a, a.vout, (size_t)po + x), Xs[r * S + x])
-                                           : Xs[r * S + x] + sPW[r];
+                    const float pw = sPW[r];
+                    float2 v = X2[r * S2 + x];
+                    if (lab2) {
+                        const float2 cp = col_ld2<FP16>(a, a.vout, (size_t)po + 2 * x);
+                        v.x = fmaf(pw, cp.x, v.x);
+                        v.y = fmaf(pw, cp.y, v.y);
+                    } else {
+                        v.x += pw;
+                    }
+                    X2[r * S2 + x] = v;
                 }
             }
         }
         // ---- the recurrence along the rows, per column
         if (col) {
-            float acc = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
             for (int k = 0; k < n; ++k) {
                 const int r = UP ? n - 1 - k : k;
-                acc = fmaf(sM[r], acc, Xs[r * S + x]);
-                Xs[r * S + x] = acc;
+                const float m = sM[r];
+                const float2 v = X2[r * S2 + x];
+                acc.x = fmaf(m, acc.x, v.x);
+                acc.y = fmaf(m, acc.y, v.y);
+                X2[r * S2 + x] = acc;
             }
         }
         __syncthreads();
@@ -1035,7 +1064,7 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
         // tile from it outwards, so the rounding does not depend on timing)
         const int rfirst = UP ? n - 1 : 0, rlast = UP ? 0 : n - 1;
         const int dir = UP ? 1 : -1;
-        float cin = 0.f;
+        float2 cin = make_float2(0.f, 0.f);
         if (sM[rfirst] != 0.f) {
             if (x == 0) {
                 const int j1 = u + dir;
@@ -1044,7 +1073,7 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
             }
             __syncthreads();
             if (s_D == 0) {
-                if (col) a.aggA[(size_t)u * SCR_STRIDE + x] = Xs[rlast * S + x];
+                if (col) *(float2*)(a.aggA + (size_t)u * SCR_STRIDE + 2 * x) = X2[rlast * S2 + x];
                 if (x == 0) a.aggM[u] = sP[rlast];
                 __threadfence();
                 __syncthreads();
@@ -1079,53 +1108,69 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
             const int D = s_D;
             if (col && D > 0) {
                 const int jI = u + dir * D;
-                cin = (jI >= 0 && jI < ntiles) ? __ldcg(a.inclA + (size_t)jI * SCR_STRIDE + x) : 0.f;
+                if (jI >= 0 && jI < ntiles) cin = __ldcg((const float2*)(a.inclA + (size_t)jI * SCR_STRIDE + 2 * x));
                 for (int k1 = D - 1; k1 >= 1; k1 -= 8) {   // 8 loads in flight, then the fma chain
-                    float av[8], mv[8];
+                    float2 av[8];
+                    float mv[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int k = k1 - i;
                         const int j = u + dir * k;
                         const bool ok = k >= 1 && j >= 0 && j < ntiles;
-                        av[i] = ok ? __ldcg(a.aggA + (size_t)j * SCR_STRIDE + x) : 0.f;
+                        av[i] = ok ? __ldcg((const float2*)(a.aggA + (size_t)j * SCR_STRIDE + 2 * x)) : make_float2(0.f, 0.f);
                         mv[i] = ok ? __ldcg(a.aggM + j) : 0.f;
                     }
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        if (k1 - i >= 1) cin = fmaf(mv[i], cin, av[i]);
+                        if (k1 - i >= 1) {
+                            cin.x = fmaf(mv[i], cin.x, av[i].x);
+                            cin.y = fmaf(mv[i], cin.y, av[i].y);
+                        }
                 }
             }
         }
         // ---- final values, stores, the inclusive value for the next tile
         if (col)
-            for (int r = 0; r < n; ++r) Xs[r * S + x] = fmaf(sP[r], cin, Xs[r * S + x]);
+            for (int r = 0; r < n; ++r) {
+                const float p = sP[r];
+                float2 v = X2[r * S2 + x];
+                v.x = fmaf(p, cin.x, v.x);
+                v.y = fmaf(p, cin.y, v.y);
+                X2[r * S2 + x] = v;
+            }
         if (FP16) {
-            if (x == kp)
+            if (x == P2)
                 for (int r = 0; r < n; ++r) {
-                    sMass[r] = Xs[r * S + kp];
+                    sMass[r] = X2[r * S2 + P2].x;
                     (UP ? a.nup : a.nd)[b + r] = sMass[r];
                 }
             __syncthreads();
-            if (x < kp)
-                for (int r = 0; r < n; ++r)
-                    a.volh[base + (size_t)r * kp + x] = __float2half_rn(Xs[r * S + x] * (1.f / sMass[r]));
-        } else if (x < kp) {
-            for (int r = 0; r < n; ++r) vdst[base + (size_t)r * kp + x] = Xs[r * S + x];
+            if (lab2)
+                for (int r = 0; r < n; ++r) {
+                    const float inv = 1.f / sMass[r];
+                    const float2 v = X2[r * S2 + x];
+                    *(__half2*)(a.volh + base + (size_t)r * kp + 2 * x) = __floats2half2_rn(v.x * inv, v.y * inv);
+                }
+        } else if (lab2) {
+            for (int r = 0; r < n; ++r) *(float2*)(vdst + base + (size_t)r * kp + 2 * x) = X2[r * S2 + x];
         }
         bool linked;
         if (UP) linked = !signbit(a.rs[b]) && u > 0;
         else linked = u + 1 < ntiles && !signbit(a.rs[a.tbeg[u + 1]]);
         if (linked) {
-            if (col) a.inclA[(size_t)u * SCR_STRIDE + x] = Xs[rlast * S + x];
+            if (col) *(float2*)(a.inclA + (size_t)u * SCR_STRIDE + 2 * x) = X2[rlast * S2 + x];
             __threadfence();
             __syncthreads();
             if (x == 0) atomicExch(flags + u, 2);
         }
         // ---- WTA (down pass): lowest slot on ties, per row over the block
         if (!UP) {
+            const int c0 = 2 * x, c1 = 2 * x + 1;
             for (int r = 0; r < n; ++r) {
-                float bv = x < K ? Xs[r * S + x] : INFINITY;
-                int bs = x < K ? x : INT_MAX;
+                const float2 v = lab2 ? X2[r * S2 + x] : make_float2(INFINITY, INFINITY);
+                float bv = lab2 && c0 < K ? v.x : INFINITY;
+                int bs = lab2 && c0 < K ? c0 : INT_MAX;
+                if (lab2 && c1 < K && v.y < bv) { bv = v.y; bs = c1; }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -1189,8 +1234,8 @@ static void launch_level_s(const AggArgs& a, bool fp16, int num_sms, int max_per
 template <bool FP16, bool UP>
 static void launch_col_t(const AggArgs& a, int kp, int num_sms, cudaStream_t s)
 {
-    const int threads = (kp + (FP16 ? 1 : 0) + 31) / 32 * 32;
-    const size_t smem = TILE_FLOATS_COL * sizeof(float);
+    const int threads = (kp / 2 + (FP16 ? 1 : 0) + 31) / 32 * 32;
+    const size_t smem = (TILE_FLOATS_COL + 2 * COL_MAX_ROWS) * sizeof(float);
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(k_agg_col<FP16, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
