@@ -189,7 +189,7 @@ static void layout_buffers(Ctx& c)
     c.ints = carve<int>(c, IDX_COUNT);
     c.st = carve<DevStatus>(c, 1);
     c.zero64 = carve<unsigned long long>(c, 4);
-    c.tmp_words = 4 * radix_tmp_words((int)E2) + 4 * scan_tmp_words((int)E2) + 4096;
+    c.tmp_words = radix_tmp_words((int)E2) + 4096;
     c.tmp = carve<uint32_t>(c, c.tmp_words);
     c.hist = carve<unsigned long long>(c, HDP_MAX_LEVELS * 256);
     // single-pass scans: the longest is over the 2N edge slots (radix

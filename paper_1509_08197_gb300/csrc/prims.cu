@@ -1,83 +1,157 @@
 // Stable LSD radix sort and scans (see prims.cuh).
 #include "prims.cuh"
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, const int* d_n, int shift, uint32_t* hist, int nblocks)
+// ------------------------------------------------------- one-sweep radix sort ---
+// Stable LSD radix sort, 8-bit digits, one launch per digit pass (after one
+// histogram launch per sort).  k_rs_ghist counts every pass's digits over all
+// keys.  In k_rs_onesweep each block takes a tile of RS_TILE keys by an atomic
+// ticket (so its predecessors are resident or done), counts the tile's digits
+// per warp, and for each digit (one thread per digit) publishes the tile's
+// count, walks back over the predecessors' published counts to the nearest
+// inclusive prefix (decoupled look-back) and publishes its own inclusive
+// prefix.  An item's position is the digit's global start, plus the items of
+// that digit in earlier tiles, in earlier warps of the tile, in earlier chunks
+// of the warp, then in lower lanes of the same chunk: the sort is stable.
+#define RS_FLAG_AGG (1u << 30)
+#define RS_FLAG_INC (2u << 30)
+#define RS_COUNT ((1u << 30) - 1u)
+
+__global__ void k_rs_ghist(const uint32_t* __restrict__ keys, const int* d_n, int first_bit, int npass, uint32_t* ghist)
 {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
+    __shared__ uint32_t cnt[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += RS_THREADS) cnt[i] = 0;
     __syncthreads();
     const int n = *d_n;
     const long long base = (long long)blockIdx.x * RS_TILE;
-    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-        long long idx = base + i;
-        if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255u], 1u);
+    for (int c = 0; c < RS_TILE / RS_THREADS; ++c) {
+        const long long idx = base + c * RS_THREADS + threadIdx.x;
+        const bool valid = idx < n;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
+        const uint32_t k = keys[idx];
+        for (int p = 0; p < npass; ++p) {
+            const unsigned d = (k >> (first_bit + 8 * p)) & 255u;
+            const unsigned peers = __match_any_sync(vmask, d);   // one shared atomic per digit and warp
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[p * 256 + d], __popc(peers));
+        }
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+    for (int i = threadIdx.x; i < npass * 256; i += RS_THREADS)
+        if (cnt[i]) atomicAdd(&ghist[i], cnt[i]);
 }
 
-// Each warp owns 256 consecutive items of the tile (8 chunks of 32), so the
-// rank of an item is: items of the same digit in earlier tiles (hist), in
-// earlier warps of this tile, in earlier chunks of this warp, then in lower
-// lanes of the same chunk.  This keeps the sort stable.
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* kout,
-                             uint32_t* vout, const int* d_n, int shift, const uint32_t* hist, int nblocks)
+__global__ void __launch_bounds__(RS_THREADS) k_rs_onesweep(const uint32_t* __restrict__ kin,
+                                                            const uint32_t* __restrict__ vin, uint32_t* kout,
+                                                            uint32_t* vout, const int* d_n, int shift,
+                                                            const uint32_t* __restrict__ ghist, uint32_t* status,
+                                                            unsigned* ticket, DevStatus* st)
 {
     __shared__ uint32_t cnt[8][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 8 * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t wsum[8];
+    __shared__ int s_tile;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    for (int i = t; i < 8 * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
+    const int tile = s_tile;
     const int n = *d_n;
-    const long long wbase = (long long)blockIdx.x * RS_TILE + warp * 256;
+    const int nt = (int)cdiv<long long>(n, RS_TILE);
+    if (tile >= nt) return;   // the whole block
+    const long long wbase = (long long)tile * RS_TILE + warp * 256;
+    uint32_t key[8];
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
-        long long idx = wbase + c * 32 + lane;
-        bool valid = idx < n;
-        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const long long idx = wbase + c * 32 + lane;
+        const bool valid = idx < n;
+        key[c] = valid ? kin[idx] : 0u;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const long long idx = wbase + c * 32 + lane;
+        const bool valid = idx < n;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
         if (valid) {
-            unsigned d = (kin[idx] >> shift) & 255u;
-            unsigned peers = __match_any_sync(vmask, d);
+            const unsigned d = (key[c] >> shift) & 255u;
+            const unsigned peers = __match_any_sync(vmask, d);
             if (lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;   // RS_THREADS == 256 digits
-        uint32_t run = 0;
-        for (int w = 0; w < 8; ++w) {
-            uint32_t t = cnt[w][d];
-            cnt[w][d] = run;
-            run += t;
-        }
+    // thread t = digit t: offsets of the warps, the tile's count, then the look-back
+    const int d = t;   // RS_THREADS == 256 digits
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t c = cnt[w][d];
+        cnt[w][d] = run;
+        run += c;
     }
+    uint32_t prefix = 0;
+    if (tile == 0) {
+        atomicExch(status + d, RS_FLAG_INC | run);
+    } else {
+        atomicExch(status + (size_t)tile * 256 + d, RS_FLAG_AGG | run);
+        const unsigned cap = spin_cap(st);
+        unsigned it = 0;
+        for (int j = tile - 1; j >= 0;) {
+            const uint32_t w = *(volatile const uint32_t*)(status + (size_t)j * 256 + d);
+            if (!(w & ~RS_COUNT)) {
+                if (++it > cap || dev_err(st)) {
+                    dev_fail(st, DEV_TIMEOUT, 64);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            prefix += w & RS_COUNT;
+            if ((w & ~RS_COUNT) == RS_FLAG_INC) break;
+            --j;
+        }
+        atomicExch(status + (size_t)tile * 256 + d, RS_FLAG_INC | (prefix + run));
+    }
+    // the digit's global start: exclusive scan of the pass's digit counts
+    uint32_t g = ghist[d], inc = g;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    gbase[d] = before + inc - g + prefix;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
-        long long idx = wbase + c * 32 + lane;
-        bool valid = idx < n;
-        unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        unsigned d = 0, peers = 0;
-        uint32_t key = 0, pos = 0;
+        const long long idx = wbase + c * 32 + lane;
+        const bool valid = idx < n;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        unsigned dd = 0, peers = 0;
         if (valid) {
-            key = kin[idx];
-            d = (key >> shift) & 255u;
-            peers = __match_any_sync(vmask, d);
-            pos = hist[(size_t)d * nblocks + blockIdx.x] + cnt[warp][d] + __popc(peers & lt);
-            kout[pos] = key;
+            dd = (key[c] >> shift) & 255u;
+            peers = __match_any_sync(vmask, dd);
+            const uint32_t pos = gbase[dd] + cnt[warp][dd] + __popc(peers & lt);
+            kout[pos] = key[c];
             if (vin) vout[pos] = vin[idx];
         }
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) cnt[warp][dd] += __popc(peers);
         __syncwarp();
     }
 }
 
 size_t scan_tmp_words(int n_max) { return (size_t)cdiv<long long>(n_max > 0 ? n_max : 1, SCAN_TILE) + 1; }
 
+// one-sweep scratch: the digit counts of up to 4 passes, a ticket per pass,
+// then the tiles' digit states of up to 4 passes
 size_t radix_tmp_words(int n_max)
 {
     size_t nb = (size_t)cdiv<long long>(n_max > 0 ? n_max : 1, RS_TILE);
-    return 256 * nb + scan_tmp_words((int)(256 * nb)) + 2;
+    return 4 * 256 + 64 + 4 * 256 * nb;
 }
 
 __global__ void k_set_int(int* out, int v) { out[0] = v; }
@@ -337,24 +411,22 @@ int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int
                uint32_t* tmp, const ScanState& ss, cudaStream_t s, int first_bit)
 {
     if (n_max <= 0 || key_bits <= 0) return 0;
-    int nb = (int)cdiv<long long>(n_max, RS_TILE);
-    // the histogram is laid out for nb_max tiles; unused tiles hold zeros and
-    // the device-side count limits the scan to the live part.
-    uint32_t* hist = tmp;
-    uint32_t* stmp = tmp + 256 * (size_t)nb;
-    int* hlen = (int*)(stmp + scan_tmp_words(256 * nb));
-    // digit-major histogram with a fixed stride of nb tiles (tiles past the
-    // live count hold zeros): every pass scans all of it
-    k_set_int<<<1, 1, 0, s>>>(hlen, 256 * nb);
+    const int nb = (int)cdiv<long long>(n_max, RS_TILE);
+    const int npass = (key_bits + 7) / 8;   // at most 4 (32-bit keys)
+    uint32_t* ghist = tmp;                        // [npass][256]
+    unsigned* tickets = tmp + 4 * 256;            // [npass]
+    uint32_t* status = tmp + 4 * 256 + 64;        // [npass][nb][256]
+    // one clearing of the counts, tickets and tile states of every pass
+    cudaMemsetAsync(tmp, 0, sizeof(uint32_t) * (4 * 256 + 64 + (size_t)npass * nb * 256), s);
+    k_rs_ghist<<<nb, RS_THREADS, 0, s>>>(k0, d_n, first_bit, npass, ghist);
     int cur = 0;
-    for (int shift = first_bit; shift < first_bit + key_bits; shift += 8) {
+    for (int p = 0; p < npass; ++p) {
         const uint32_t* ki = cur ? k1 : k0;
         const uint32_t* vi = cur ? v1 : v0;
         uint32_t* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
-        k_rs_hist<<<nb, RS_THREADS, 0, s>>>(ki, d_n, shift, hist, nb);
-        scan_u32(hist, hist, hlen, 256 * nb, true, ss, nullptr, s);
-        k_rs_scatter<<<nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, d_n, shift, hist, nb);
+        k_rs_onesweep<<<nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, d_n, first_bit + 8 * p, ghist + 256 * p,
+                                                status + (size_t)p * nb * 256, tickets + p, ss.st);
         cur ^= 1;
     }
     return cur;

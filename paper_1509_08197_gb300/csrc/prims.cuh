@@ -189,14 +189,11 @@ void scan_i4_inclusive(const I4* in, I4* out, const int* d_n, int n_max, const S
 #define RS_THREADS 256
 #define RS_TILE 2048     // 8 warps x 256 items
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, const int* d_n, int shift, uint32_t* hist, int nblocks);
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* kout,
-                             uint32_t* vout, const int* d_n, int shift, const uint32_t* hist, int nblocks);
 
 // Stable LSD radix sort of (key, value) pairs on bits [first_bit, first_bit + key_bits).  vals may
 // be null (keys only).  Buffers ping-pong between (k0, v0) and (k1, v1); the
 // return value says where the result is: 0 -> (k0, v0), 1 -> (k1, v1).
-// tmp: at least 256 * cdiv(n_max, RS_TILE) + cdiv(that, SCAN_TILE) uint32.
+// tmp: at least radix_tmp_words(n_max) uint32 (one-sweep digit counts and tile states).
 int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const int* d_n, int n_max, int key_bits,
                uint32_t* tmp, const ScanState& ss, cudaStream_t s, int first_bit = 0);
 size_t radix_tmp_words(int n_max);
