@@ -258,7 +258,10 @@ int hdp_graph_launch(hdp_ctx* ctx);
  * streams and joins back, so the call can be captured in a CUDA graph.
  * hdp_batch_graph_capture captures the whole batch once (the graph is kept in
  * ctxs[0], *n_kernels receives its kernel count); hdp_batch_graph_launch
- * replays it on the stream of ctxs[0]. */
+ * replays it on the stream of ctxs[0].  The CUDA runtime maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware queues (default 8, a process
+ * environment variable read when CUDA starts); with many pairs set it to 32
+ * (64 mixed pairs: 123 ms with 8, 75 ms with 32). */
 int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right, const int* pitch,
                     int32_t* const* d_disp_out);
 int hdp_batch_graph_capture(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right,
