@@ -1254,7 +1254,7 @@ static void launch_col(const AggArgs& a, bool fp16, int kp, int num_sms, cudaStr
     else launch_col_t<false, UP>(a, kp, num_sms, s);
 }
 
-void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
+static AggArgs make_agg_args(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
 {
     const LayerDims& d = c.dim[l];
     const bool hdp = c.p.mode == HDP_MODE_HDP && l < c.top;
@@ -1289,16 +1289,28 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     a.nd = c.nfull;
     a.tickets = c.tickets;
     a.tflags = c.tflags;
+    a.dflags = c.tflags + 2 * c.max_tiles;
     a.aggA = c.aggA;
     a.inclA = c.inclA;
     a.aggM = c.aggM;
     a.disp = c.disp[l];
     a.st = c.st;
-    // one launch per pass over every tile of the layer, in dependency order
-    // (look-back flags and done flags of both passes are cleared together)
-    a.dflags = c.tflags + 2 * c.max_tiles;
+    return a;
+}
+
+// tickets, look-back flags and done flags of both passes, on the context's stream
+void aggregate_clear(Ctx& c)
+{
     cudaMemsetAsync(c.tickets, 0, sizeof(int) * 2 * MAX_LIGHT_LEVELS, c.s);
     cudaMemsetAsync(c.tflags, 0, sizeof(int) * 4 * c.max_tiles, c.s);
+}
+
+void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down)
+{
+    const LayerDims& d = c.dim[l];
+    const AggArgs a = make_agg_args(c, l, Ein, vol_up, vol_down);
+    // one launch per pass over every tile of the layer, in dependency order
+    aggregate_clear(c);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
     const int tf = layer_tile_floats(c, l);
     const int cap = c.tune.agg_ctas_per_sm;
@@ -1322,3 +1334,132 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
 }
 
 void launch_aggregate(Ctx& c, int l) { launch_aggregate_ex(c, l, nullptr, nullptr, nullptr); }
+
+// ---- one launch per pass over the tiles of many pairs (batches) -------------
+// The pairs' arguments travel as one kernel parameter (at most AGG_MULTI_MAX
+// pairs, under the 32 KB parameter limit).  Tickets run over the pairs one
+// after another, each pair's tiles in its own dependency order, so a tile only
+// waits on an earlier ticket of its own pair and every wait ends.
+#define AGG_MULTI_MAX 64
+
+struct AggMulti {
+    int n;
+    AggArgs a[AGG_MULTI_MAX];
+};
+
+template <bool FP16, bool UP, int TF>
+__global__ void __launch_bounds__(AGG_THREADS, TF == TILE_FLOATS ? AGG_MINB_2048 : TF == TILE_FLOATS_HDP ? AGG_MINB_1024
+                                                                                                    : AGG_MINB_512)
+    k_agg_multi(const __grid_constant__ AggMulti m)
+{
+    constexpr int RM = tile_rows_max(TF);
+    extern __shared__ float4 smem[];
+    __shared__ int pre[AGG_MULTI_MAX + 1];
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int p = 0; p < m.n; ++p) {
+            pre[p] = s;
+            s += *m.a[p].d_ntiles;
+        }
+        pre[m.n] = s;
+    }
+    __syncthreads();
+    const int total = pre[m.n];
+    if (total == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* X = smem + (size_t)warp * agg_warp_f4<TF>();
+    float* M = (float*)(X + TF / 4);
+    float* P = M + RM;
+    float* PT = P + RM;
+    float* Q = PT + RM;
+    float4* CIN = (float4*)(Q + RM);
+    int* CO = (int*)(CIN + 80);
+    float* CS = (float*)(CO + AGG_CHUNK);
+    __shared__ __align__(8) uint64_t bars[AGG_WARPS];
+    uint64_t* bar = bars + warp;
+    uint32_t bar_phase = 0;
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    // the batch's own ticket: slot 1 of the first pair's tickets of this pass
+    int* tk = m.a[0].tickets + (UP ? 0 : MAX_LIGHT_LEVELS) + 1;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(tk, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        int p = 0;
+        while (p + 1 < m.n && pre[p + 1] <= t) ++p;
+        const int tl = t - pre[p], nt = pre[p + 1] - pre[p];
+        const int u = UP ? nt - 1 - tl : tl;
+        tile_pass<FP16, UP, TF>(m.a[p], u, X, M, P, PT, Q, CIN, CO, CS, bar, bar_phase);
+    }
+    if (lane == 0) bulk_store_complete();
+}
+
+template <bool FP16, bool UP, int TF>
+static void launch_multi_t(const AggMulti& m, int num_sms, int max_per_sm, cudaStream_t s)
+{
+    const size_t sm = agg_smem<TF>();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_agg_multi<FP16, UP, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_agg_multi<FP16, UP, TF>, AGG_THREADS, sm);
+        if (per_sm < 1) per_sm = 1;
+    }
+    k_agg_multi<FP16, UP, TF><<<num_sms * min(per_sm, max_per_sm), AGG_THREADS, sm, s>>>(m);
+}
+
+template <bool UP>
+static void launch_multi(const AggMulti& m, int tf, bool fp16, int num_sms, int cap, cudaStream_t s)
+{
+    if (tf == TILE_FLOATS_SMALL) {
+        if (fp16) launch_multi_t<true, UP, TILE_FLOATS_SMALL>(m, num_sms, cap, s);
+        else launch_multi_t<false, UP, TILE_FLOATS_SMALL>(m, num_sms, cap, s);
+    } else if (tf == TILE_FLOATS_HDP) {
+        if (fp16) launch_multi_t<true, UP, TILE_FLOATS_HDP>(m, num_sms, cap, s);
+        else launch_multi_t<false, UP, TILE_FLOATS_HDP>(m, num_sms, cap, s);
+    } else {
+        if (fp16) launch_multi_t<true, UP, TILE_FLOATS>(m, num_sms, cap, s);
+        else launch_multi_t<false, UP, TILE_FLOATS>(m, num_sms, cap, s);
+    }
+}
+
+// Layer l of every context, on stream s, after each context's aggregate_clear
+// (and the layer's forest and layout) has completed: the warp-kernel pairs
+// grouped by (tile size, storage), one launch per group and pass; pairs of the
+// column kernel one by one.  Returns the number of launches.
+int launch_aggregate_multi(Ctx* const* cs, int n, int l, cudaStream_t s)
+{
+    int launches = 0;
+    static AggMulti m;   // host staging only: kernel parameters are copied at launch (or into the graph)
+    const int tfs[3] = {TILE_FLOATS_SMALL, TILE_FLOATS_HDP, TILE_FLOATS};
+    for (int fp = 0; fp < 2; ++fp)
+        for (int k = 0; k < 3; ++k) {
+            int i = 0;
+            while (i < n) {
+                m.n = 0;
+                int num_sms = 0, cap = 8;
+                for (; i < n && m.n < AGG_MULTI_MAX; ++i) {
+                    Ctx& c = *cs[i];
+                    if ((c.p.storage == HDP_STORE_FP16) != (fp == 1) || layer_tile_floats(c, l) != tfs[k]) continue;
+                    m.a[m.n++] = make_agg_args(c, l, nullptr, nullptr, nullptr);
+                    num_sms = c.num_sms;
+                    cap = min(cap, c.tune.agg_ctas_per_sm);
+                }
+                if (m.n == 0) continue;
+                launch_multi<true>(m, tfs[k], fp == 1, num_sms, cap, s);
+                launch_multi<false>(m, tfs[k], fp == 1, num_sms, cap, s);
+                launches += 2;
+            }
+        }
+    for (int i = 0; i < n; ++i) {
+        Ctx& c = *cs[i];
+        if (layer_tile_floats(c, l) != TILE_FLOATS_COL) continue;
+        const AggArgs a = make_agg_args(c, l, nullptr, nullptr, nullptr);
+        const int kp = (c.dim[l].d + 1 + 3) / 4 * 4;
+        launch_col<true>(a, c.p.storage == HDP_STORE_FP16, kp, c.num_sms, s);
+        launch_col<false>(a, c.p.storage == HDP_STORE_FP16, kp, c.num_sms, s);
+        launches += 2;
+    }
+    return launches;
+}

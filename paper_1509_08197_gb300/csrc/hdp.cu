@@ -404,7 +404,8 @@ extern "C" int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_
     return check_launch(ctx, "hdp_build_trees");
 }
 
-extern "C" int hdp_run_level(hdp_ctx* ctx, int level)
+// hdp_run_level without the aggregation: interval prediction, edges, forest, orders
+static int run_level_pre(hdp_ctx* ctx, int level)
 {
     if (!ctx) return HDP_ERR_ARG;
     Ctx& c = ctx->c;
@@ -428,6 +429,14 @@ extern "C" int hdp_run_level(hdp_ctx* ctx, int level)
         mark(ctx, level, 1);
         build_layer_tree(ctx, level);
     }
+    return HDP_OK;
+}
+
+extern "C" int hdp_run_level(hdp_ctx* ctx, int level)
+{
+    int rc = run_level_pre(ctx, level);
+    if (rc) return rc;
+    Ctx& c = ctx->c;
     if (!ctx->ev_used[level][4]) mark(ctx, level, 4);
     launch_aggregate(c, level);
     mark(ctx, level, 5);
@@ -1116,6 +1125,8 @@ extern "C" int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d
 }
 
 // ------------------------------------------------------------------ batch ---
+#define HDP_BATCH_MAX 1024
+
 extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right,
                                const int* pitch, int32_t* const* d_out)
 {
@@ -1133,12 +1144,50 @@ extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_le
     for (int i = 1; i < n; ++i) TRY_CUDA(cudaStreamWaitEvent(ctxs[i]->c.s, ctx->fork, 0));
     // no side streams inside a batch: the pairs already fill the GPU, and twice
     // the concurrent branches made the batch graph 1.6x slower
-    for (int i = 0; i < n; ++i) {
-        ctxs[i]->use_side = 0;
-        int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
-        if (!rc) rc = hdp_match(ctxs[i], d_out[i]);
-        ctxs[i]->use_side = 1;
-        if (rc) return rc;
+    bool same_layers = true;
+    for (int i = 1; i < n; ++i) same_layers = same_layers && ctxs[i]->c.nlev == ctx->c.nlev;
+    if (!same_layers || n > HDP_BATCH_MAX) {
+        // pairs of different depths: every pair runs its own chain
+        for (int i = 0; i < n; ++i) {
+            ctxs[i]->use_side = 0;
+            int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
+            if (!rc) rc = hdp_match(ctxs[i], d_out[i]);
+            ctxs[i]->use_side = 1;
+            if (rc) return rc;
+        }
+    } else {
+        // level by level: each pair prepares the level on its own stream (interval
+        // prediction, edges, forest, orders), then one aggregation launch per pass
+        // and tile class takes the tiles of every pair (a6-a7 of the batch in one
+        // launch per level), then the pairs go on
+        Ctx* cs[HDP_BATCH_MAX];
+        for (int i = 0; i < n; ++i) {
+            cs[i] = &ctxs[i]->c;
+            ctxs[i]->use_side = 0;
+            int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
+            ctxs[i]->use_side = 1;
+            if (rc) return rc;
+            ctxs[i]->c.refined = 0;
+        }
+        for (int l = ctx->c.top; l >= 0; --l) {
+            for (int i = 0; i < n; ++i) {
+                int rc = run_level_pre(ctxs[i], l);
+                if (rc) return rc;
+                aggregate_clear(ctxs[i]->c);
+                if (i > 0) {
+                    TRY_CUDA(cudaEventRecord(ctxs[i]->join, ctxs[i]->c.s));
+                    TRY_CUDA(cudaStreamWaitEvent(ctx->c.s, ctxs[i]->join, 0));
+                }
+            }
+            launch_aggregate_multi(cs, n, l, ctx->c.s);
+            int rc = check_launch(ctx, "hdp_match_batch");
+            if (rc) return rc;
+            TRY_CUDA(cudaEventRecord(ctx->fork, ctx->c.s));
+            for (int i = 1; i < n; ++i) TRY_CUDA(cudaStreamWaitEvent(ctxs[i]->c.s, ctx->fork, 0));
+        }
+        for (int i = 0; i < n; ++i)
+            TRY_CUDA(cudaMemcpyAsync(d_out[i], ctxs[i]->c.disp[0], sizeof(int32_t) * ctxs[i]->c.dim[0].N,
+                                     cudaMemcpyDeviceToDevice, ctxs[i]->c.s));
     }
     for (int i = 1; i < n; ++i) {
         TRY_CUDA(cudaEventRecord(ctxs[i]->join, ctxs[i]->c.s));

@@ -214,6 +214,9 @@ void launch_bfs(Ctx& c, int l);
 // aggregate.cu
 void launch_aggregate(Ctx& c, int l);
 void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* vol_down);
+// batches: clear a context's aggregation state, then aggregate layer l of many contexts together
+void aggregate_clear(Ctx& c);
+int launch_aggregate_multi(Ctx* const* cs, int n, int l, cudaStream_t s);
 
 // grad.cu
 // GMM_l by EM (gmm.cu)

@@ -11,7 +11,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_batch_equals_one_at_a_time():
+@pytest.mark.parametrize("depths", ["mixed", "equal"])
+def test_batch_equals_one_at_a_time(depths):
+    # mixed depths: every pair runs its own chain; equal depths: level by level,
+    # one aggregation launch per pass and tile class over every pair's tiles
     dev = torch.device("cuda:0")
     specs = [("tiny", dict()), ("tiny", dict(width=77, height=41, max_disp=31)),
              ("tiny", dict(width=120, height=90, max_disp=47)), ("third", dict())]
@@ -20,7 +23,8 @@ def test_batch_equals_one_at_a_time():
         p = workload_pair(name, index=i, **over)
         pairs.append(p)
         H, W, _ = p.left.shape
-        params.append(hdp.HDPParams(width=W, height=H, max_disp=p.max_disp, levels=3 if W < 200 else 4,
+        levels = (3 if W < 200 else 4) if depths == "mixed" else 3
+        params.append(hdp.HDPParams(width=W, height=H, max_disp=p.max_disp, levels=levels,
                                     tree="mst" if i % 2 == 0 else "st", storage="fp16" if i == 3 else "fp32"))
     # two contexts on caller streams, two that own theirs
     ctxs = [hdp.hdp_create(hp, torch.cuda.Stream(device=dev)) if i < 2 else hdp.hdp_create_own_stream(hp)
