@@ -18,9 +18,14 @@ struct hdp_ctx {
     int ev_used[HDP_MAX_LEVELS][6] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // hdp_match_host: the pyramid on the staging buffers, captured on first use
+    cudaGraph_t host_graph = nullptr;
+    cudaGraphExec_t host_exec = nullptr;
     bool own_stream = false;   // created by hdp_create_own_stream, destroyed with the context
     int use_side = 1;          // 0 inside a batch: the other pairs already fill the GPU
 };
+
+static void drop_host_graph(hdp_ctx* ctx);
 
 static void mark(hdp_ctx* ctx, int l, int k)
 {
@@ -508,6 +513,7 @@ extern "C" int hdp_set_tuning(hdp_ctx* ctx, const hdp_tuning* t)
     if (!ctx || !t) return HDP_ERR_ARG;
     if (const char* why = tuning_error(*t)) return fail(ctx, HDP_ERR_ARG, why);
     ctx->c.tune = *t;
+    drop_host_graph(ctx);   // captured with the old launch shapes
     return HDP_OK;
 }
 
@@ -577,6 +583,7 @@ extern "C" int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* 
         c.tune = keep;
     }
     ctx->timing = timing;
+    drop_host_graph(ctx);   // captured with other launch shapes
     if (rc != HDP_OK) return rc;
     if (out) *out = c.tune;
     return HDP_OK;
@@ -609,6 +616,12 @@ extern "C" int hdp_refine(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_
     return check_launch(ctx, "hdp_refine");
 }
 
+static void drop_host_graph(hdp_ctx* ctx)
+{
+    if (ctx->host_exec) { cudaGraphExecDestroy(ctx->host_exec); ctx->host_exec = nullptr; }
+    if (ctx->host_graph) { cudaGraphDestroy(ctx->host_graph); ctx->host_graph = nullptr; }
+}
+
 extern "C" int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right, int32_t* h_disp_out)
 {
     if (!ctx || !h_left || !h_right || !h_disp_out) return HDP_ERR_ARG;
@@ -616,10 +629,32 @@ extern "C" int hdp_match_host(hdp_ctx* ctx, const uint8_t* h_left, const uint8_t
     const size_t bytes = 3 * (size_t)c.dim[0].N;
     TRY_CUDA(cudaMemcpyAsync(c.stage_l, h_left, bytes, cudaMemcpyHostToDevice, c.s));
     TRY_CUDA(cudaMemcpyAsync(c.stage_r, h_right, bytes, cudaMemcpyHostToDevice, c.s));
-    int rc = hdp_build_trees(ctx, c.stage_l, c.stage_r, 3 * c.p.width);
-    if (rc) return rc;
-    rc = hdp_match(ctx, c.disp_host_stage);
-    if (rc) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool graphable = c.s && !ctx->timing && cudaStreamIsCapturing(c.s, &cs) == cudaSuccess &&
+                           cs == cudaStreamCaptureStatusNone;
+    int rc = HDP_OK;
+    if (graphable) {
+        // the device side of every call is the same work on the same staging
+        // buffers: capture it once (first call) and replay it
+        if (!ctx->host_exec) {
+            if (c.s2) TRY_CUDA(cudaStreamSynchronize(c.s2));   // a capture cannot wait on earlier side work
+            for (int l = 0; l < HDP_MAX_LEVELS; ++l) c.side_pending[l] = 0;
+            TRY_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+            rc = hdp_build_trees(ctx, c.stage_l, c.stage_r, 3 * c.p.width);
+            if (!rc) rc = hdp_match(ctx, c.disp_host_stage);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c.s, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return fail(ctx, HDP_ERR_CUDA, std::string("host-path capture: ") + cudaGetErrorString(e));
+            ctx->host_graph = g;
+            TRY_CUDA(cudaGraphInstantiate(&ctx->host_exec, g, 0));
+        }
+        TRY_CUDA(cudaGraphLaunch(ctx->host_exec, c.s));
+    } else {
+        rc = hdp_build_trees(ctx, c.stage_l, c.stage_r, 3 * c.p.width);
+        if (!rc) rc = hdp_match(ctx, c.disp_host_stage);
+        if (rc) return rc;
+    }
     TRY_CUDA(cudaMemcpyAsync(h_disp_out, c.disp_host_stage, sizeof(int32_t) * c.dim[0].N, cudaMemcpyDeviceToHost, c.s));
     return hdp_sync(ctx);
 }
@@ -655,6 +690,7 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
         if (ctx->c.ev_side[l]) cudaEventDestroy(ctx->c.ev_side[l]);
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    drop_host_graph(ctx);
     if (ctx->own_stream && ctx->c.s) cudaStreamDestroy(ctx->c.s);
     delete ctx;
     return rc;

@@ -317,3 +317,28 @@ def test_fp16_storage_error(case):
     for l in r16:
         g16, o = r16[l]
         _assert_fp16_layer(l, None, pair, g16, o)
+
+
+def test_host_path_replays_its_graph():
+    # on a context with its own stream, hdp_match_host captures its device work
+    # on the first call and replays it; a tuning change drops the graph
+    pair = workload_pair("tiny", index=3)
+    hp = hdp.HDPParams(width=96, height=72, max_disp=15, levels=2, tree="st", st_k=300)
+    ref_ctx = hdp.hdp_create(hp)
+    ctx = hdp.hdp_create_own_stream(hp)
+    try:
+        ref = hdp.hdp_match_host(ref_ctx, pair.left, pair.right)       # default stream: eager
+        maps = [hdp.hdp_match_host(ctx, pair.left, pair.right) for _ in range(3)]
+        t = hdp.hdp_get_tuning(ctx)
+        t.agg_ctas_per_sm = 3
+        hdp.hdp_set_tuning(ctx, t)
+        maps.append(hdp.hdp_match_host(ctx, pair.left, pair.right))
+        other = workload_pair("tiny", index=4)
+        D_other = hdp.hdp_match_host(ctx, other.left, other.right)    # new inputs through the same graph
+        D_other_ref = hdp.hdp_match_host(ref_ctx, other.left, other.right)
+    finally:
+        hdp.hdp_destroy(ctx)
+        hdp.hdp_destroy(ref_ctx)
+    for m in maps:
+        assert np.array_equal(m, ref)
+    assert np.array_equal(D_other, D_other_ref)
