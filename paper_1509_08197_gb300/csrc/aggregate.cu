@@ -872,9 +872,6 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
     __shared__ float sP[COL_MAX_ROWS];            // coefficient of the carry
     __shared__ float sW[COL_MAX_ROWS];            // down: 1 - s^2 (x the up-pass mass in FP16)
     __shared__ float sPW[COL_MAX_ROWS];           // down: s (x the parent's mass in FP16)
-    __shared__ float sMass[COL_MAX_ROWS];
-    __shared__ float sBest[COL_MAX_ROWS][COL_THREADS_MAX / 32];
-    __shared__ int sSlot[COL_MAX_ROWS][COL_THREADS_MAX / 32];
     __shared__ int sCR[COL_CHUNK];                // staged light children: row in the tile,
     __shared__ int sCO[COL_CHUNK];                // row offset,
     __shared__ float sCS[COL_CHUNK];              // weight (x mass in FP16)
@@ -1138,16 +1135,12 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
                 v.y = fmaf(p, cin.y, v.y);
                 X2[r * S2 + x] = v;
             }
+        __syncthreads();   // every column's final values (and the masses) are in shared memory
         if (FP16) {
-            if (x == P2)
-                for (int r = 0; r < n; ++r) {
-                    sMass[r] = X2[r * S2 + P2].x;
-                    (UP ? a.nup : a.nd)[b + r] = sMass[r];
-                }
-            __syncthreads();
+            for (int r = x; r < n; r += blockDim.x) (UP ? a.nup : a.nd)[b + r] = X2[r * S2 + P2].x;
             if (lab2)
                 for (int r = 0; r < n; ++r) {
-                    const float inv = 1.f / sMass[r];
+                    const float inv = 1.f / X2[r * S2 + P2].x;
                     const float2 v = X2[r * S2 + x];
                     *(__half2*)(a.volh + base + (size_t)r * kp + 2 * x) = __floats2half2_rn(v.x * inv, v.y * inv);
                 }
@@ -1163,32 +1156,24 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_agg_col(AggArgs a, int kp)
             __syncthreads();
             if (x == 0) atomicExch(flags + u, 2);
         }
-        // ---- WTA (down pass): lowest slot on ties, per row over the block
+        // ---- WTA (down pass): lowest slot on ties; a warp per row, each lane
+        // scanning its column pairs in increasing order
         if (!UP) {
-            const int c0 = 2 * x, c1 = 2 * x + 1;
-            for (int r = 0; r < n; ++r) {
-                const float2 v = lab2 ? X2[r * S2 + x] : make_float2(INFINITY, INFINITY);
-                float bv = lab2 && c0 < K ? v.x : INFINITY;
-                int bs = lab2 && c0 < K ? c0 : INT_MAX;
-                if (lab2 && c1 < K && v.y < bv) { bv = v.y; bs = c1; }
+            for (int r = warp; r < n; r += nwarps) {
+                float bv = INFINITY;
+                int bs = INT_MAX;
+                for (int j = lane; j < P2; j += 32) {
+                    const float2 v = X2[r * S2 + j];
+                    if (2 * j < K && v.x < bv) { bv = v.x; bs = 2 * j; }
+                    if (2 * j + 1 < K && v.y < bv) { bv = v.y; bs = 2 * j + 1; }
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
                     const int os = __shfl_xor_sync(0xffffffffu, bs, o);
                     if (ov < bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
                 }
-                if (lane == 0) {
-                    sBest[r][warp] = bv;
-                    sSlot[r][warp] = bs;
-                }
-            }
-            __syncthreads();
-            for (int r = x; r < n; r += blockDim.x) {
-                float bv = INFINITY;
-                int bs = INT_MAX;
-                for (int w = 0; w < nwarps; ++w)
-                    if (sBest[r][w] < bv || (sBest[r][w] == bv && sSlot[r][w] < bs)) { bv = sBest[r][w]; bs = sSlot[r][w]; }
-                a.disp[a.lay[b + r]] = bs;   // full range: the slot is the label
+                if (lane == 0) a.disp[a.lay[b + r]] = bs;   // full range: the slot is the label
             }
         }
         // ---- the tile's rows are final: done
