@@ -317,7 +317,8 @@ __device__ __forceinline__ void g_find_many(int* parent, int* a, int* b, unsigne
 // edge from that edge's cache, broadcast by shuffles, and every merge or
 // freeze is applied to the caches of all lanes (so no shared-memory round
 // trip sits on the serial path).  Lane 0 writes the same changes to shared
-// memory for the next group.
+// memory for the next group.  A ballot over the caches jumps to the next
+// edge that can still merge, so cycles and edges of frozen trees cost no step.
 template <int NE>
 __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S, const uint32_t* bm, int cnt)
 {
@@ -352,13 +353,19 @@ __device__ __noinline__ void lw_sequential(const ForestArgs& a, LocalWinT<NE>& S
             py = (long long)(w - iy) * sy <= kq;
         }
         __syncwarp();   // every lane has read before lane 0 writes
-        for (uint32_t mm = m; mm; mm &= mm - 1u) {
-            const int k = __ffs(mm) - 1;
-            const unsigned v = __shfl_sync(FULL, (unsigned)x | (unsigned)y << 14 | (unsigned)zx << 28 |
-                                                     (unsigned)zy << 29 | (unsigned)!px << 30 | (unsigned)!py << 31, k);
+        uint32_t pend = m;
+        for (;;) {
+            // the next edge of the group whose trees differ and are not frozen;
+            // the edges before it are cycles or touch a frozen tree on the
+            // current caches, which hold their state in the sequential order
+            const unsigned act = __ballot_sync(FULL, (pend >> lane & 1u) && x != y && !zx && !zy);
+            if (!act) break;
+            const int k = __ffs(act) - 1;
+            pend &= ~(uint32_t)((2ull << k) - 1ull);   // decided: every edge up to k
+            const unsigned v = __shfl_sync(FULL, (unsigned)x | (unsigned)y << 14 | (unsigned)!px << 28 |
+                                                     (unsigned)!py << 29, k);
             const int xk = (int)(v & 0x3fffu), yk = (int)((v >> 14) & 0x3fffu);
-            if (xk == yk || ((v >> 28) & 3u)) continue;   // a cycle, or a frozen tree
-            const bool fx = (v >> 30) & 1u, fy = v >> 31;
+            const bool fx = (v >> 28) & 1u, fy = (v >> 29) & 1u;
             if (fx || fy) {   // criterion fails: that tree can never merge again
                 if (fx) { zx |= x == xk; zy |= y == xk; }
                 if (fy) { zx |= x == yk; zy |= y == yk; }
