@@ -272,13 +272,17 @@ def run_batch(hdp, torch, dev, steps, warmup, flush, rank, per_size=16):
             hdp.hdp_destroy(c)
 
 
-def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
-    """Differentiable aggregation: B seeded 256x256 pairs, disparity 0-63, one full-range MST per pair, a
-    seeded FP32 cost volume E; a step is, for every pair, the forward Eq. C, the soft-argmin (T = 1) with
-    the L1 loss against the synthetic ground truth, and the backward (dL/dE, dL/dw, dL/dgamma) with the
-    forward recomputed."""
+def run_grad(hdp, torch, dev, steps, warmup, flush, B=8, fit_steps=20):
+    """Differentiable aggregation: B seeded 256x256 pairs, disparity 0-63, one full-range MST per pair.  A step
+    is, for every pair, the matching-cost volume E(alpha, tau_c, tau_g) from the pair's images, the forward
+    Eq. C, the soft-argmin (T = 1) with the L1 loss against the synthetic ground truth, and the backward: dL/dE
+    (forward recomputed), dL/dw, dL/dgamma and dL/d(alpha, tau_c, tau_g).  Then, untimed by the step, a short
+    fit of (alpha, tau_c, tau_g, gamma) by Adam on the mean loss of the B pairs through the autograd
+    functions, from a deliberately poor start."""
     from paper_1509_08197_gb300.scenes import workload_pair
+    from paper_1509_08197_gb300.autograd import CostVolume, HDPAggregate, SoftArgminL1
     st = torch.cuda.Stream(device=dev)
+    theta0 = (0.9, 7.0, 2.0)   # the matching-cost parameters of the pipeline
     ctxs, bufs = [], []
     try:
         with torch.cuda.stream(st):
@@ -290,10 +294,10 @@ def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
                 ctx = hdp.hdp_create(hp, st)
                 ctxs.append(ctx)
                 hdp.hdp_build_trees(ctx, torch.from_numpy(pr.left).to(dev), torch.from_numpy(pr.right).to(dev))
-                g = torch.Generator().manual_seed(5000 + i)
-                E = (torch.rand((H, W, X), generator=g) * 2.5).to(dev)
+                E = torch.empty((H, W, X), device=dev)
                 bufs.append(dict(E=E, C=torch.empty_like(E), gC=torch.empty_like(E), gE=torch.empty_like(E),
                                  gw=torch.empty(2 * H * W, device=dev), gg=torch.empty(1, device=dev),
+                                 gtheta=torch.empty(3, device=dev),
                                  d=torch.empty((H, W), device=dev), loss=torch.zeros(1, device=dev),
                                  gt=torch.from_numpy(pr.gt.astype(np.float32)).to(dev),
                                  valid=torch.from_numpy((~pr.occluded).astype(np.uint8)).to(dev)))
@@ -301,9 +305,11 @@ def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
             def step():
                 for ctx, b in zip(ctxs, bufs):
                     b["loss"].zero_()
+                    hdp.hdp_cost_volume(ctx, *theta0, b["E"])
                     hdp.hdp_aggregate_fwd(ctx, b["E"], b["C"])
                     hdp.hdp_soft_argmin_l1(ctx, b["C"], b["gt"], b["valid"], 1.0, b["d"], b["loss"], b["gC"])
                     hdp.hdp_aggregate_bwd(ctx, b["E"], b["gC"], b["gE"], b["gw"], b["gg"])
+                    hdp.hdp_cost_volume_bwd(ctx, *theta0, b["gE"], b["gtheta"])
 
             for _ in range(warmup):
                 step()
@@ -318,12 +324,51 @@ def run_grad(hdp, torch, dev, steps, warmup, flush, B=8):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
             loss = float(sum(float(b["loss"]) for b in bufs) / B)
+
+            # the fit: every parameter from a poor start, Adam with a step size per parameter
+            alpha = torch.tensor(0.5, device=dev, requires_grad=True)
+            tau_c = torch.tensor(20.0, device=dev, requires_grad=True)
+            tau_g = torch.tensor(5.0, device=dev, requires_grad=True)
+            gamma = torch.tensor(12.0, device=dev, requires_grad=True)
+            opt = torch.optim.Adam([{"params": [alpha], "lr": 0.03}, {"params": [tau_c, tau_g], "lr": 0.3},
+                                    {"params": [gamma], "lr": 0.5}])
+            hist = []
+            t0 = time.perf_counter()
+            for it in range(fit_steps + 1):
+                opt.zero_grad()
+                theta = torch.stack([alpha, tau_c, tau_g])
+                total = 0.0
+                for ctx, b in zip(ctxs, bufs):
+                    Ef = CostVolume.apply(theta, ctx)
+                    Cf = HDPAggregate.apply(Ef, gamma, ctx)
+                    _, lf = SoftArgminL1.apply(Cf, b["gt"], b["valid"], ctx)
+                    total = total + lf / B
+                hist.append(float(total))
+                if it == fit_steps:
+                    break
+                total.backward()
+                opt.step()
+                with torch.no_grad():
+                    alpha.clamp_(0.0, 1.0)
+                    tau_c.clamp_(min=0.0)
+                    tau_g.clamp_(min=0.0)
+                    gamma.clamp_(min=0.5)
+            st.synchronize()
+            fit_s = time.perf_counter() - t0
         ms = float(np.mean(times))
         n = sum(b["E"].numel() for b in bufs)
-        return {"workload": f"{B} pairs of 256x256, disparity 0-63, full-range MST, FP32 volume; forward + "
-                            "soft-argmin (T=1) + L1 + backward (dE, dw, dgamma), forward recomputed",
+        return {"workload": f"{B} pairs of 256x256, disparity 0-63, full-range MST, FP32 volume; cost volume "
+                            "E(alpha, tau_c, tau_g) + forward + soft-argmin (T=1) + L1 + backward (dE, dw, dgamma, "
+                            "dalpha, dtau_c, dtau_g), forward recomputed",
                 "ms_per_step": ms, "pairs_per_s": B / (ms / 1000.0),
-                "Mpix_disp_per_s": n / (ms / 1000.0) / 1e6, "mean_l1_loss": loss}
+                "Mpix_disp_per_s": n / (ms / 1000.0) / 1e6, "mean_l1_loss": loss,
+                "fit": {"what": "alpha, tau_c, tau_g, gamma by Adam on the mean L1 loss of the pairs "
+                                "(autograd, host-side parameter reads each step)",
+                        "steps": fit_steps, "start": {"alpha": 0.5, "tau_c": 20.0, "tau_g": 5.0, "gamma": 12.0},
+                        "end": {"alpha": float(alpha), "tau_c": float(tau_c), "tau_g": float(tau_g),
+                                "gamma": float(gamma)},
+                        "loss_start": hist[0], "loss_end": hist[-1], "loss_at_pipeline_params": loss,
+                        "s_total": fit_s}}
     finally:
         for c in ctxs:
             hdp.hdp_destroy(c)

@@ -109,9 +109,9 @@ typedef struct {
  * same results bit for bit (the forest engines are exact, and the carries of
  * the aggregation are evaluated in a fixed order); only the speed changes.
  * Defaults in brackets; hdp_set_tuning rejects values outside the ranges.
- *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..8 [5] (the
- *                          kernels of full-range layers fit 4, those of
- *                          predicted layers 5)
+ *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..8 [8] (each
+ *                          kernel also stops at its own occupancy: 4 CTAs
+ *                          of 2048-float tiles, 7 of 1024, 5 of 512)
  *   region_ctas_per_sm     first-pass CTAs per SM on HDP layers, 1..4 [4]
  *   big_class_edges        first pass of big full-range layers: a weight class
  *                          with at least this many edges runs as a grid
@@ -284,12 +284,40 @@ int hdp_batch_graph_launch(hdp_ctx* ctx0);
  *   hdp_soft_argmin_l1: d(p) = sum_x x softmax(-C(p,.)/T), the mean |d - gt|
  *     over pixels with valid[p] != 0 (valid may be NULL), and dL/dC; d_disp,
  *     d_loss (one float) and d_gC may each be NULL.
- * The first call allocates four volume-sized buffers in the context. */
+ * The first call allocates four volume-sized buffers and the edge-weight
+ * buffer in the context. */
 int hdp_aggregate_fwd(hdp_ctx* ctx, const float* d_E, float* d_C);
 int hdp_aggregate_bwd(hdp_ctx* ctx, const float* d_E, const float* d_gC, float* d_gE, float* d_gw, float* d_ggamma);
 int hdp_set_gamma(hdp_ctx* ctx, float gamma);
 int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const uint8_t* d_valid, float T,
                        float* d_disp, float* d_loss, float* d_gC);
+
+/* The inputs of Eq. C made differentiable as well, on the same loaded layer
+ * (same requirements as above).
+ *   hdp_cost_volume: the matching cost of Sec. 3.3 with real-valued
+ *     parameters, E(p, x) = (1 - alpha) min(dc, tau_c) + alpha min(dg, tau_g)
+ *     for every pixel p and label x in 0..d_l, dc the mean absolute RGB
+ *     difference and dg the absolute horizontal-gradient difference / 6 of
+ *     left pixel (px, py) and right pixel (max(px - x, 0), py), in 0..255
+ *     intensity units (the pyramid's scale 4^l divided out).  d_E as above.
+ *   hdp_cost_volume_bwd: from d_gE = dL/dE, d_gparams (3 floats) receives
+ *     dL/dalpha = sum gE (min(dg, tau_g) - min(dc, tau_c)),
+ *     dL/dtau_c = sum gE (1 - alpha) [dc > tau_c] and
+ *     dL/dtau_g = sum gE alpha [dg > tau_g] (0 taken at dc = tau_c).
+ *   alpha, tau_c, tau_g must be finite and tau_c, tau_g >= 0 (HDP_ERR_ARG);
+ *   unlike hdp_params they need not sit on the 1/20, 1/3, 1/6 grids.
+ *   hdp_set_edge_weights: real-valued weights for the loaded tree's edges,
+ *     d_w[e] per grid edge id e (2 * width * height floats, intensity units,
+ *     copied), so the similarities become exp(-d_w[e] / gamma); NULL returns
+ *     to the image's integer weights.  The tree is not rebuilt.  Every later
+ *     aggregation on this tree uses them (hdp_aggregate_fwd/bwd, whose
+ *     dL/dgamma then sums d_w[e] dL/dw[e], hdp_set_gamma, hdp_match on the
+ *     same layer) until hdp_build_trees loads a tree again.
+ * These calls, like hdp_aggregate_fwd, enqueue on the context's stream and
+ * return without waiting. */
+int hdp_cost_volume(hdp_ctx* ctx, float alpha, float tau_c, float tau_g, float* d_E);
+int hdp_cost_volume_bwd(hdp_ctx* ctx, float alpha, float tau_c, float tau_g, const float* d_gE, float* d_gparams);
+int hdp_set_edge_weights(hdp_ctx* ctx, const float* d_w);
 
 /* hdp_build_trees + hdp_match without any allocation, for callers that cannot
  * allocate device memory: code running where cudaMalloc is not allowed or

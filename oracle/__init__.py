@@ -61,6 +61,7 @@ def _declare(L):
         "orc_gradient": (I, [P, I, I, P]),
         "orc_cost_m": (D, [P, P, P, P, I, I, I, I, I, D, D, D]),
         "orc_cost_mq": (I64, [P, P, P, P, I, I, I, I, I, I, I, I]),
+        "orc_cost_volume": (I, [P, P, P, P, I, I, I, I, D, D, D, P]),
         "orc_edge_weights": (I, [P, I, I, P]),
         "orc_median3": (I, [P, I, I, P]),
         "orc_sort_edges": (I, [P, I, I, P]),
@@ -120,6 +121,15 @@ def gradient(img: np.ndarray) -> np.ndarray:
 def cost_m(L, gL, R, gR, level, px, py, x, alpha=0.9, tau_c=7.0, tau_g=2.0):
     H, W, _ = L.shape
     return lib().orc_cost_m(_p(L), _p(gL), _p(R), _p(gR), W, level, px, py, x, alpha, tau_c, tau_g)
+
+
+def cost_volume(L, gL, R, gR, level, X, alpha=0.9, tau_c=7.0, tau_g=2.0):
+    """Dense FP64 cost volume [H*W][X] of a layer (orc_cost_m at every pixel and label)."""
+    L, gL, R, gR = _c(L, np.int32), _c(gL, np.int32), _c(R, np.int32), _c(gR, np.int32)
+    H, W, _ = L.shape
+    E = np.empty((H * W, X), np.float64)
+    lib().orc_cost_volume(_p(L), _p(gL), _p(R), _p(gR), W, H, level, X, alpha, tau_c, tau_g, _p(E))
+    return E
 
 
 def cost_mq(L, gL, R, gR, level, px, py, x, a20=18, tc3=21, tg6=12):

@@ -91,6 +91,19 @@ double orc_cost_m(const int32_t* L, const int32_t* gL, const int32_t* R, const i
     return (1.0 - alpha) * fmin(dc, tau_c) + alpha * fmin(dg, tau_g);
 }
 
+/* The dense cost volume E[p][x] = M(p, x) of one layer, every pixel p
+ * (row-major) and label x in 0..X-1: orc_cost_m at each entry.  The
+ * differentiable path evaluates it for real-valued alpha, tau_c, tau_g.     */
+int orc_cost_volume(const int32_t* L, const int32_t* gL, const int32_t* R, const int32_t* gR,
+                    int W, int H, int level, int X, double alpha, double tau_c, double tau_g, double* E)
+{
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px)
+            for (int x = 0; x < X; ++x)
+                E[((int64_t)py * W + px) * X + x] = orc_cost_m(L, gL, R, gR, W, level, px, py, x, alpha, tau_c, tau_g);
+    return 0;
+}
+
 /* The same cost written as an exact integer: with a20 = 20*alpha,
  * tc3 = 3*tau_c and tg6 = 6*tau_g integers,
  *   120 * 4^l * M = 2*(20 - a20) * min(sum_c |dI_c|, tc3*4^l) + a20 * min(|dg|, tg6*4^l).

@@ -141,6 +141,9 @@ def load(path: str = LIB_PATH):
         "hdp_aggregate_bwd": (I, [P, P, P, P, P, P]),
         "hdp_set_gamma": (I, [P, ctypes.c_float]),
         "hdp_soft_argmin_l1": (I, [P, P, P, P, ctypes.c_float, P, P, P]),
+        "hdp_cost_volume": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
+        "hdp_cost_volume_bwd": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P]),
+        "hdp_set_edge_weights": (I, [P, P]),
         "hdp_match_batch": (I, [P, I, P, P, P, P]),
         "hdp_batch_graph_capture": (I, [P, I, P, P, P, P, P]),
         "hdp_batch_graph_launch": (I, [P]),
@@ -484,6 +487,31 @@ def hdp_soft_argmin_l1(ctx: Context, C, gt=None, valid=None, T=1.0, disp=None, l
                                           _optr(loss), _optr(gC)), "hdp_soft_argmin_l1")
 
 
+def _f32(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+        raise TypeError("expected a float32 CUDA tensor")
+    return _ptr(t)
+
+
+def hdp_cost_volume(ctx: Context, alpha: float, tau_c: float, tau_g: float, E):
+    """E (H, W, X) float32 CUDA tensor <- the matching cost with real-valued parameters."""
+    _check(ctx, load().hdp_cost_volume(ctx.handle, float(alpha), float(tau_c), float(tau_g), _f32(E)),
+           "hdp_cost_volume")
+
+
+def hdp_cost_volume_bwd(ctx: Context, alpha: float, tau_c: float, tau_g: float, gE, gparams):
+    """gparams (3,) float32 CUDA tensor <- dL/d(alpha, tau_c, tau_g) from gE = dL/dE."""
+    _check(ctx, load().hdp_cost_volume_bwd(ctx.handle, float(alpha), float(tau_c), float(tau_g), _f32(gE),
+                                           _f32(gparams)), "hdp_cost_volume_bwd")
+
+
+def hdp_set_edge_weights(ctx: Context, w=None):
+    """Real-valued weights per grid edge id (float32 CUDA tensor of 2*H*W) for the loaded tree, or None for the
+    image's own."""
+    _check(ctx, load().hdp_set_edge_weights(ctx.handle, None if w is None else _f32(w)), "hdp_set_edge_weights")
+
+
 def _batch_arrays(ctxs, lefts, rights, outs):
     n = len(ctxs)
     H = (ctypes.c_void_p * n)(*[c.handle for c in ctxs])
@@ -521,4 +549,5 @@ def exported_symbols():
             "hdp_get_stage", "hdp_set_stage", "hdp_set_timing", "hdp_get_timings", "hdp_graph_capture",
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
             "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch",
-            "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em", "hdp_refine"]
+            "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em", "hdp_refine", "hdp_cost_volume", "hdp_cost_volume_bwd",
+            "hdp_set_edge_weights"]

@@ -374,6 +374,7 @@ static void build_layer_tree(hdp_ctx* ctx, int l)
     launch_order(c, l);
     mark(ctx, l, 4);
     c.tree_level = l;
+    c.use_wf = false;   // the new layout's similarities come from the image's weights
 }
 
 extern "C" int hdp_build_trees(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int pitch)
@@ -679,6 +680,7 @@ extern "C" int hdp_destroy(hdp_ctx* ctx)
     for (int i = 0; i < 4; ++i)
         if (ctx->c.gvol[i]) cudaFree(ctx->c.gvol[i]);
     if (ctx->c.gacc) cudaFree(ctx->c.gacc);
+    if (ctx->c.wf) cudaFree(ctx->c.wf);
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->join) cudaEventDestroy(ctx->join);
     if (ctx->c.s2) {
@@ -1158,6 +1160,41 @@ extern "C" int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d
     rc = launch_soft_argmin_l1(ctx->c, d_C, d_gt, d_valid, T, d_disp, d_loss, d_gC);
     if (rc) return fail(ctx, rc, "workspace for the differentiable path");
     return check_launch(ctx, "hdp_soft_argmin_l1");
+}
+
+extern "C" int hdp_set_edge_weights(hdp_ctx* ctx, const float* d_w)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    rc = set_edge_weights(ctx->c, d_w);
+    if (rc) return fail(ctx, rc, "workspace for the differentiable path");
+    return check_launch(ctx, "hdp_set_edge_weights");
+}
+
+static bool cost_params_ok(float alpha, float tau_c, float tau_g)
+{
+    return std::isfinite(alpha) && std::isfinite(tau_c) && std::isfinite(tau_g) && tau_c >= 0.f && tau_g >= 0.f;
+}
+
+extern "C" int hdp_cost_volume(hdp_ctx* ctx, float alpha, float tau_c, float tau_g, float* d_E)
+{
+    if (!ctx || !d_E || !cost_params_ok(alpha, tau_c, tau_g)) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    launch_cost_volume(ctx->c, alpha, tau_c, tau_g, d_E);
+    return check_launch(ctx, "hdp_cost_volume");
+}
+
+extern "C" int hdp_cost_volume_bwd(hdp_ctx* ctx, float alpha, float tau_c, float tau_g, const float* d_gE,
+                                   float* d_gparams)
+{
+    if (!ctx || !d_gE || !d_gparams || !cost_params_ok(alpha, tau_c, tau_g)) return HDP_ERR_ARG;
+    int rc = grad_ready(ctx);
+    if (rc) return rc;
+    rc = launch_cost_param_grad(ctx->c, alpha, tau_c, tau_g, d_gE, d_gparams);
+    if (rc) return fail(ctx, rc, "workspace for the differentiable path");
+    return check_launch(ctx, "hdp_cost_volume_bwd");
 }
 
 // ------------------------------------------------------------------ batch ---

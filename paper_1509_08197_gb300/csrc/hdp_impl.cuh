@@ -31,9 +31,9 @@
 // aggregation CTAs (4 warps) per SM: launch bounds of the three tile sizes
 // and the default cap (occupancy limits each kernel below the cap)
 #define AGG_MINB_2048 4
-#define AGG_MINB_1024 5
+#define AGG_MINB_1024 7
 #define AGG_MINB_512 5
-#define AGG_CTAS_DEFAULT 5
+#define AGG_CTAS_DEFAULT 8
 #define SMALL_TILE_NODES (1 << 17)       // layers with one label set (full range, the top layer)
 #define SMALL_TILE_NODES_HDP (1 << 19)   // predicted layers (the 1390x1110 pair: layers 1-3)
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
@@ -154,6 +154,8 @@ struct Ctx {
     size_t vol_elems = 0;
     float *gvol[4] = {nullptr, nullptr, nullptr, nullptr};   // differentiable path: U_E, C_E, U_g, G (lazy)
     double* gacc = nullptr;
+    float* wf = nullptr;       // differentiable path: real-valued edge weights per grid edge id (lazy)
+    bool use_wf = false;       // the loaded layout's similarities follow wf
 
     // scalars on the device
     int* ints = nullptr;   // see IDX_* below
@@ -233,6 +235,9 @@ void launch_refine(Ctx& c);
 int grad_forward(Ctx& c, const float* E, float* C);
 int grad_backward(Ctx& c, const float* E, const float* gC, float* gE, float* gw, float* ggamma);
 void launch_set_gamma(Ctx& c, float gamma);
+int set_edge_weights(Ctx& c, const float* w);
+void launch_cost_volume(Ctx& c, float alpha, float tau_c, float tau_g, float* E);
+int launch_cost_param_grad(Ctx& c, float alpha, float tau_c, float tau_g, const float* gE, float* out);
 int launch_soft_argmin_l1(Ctx& c, const float* C, const float* gt, const uint8_t* valid, float T, float* disp,
                           float* loss, float* gC);
 

@@ -34,7 +34,9 @@ def _case(seed=0):
     wn = oracle.node_weights(W, H, parent, w)
     rng = np.random.default_rng(seed)
     E = rng.uniform(0, 2.5, size=(W * H, X))
-    return ctx, dev, dict(w=w, bo=bo, parent=parent, wn=wn, E=E, gt=gt, rng=rng)
+    Ri = oracle.to_level0(R)
+    return ctx, dev, dict(w=w, bo=bo, parent=parent, wn=wn, E=E, gt=gt, rng=rng, Li=Li, Ri=Ri,
+                          gL=oracle.gradient(Li), gR=oracle.gradient(Ri))
 
 
 def _s(o, gamma=GAMMA):
@@ -150,5 +152,110 @@ def test_soft_argmin_l1_and_autograd_chain():
             assert gEg[i, x] == pytest.approx(fd, rel=5e-3, abs=1e-6)
         fd = (Lfull(E64, GAMMA + h)[0] - Lfull(E64, GAMMA - h)[0]) / (2 * h)
         assert float(gamma.grad) == pytest.approx(fd, rel=5e-3, abs=1e-7)
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+# cost parameters off the integer grids of hdp_params; no dc (a multiple of 1/3) or dg (of 1/6) lies within
+# 1e-6 of tau_c or tau_g, so central differences with h = 1e-6 do not cross a truncation point
+THETA = (0.83, 7.1, 2.05)
+
+
+def _theta32(th):
+    return [float(np.float32(v)) for v in th]
+
+
+def test_cost_volume_matches_oracle():
+    ctx, dev, o = _case()
+    try:
+        E = torch.empty((H, W, X), dtype=torch.float32, device=dev)
+        hdp.hdp_cost_volume(ctx, *THETA, E)
+        hdp.hdp_sync(ctx)
+        ref = oracle.cost_volume(o["Li"], o["gL"], o["Ri"], o["gR"], 0, X, *_theta32(THETA))
+        assert np.abs(E.cpu().numpy().reshape(-1, X) - ref).max() <= 2e-6 * max(1.0, np.abs(ref).max())
+        with pytest.raises(hdp.HDPError):
+            hdp.hdp_cost_volume(ctx, 0.5, -1.0, 2.0, E)    # a negative truncation is refused
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def _loss_oracle(o, E, wn, gamma, valid_np):
+    s = np.where(o["parent"] >= 0, np.exp(-wn / gamma), 0.0)
+    dr = oracle.soft_argmin(oracle.aggregate_given(o["bo"], o["parent"], s, E))
+    return float(np.abs(dr - o["gt"].ravel())[valid_np.ravel()].mean())
+
+
+def test_cost_parameter_and_gamma_gradients_match_central_differences():
+    from paper_1509_08197_gb300.autograd import CostVolume, HDPAggregate, SoftArgminL1
+    ctx, dev, o = _case(3)
+    try:
+        valid_np = o["rng"].uniform(size=(H, W)) > 0.2
+        theta = torch.tensor(THETA, dtype=torch.float32, device=dev, requires_grad=True)
+        gamma = torch.tensor(GAMMA, dtype=torch.float32, device=dev, requires_grad=True)
+        gt = torch.from_numpy(o["gt"]).to(dev)
+        valid = torch.from_numpy(valid_np.astype(np.uint8)).to(dev)
+        E = CostVolume.apply(theta, ctx)
+        C = HDPAggregate.apply(E, gamma, ctx)
+        _, loss = SoftArgminL1.apply(C, gt, valid, ctx)
+        loss.backward()
+        torch.cuda.synchronize()
+
+        def Lfull(th, gam):
+            Eo = oracle.cost_volume(o["Li"], o["gL"], o["Ri"], o["gR"], 0, X, *th)
+            return _loss_oracle(o, Eo, o["wn"], gam, valid_np)
+        th0 = _theta32(THETA)
+        assert float(loss) == pytest.approx(Lfull(th0, GAMMA), rel=1e-4)
+        h = 1e-6
+        g = theta.grad.cpu().numpy()
+        for k in range(3):
+            tp, tm = list(th0), list(th0)
+            tp[k] += h
+            tm[k] -= h
+            fd = (Lfull(tp, GAMMA) - Lfull(tm, GAMMA)) / (2 * h)
+            assert g[k] == pytest.approx(fd, rel=5e-3, abs=1e-6), f"parameter {k}"
+        fd = (Lfull(th0, GAMMA + h) - Lfull(th0, GAMMA - h)) / (2 * h)
+        assert float(gamma.grad) == pytest.approx(fd, rel=5e-3, abs=1e-7)
+    finally:
+        hdp.hdp_destroy(ctx)
+
+
+def test_edge_weights_as_an_input():
+    from paper_1509_08197_gb300.autograd import HDPAggregate, SoftArgminL1, image_edge_weights
+    ctx, dev, o = _case(4)
+    try:
+        rng = o["rng"]
+        valid_np = rng.uniform(size=(H, W)) > 0.2
+        w_img = image_edge_weights(ctx, device=dev)
+        assert np.array_equal(w_img.cpu().numpy(), np.where(o["w"] >= 0, o["w"], 0).astype(np.float32))
+        w_np = np.maximum(w_img.cpu().numpy() + rng.uniform(-0.4, 0.4, size=2 * H * W).astype(np.float32), 0)
+        w = torch.from_numpy(w_np).to(dev).requires_grad_(True)
+        E = torch.from_numpy(o["E"].astype(np.float32).reshape(H, W, X)).to(dev)
+        gamma = torch.tensor(GAMMA, dtype=torch.float32, device=dev)
+        gt = torch.from_numpy(o["gt"]).to(dev)
+        valid = torch.from_numpy(valid_np.astype(np.uint8)).to(dev)
+        C = HDPAggregate.apply(E, gamma, ctx, w)
+        _, loss = SoftArgminL1.apply(C, gt, valid, ctx)
+        loss.backward()
+        torch.cuda.synchronize()
+        E64 = o["E"].astype(np.float32).astype(np.float64)
+        wn = oracle.node_weights(W, H, o["parent"], w_np.astype(np.float64))
+        assert float(loss) == pytest.approx(_loss_oracle(o, E64, wn, GAMMA, valid_np), rel=1e-4)
+        gw = w.grad.cpu().numpy()
+        tree = np.zeros(2 * H * W, bool)
+        for v in np.flatnonzero(o["parent"] >= 0):
+            tree[_edge_id(v, o["parent"][v])] = True
+        assert np.all(gw[~tree] == 0)   # the tree is fixed: other edges carry no gradient
+        h = 1e-6
+        scale = np.abs(gw).max()
+        for v in np.flatnonzero(o["parent"] >= 0)[::61]:
+            wp, wm = wn.copy(), wn.copy()
+            wp[v] += h
+            wm[v] -= h
+            fd = (_loss_oracle(o, E64, wp, GAMMA, valid_np) - _loss_oracle(o, E64, wm, GAMMA, valid_np)) / (2 * h)
+            assert gw[_edge_id(v, o["parent"][v])] == pytest.approx(fd, rel=5e-3, abs=2e-3 * scale)
+        # without weights the next call aggregates with the image's own again
+        C2 = HDPAggregate.apply(E, gamma, ctx)
+        ref = oracle.aggregate_given(o["bo"], o["parent"], _s(o), E64)
+        assert (np.abs(C2.cpu().numpy().reshape(-1, X) - ref) / np.abs(ref)).max() < 1e-5
     finally:
         hdp.hdp_destroy(ctx)

@@ -86,6 +86,29 @@ def test_cost_integer_form_equals_definition():
             assert mq / (120.0 * s) == pytest.approx(m, rel=1e-13, abs=1e-13)
 
 
+def test_cost_volume_layout_hand():
+    # the hand-worked entries above, read from the dense volume (pixel-major, label-minor, clamped columns)
+    L, gL, R, gR = _cost_fixture()
+    E = oracle.cost_volume(L, gL, R, gR, 0, 4)
+    assert E.shape == (4, 4)
+    for (px, x), want in {(0, 0): 0.3, (1, 1): 0.1 * 2 / 3 + 1.8, (2, 1): 2.5, (2, 0): 2.5, (3, 0): 2.5,
+                          (1, 3): 0.1 * 2 / 3 + 1.8}.items():
+        assert E[px, x] == pytest.approx(want, abs=1e-12)
+
+
+def test_cost_volume_real_valued_parameters_hand():
+    # alpha = 0.25, tau_c = 0.5, tau_g = 1 (off the 1/20, 1/3, 1/6 grids of the integer form)
+    L, gL, R, gR = _cost_fixture()
+    E = oracle.cost_volume(L, gL, R, gR, 0, 4, alpha=0.25, tau_c=0.5, tau_g=1.0)
+    assert E[0, 0] == pytest.approx(0.25 * (2 / 6), abs=1e-12)         # dc = 0, dg = 1/3 under tau_g
+    assert E[1, 1] == pytest.approx(0.75 * 0.5 + 0.25 * 1.0, abs=1e-12)   # dc = 2/3 and dg = 5/2 both truncated
+    # alpha = 0: the colour term alone, untruncated with a large tau_c: the mean absolute RGB difference
+    E0 = oracle.cost_volume(L, gL, R, gR, 0, 4, alpha=0.0, tau_c=1e9, tau_g=0.0)
+    assert E0[2, 1] == pytest.approx((30 + 30 + 30) / 3, abs=1e-12)   # (40,50,60) against (10,20,30)
+    assert E0[2, 0] == pytest.approx((29 + 31 + 29) / 3, abs=1e-12)   # (40,50,60) against (11,19,31)
+    assert E0[3, 0] == pytest.approx(100.0, abs=1e-12)
+
+
 def test_cost_constant_pair_is_zero_and_saturates():
     L = np.full((2, 6, 3), 77, np.int32)
     g = oracle.gradient(L)
