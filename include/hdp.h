@@ -122,9 +122,13 @@ typedef struct {
  *                          1024..1<<24 [131072]
  *   boruvka_edges_per_cta  cooperative grids get one CTA per this many edges
  *                          (at most one wave), 512..1<<20 [4096]
- *   region_max_nodes       HDP layers with fewer nodes run the first pass
- *                          region by region (bigger ones by weight class),
- *                          0..1<<30 [1<<24]
+ *   region_max_nodes       HDP layers with fewer nodes run the forest
+ *                          region by region: the segment tree's first pass
+ *                          over same-set regions, and every pass of a risky
+ *                          layer (MST, ST or RT) over the components of the
+ *                          edges that survive DT-Rule 1; bigger layers take
+ *                          the first pass by weight class and a risky layer
+ *                          on one CTA, 0..1<<30 [1<<24]
  */
 typedef struct {
     int agg_ctas_per_sm;

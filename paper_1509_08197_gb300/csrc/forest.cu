@@ -66,6 +66,7 @@ struct ForestArgs {
     int bnum, bden;
     int passes, crit_first;
     int big_class;       // k_fh_hybrid: weight classes with at least this many edges run as a grid Boruvka
+    int risky_only;      // region kernels: 1 = serve risky layers only (MST: k_boruvka takes the others)
     int* stats;          // [2]: reservation rounds and windows of the windowed engines (reported per layer)
     int* engine;
     DevStatus* st;
@@ -82,6 +83,34 @@ __device__ __forceinline__ void decode(uint32_t key, int ebits, int W, int& e, i
 __device__ __forceinline__ bool same_set(const ForestArgs& a, int p, int q)
 {
     return !a.pixset || a.canon[a.pixset[p]] == a.canon[a.pixset[q]];
+}
+
+// the end points' PixelIntv intersect: the edge survives DT-Rule 1
+__device__ __forceinline__ bool sets_meet(const ForestArgs& a, int p, int q)
+{
+    if (!a.pixset) return true;
+    const uint32_t* mp = a.table + (size_t)a.pixset[p] * HDP_WORDS;
+    const uint32_t* mq = a.table + (size_t)a.pixset[q] * HDP_WORDS;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < HDP_WORDS; ++w) m |= mp[w] & mq[w];
+    return m != 0u;
+}
+
+// Regions of the region engine.  A layer without a risky edge: connected
+// same-set regions (no accepted edge joins different sets).  A risky layer:
+// connected components of the edges that survive DT-Rule 1 (no edge joins two
+// components, so each is its own sequential problem).
+__device__ __forceinline__ bool region_edge(const ForestArgs& a, int p, int q, bool rk)
+{
+    return rk ? sets_meet(a, p, q) : same_set(a, p, q);
+}
+
+// the region kernels' mode: -1 = nothing to do, else 1 for a risky layer
+__device__ __forceinline__ int region_mode(const ForestArgs& a)
+{
+    const bool rk = a.risky && __ldcg(a.risky);
+    return a.risky_only && !rk ? -1 : (int)rk;
 }
 
 __device__ __forceinline__ void append(const ForestArgs& a, int which, int idx, int ra, int rb)
@@ -597,7 +626,8 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
                 S.best[id] = (w0 - iw) * sz > kq ? 0u : 0xffffffffu;
                 if (RISKY)
 #pragma unroll
-                    for (int h = 0; h < HDP_WORDS; ++h) ST[id * HDP_WORDS + h] = a.T[(size_t)r * HDP_WORDS + h];
+                    for (int h = 0; h < HDP_WORDS; ++h)
+                        ST[id * HDP_WORDS + h] = L2 ? __ldcg(a.T + (size_t)r * HDP_WORDS + h) : a.T[(size_t)r * HDP_WORDS + h];
             }
         }
     }
@@ -750,6 +780,9 @@ __device__ void lw_window(const ForestArgs& a, const uint32_t* keys, int* loc, L
         } else if (L2) {
             __stcg(a.size + r, S.size[x]);
             __stcg(a.intw + r, S.intw[x]);
+            if (RISKY)
+#pragma unroll
+                for (int h = 0; h < HDP_WORDS; ++h) __stcg(a.T + (size_t)r * HDP_WORDS + h, ST[x * HDP_WORDS + h]);
         } else {
             a.size[r] = S.size[x];
             a.intw[r] = S.intw[x];
@@ -893,7 +926,8 @@ __device__ __forceinline__ int cc_find(int* par, int v)
 #define CC_RUN 32
 __global__ void k_cc_runs(ForestArgs a, int* par)
 {
-    if (a.risky && __ldcg(a.risky)) return;
+    const int mode = region_mode(a);
+    if (mode < 0) return;
     const int per_row = (a.W + CC_RUN - 1) / CC_RUN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= per_row * (a.N / a.W)) return;
@@ -901,23 +935,18 @@ __global__ void k_cc_runs(ForestArgs a, int* par)
     int run = y * a.W + x0;
     for (int x = x0 + 1; x < x1; ++x) {
         const int v = y * a.W + x;
-        if (same_set(a, v - 1, v)) par[v] = run;
+        if (region_edge(a, v - 1, v, mode)) par[v] = run;
         else run = v;
     }
 }
 
-__global__ void k_cc_hook(ForestArgs a, int* par)
+__device__ __forceinline__ void cc_hook_edge(const ForestArgs& a, int* par, int e, int mode)
 {
-    if (a.risky && __ldcg(a.risky)) return;
-    // edge ids in image order (the regions do not depend on the order), so
-    // that neighbouring threads share parent cache lines
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * a.N) return;
     const int p = e >> 1;
     if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) return;   // no neighbour there
     if (!(e & 1) && (p % a.W) % CC_RUN != CC_RUN - 1) return;      // linked by k_cc_runs
     const int q = (e & 1) ? p + a.W : p + 1;
-    if (!same_set(a, p, q)) return;
+    if (!region_edge(a, p, q, mode)) return;
     int u = cc_find(par, p), v = cc_find(par, q);
     for (int it = 0; it < (1 << 20); ++it) {
         if (u == v) return;
@@ -932,44 +961,66 @@ __global__ void k_cc_hook(ForestArgs a, int* par)
     dev_fail(a.st, DEV_TIMEOUT, 41);
 }
 
-// edges per region (same-set edges, by their first end point's region root)
-__global__ void k_region_count(ForestArgs a, const int* label, int* rcnt)
+// The region kernels below stride over a grid of at most a few CTAs per SM,
+// so that where they have nothing to do they end at once.
+__global__ void k_cc_hook(ForestArgs a, int* par)
 {
-    if (a.risky && __ldcg(a.risky)) return;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // image order: neighbouring lanes share a region
-    if (e >= 2 * a.N) return;
-    const int p = e >> 1;
-    if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) return;
-    const int q = (e & 1) ? p + a.W : p + 1;
-    if (same_set(a, p, q)) count_by_key(rcnt, label[p]);
+    const int mode = region_mode(a);
+    if (mode < 0) return;
+    // edge ids in image order (the regions do not depend on the order), so
+    // that neighbouring threads share parent cache lines
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * a.N; e += gridDim.x * blockDim.x)
+        cc_hook_edge(a, par, e, mode);
 }
 
-// sort key of every same-set edge: its region label, with bit rbits set for
+// edges per region (region edges, by their first end point's region root)
+__global__ void k_region_count(ForestArgs a, const int* label, int* rcnt)
+{
+    const int mode = region_mode(a);
+    if (mode < 0) return;
+    // image order: neighbouring lanes share a region
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * a.N; e += gridDim.x * blockDim.x) {
+        const int p = e >> 1;
+        if ((e & 1) ? p + a.W >= a.N : (p % a.W) + 1 >= a.W) continue;
+        const int q = (e & 1) ? p + a.W : p + 1;
+        if (region_edge(a, p, q, mode)) count_by_key(rcnt, label[p]);
+    }
+}
+
+// sort key of every region edge: its region label, with bit rbits set for
 // regions of more than RG_SMALL edges (small regions come first); other
 // edges get 2^(rbits+1) - 1 and sort last.  nsmall counts the edges of the
-// small regions.
+// small regions; sort_n receives the list length for the sort (it stays 0,
+// and the sort does nothing, where these kernels have nothing to do).
 __global__ void k_region_keys(ForestArgs a, const int* label, const int* rcnt, int rbits, uint32_t* rk, uint32_t* rv,
-                              int* nvalid, int* nsmall)
+                              int* nvalid, int* nsmall, int* sort_n)
 {
-    if (a.risky && __ldcg(a.risky)) return;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false, small = false;
-    if (idx < *a.d_n) {
-        const uint32_t key = a.keys[idx];
-        int e, w, p, q;
-        decode(key, a.ebits, a.W, e, w, p, q);
-        valid = same_set(a, p, q);
-        uint32_t k = (2u << rbits) - 1u;
-        if (valid) {
-            const int r = label[p];
-            small = rcnt[r] <= RG_SMALL;
-            k = (uint32_t)r | (small ? 0u : 1u << rbits);
+    const int mode = region_mode(a);
+    if (mode < 0) return;
+    const int n = *a.d_n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sort_n = n;
+    int cv = 0, cs = 0;
+    for (int b0 = blockIdx.x * blockDim.x; b0 < n; b0 += gridDim.x * blockDim.x) {   // block-uniform trips
+        const int idx = b0 + threadIdx.x;
+        bool valid = false, small = false;
+        if (idx < n) {
+            const uint32_t key = a.keys[idx];
+            int e, w, p, q;
+            decode(key, a.ebits, a.W, e, w, p, q);
+            valid = region_edge(a, p, q, mode);
+            uint32_t k = (2u << rbits) - 1u;
+            if (valid) {
+                const int r = label[p];
+                small = rcnt[r] <= RG_SMALL;
+                k = (uint32_t)r | (small ? 0u : 1u << rbits);
+            }
+            rk[idx] = k;
+            rv[idx] = key;
         }
-        rk[idx] = k;
-        rv[idx] = key;
+        cv += __syncthreads_count(valid);
+        cs += __syncthreads_count(small);
     }
     // one atomic per block on each grid-wide count
-    const int cv = __syncthreads_count(valid), cs = __syncthreads_count(small);
     if (threadIdx.x == 0) {
         if (cv) atomicAdd(nvalid, cv);
         if (cs) atomicAdd(nsmall, cs);
@@ -982,20 +1033,43 @@ __global__ void k_region_keys(ForestArgs a, const int* label, const int* rcnt, i
 __global__ void k_region_buckets(ForestArgs a, const int* d_nvalid, const int* d_nsmall, int* wb_lo, int* wb_hi,
                                  int* nsmall_regions)
 {
-    if (a.risky && __ldcg(a.risky)) return;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x, nreg = *a.d_ncls;
-    if (r >= nreg) return;
-    const int s = a.cls_start[r];
-    if (s >= *d_nsmall) return;
-    const int e = r + 1 < nreg ? a.cls_start[r + 1] : *d_nvalid;
-    const int b = s / RG_SMALL;
-    atomicMin(wb_lo + b, s);
-    atomicMax(wb_hi + b, e);
-    grid_ticket(nsmall_regions);   // a count: one atomic per group of lanes
+    if (region_mode(a) < 0) return;
+    const int nreg = *a.d_ncls;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+        const int s = a.cls_start[r];
+        if (s >= *d_nsmall) continue;
+        const int e = r + 1 < nreg ? a.cls_start[r + 1] : *d_nvalid;
+        const int b = s / RG_SMALL;
+        atomicMin(wb_lo + b, s);
+        atomicMax(wb_hi + b, e);
+        grid_ticket(nsmall_regions);   // a count: one atomic per group of lanes
+    }
+}
+
+// A run [s, e) of the region-sorted list on a risky layer (one component, or
+// a bucket of whole small ones): every pass over it in windows of RK_EDGES,
+// with each local tree's TreeIntv in shared memory (as k_fh_risky does for
+// the whole list).
+__device__ void region_risky(const ForestArgs& a, const uint32_t* rkeys, int* loc, unsigned char* raw, int s, int e)
+{
+    RiskyWin& S = *reinterpret_cast<RiskyWin*>(raw);
+    uint32_t* ST = reinterpret_cast<uint32_t*>(raw + sizeof(RiskyWin));
+    for (int pass = 0; pass < a.passes; ++pass) {
+        const long long kq = a.crit_first && pass == 0 ? a.kq : (1LL << 60);
+        for (int base = s; base < e; base += RK_EDGES)
+            lw_window<true, RG_THREADS, RK_EDGES, true>(a, rkeys, loc, S, base, min(RK_EDGES, e - base), ST, kq);
+    }
+}
+
+__host__ __device__ constexpr size_t regions_smem()
+{
+    return sizeof(RegionWin) > risky_smem() ? sizeof(RegionWin) : risky_smem();
 }
 
 // Work items: every big region (its windows in order, on one CTA), then one
-// window per bucket of small regions.
+// window per bucket of small regions.  Layers without a risky edge: the
+// segment tree's first pass (engine 5).  Risky layers: every pass, region by
+// region (engine 7).
 __global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
                                                            const int* d_nsmall, const int* d_nsmall_regions,
                                                            const int* wb_lo, const int* wb_hi, int* loc, int* ticket)
@@ -1003,10 +1077,11 @@ __global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const u
     extern __shared__ __align__(16) unsigned char rg_raw[];
     RegionWin& S = *reinterpret_cast<RegionWin*>(rg_raw);
     __shared__ int s_r;
-    if (a.risky && __ldcg(a.risky)) return;
+    const int mode = region_mode(a);
+    if (mode < 0) return;
     const int nreg = *a.d_ncls, nv = *d_nvalid, nsr = *d_nsmall_regions;
     const int nbig = nreg - nsr, nbuckets = cdiv(*d_nsmall, RG_SMALL);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.engine = 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.engine = mode ? 7 : 5;
     for (;;) {
         if (threadIdx.x == 0) s_r = atomicAdd(ticket, 1);
         __syncthreads();
@@ -1015,11 +1090,18 @@ __global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const u
         if (t < nbig) {
             const int r = nsr + t;
             const int s = a.cls_start[r], e = r + 1 < nreg ? a.cls_start[r + 1] : nv;
-            for (int base = s; base < e; base += RG_EDGES)
-                lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
+            if (mode) {
+                region_risky(a, rkeys, loc, rg_raw, s, e);
+            } else {
+                for (int base = s; base < e; base += RG_EDGES)
+                    lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
+            }
         } else if (t - nbig < nbuckets) {
             const int lo = wb_lo[t - nbig], hi = wb_hi[t - nbig];
-            if (lo < hi) lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, lo, hi - lo);
+            if (lo < hi) {
+                if (mode) region_risky(a, rkeys, loc, rg_raw, lo, hi);
+                else lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, lo, hi - lo);
+            }
         } else {
             break;
         }
@@ -1057,18 +1139,18 @@ __global__ void k_T_init(uint32_t* T, const int* pixset, const uint32_t* table, 
 
 __global__ void k_class_flags(const uint32_t* keys, const int* d_n, int ebits, uint32_t* flags)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *d_n) return;
-    flags[i] = i == 0 || (keys[i] >> ebits) != (keys[i - 1] >> ebits);
+    const int n = *d_n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flags[i] = i == 0 || (keys[i] >> ebits) != (keys[i - 1] >> ebits);
 }
 
 __global__ void k_class_scatter(const uint32_t* flags, const uint32_t* pos, const int* d_n, int* cls_start,
                                 const uint32_t* total, int* ncls)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *ncls = (int)*total;
-    if (i >= *d_n) return;
-    if (flags[i] && pos[i] < (uint32_t)*d_n) cls_start[pos[i]] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ncls = (int)*total;
+    const int n = *d_n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (flags[i] && pos[i] < (uint32_t)n) cls_start[pos[i]] = i;
 }
 
 __global__ void k_flatten(int* parent, int* rootof, int* minid, int N)
@@ -1091,7 +1173,7 @@ __global__ void k_finish_roots(const int* rootof, const int* minid, int* dtroot,
     dtroot[v] = minid[r];
     if (r == v) {
         // the reservation engines of risky layers keep the unions themselves
-        bool maintained = pixset != nullptr && (*engine == 2 || *engine == 6);
+        bool maintained = pixset != nullptr && (*engine == 2 || *engine == 6 || *engine == 7);
         if (!maintained) {
             const uint32_t* src = pixset ? table + (size_t)pixset[v] * HDP_WORDS : full_mask;
             for (int k = 0; k < HDP_WORDS; ++k) T[(size_t)v * HDP_WORDS + k] = src[k];
@@ -1129,6 +1211,92 @@ cudaError_t coop_launch(const void* fn, int threads, void** args, cudaStream_t s
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, s);
 }
 
+
+// The region machinery's size-proportional steps, skipped where the region
+// kernels have nothing to do (a layer without a risky edge under risky_only)
+__global__ void k_region_flatten(ForestArgs a, int* parent, int* rootof, int* rcnt)
+{
+    if (region_mode(a) < 0) return;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.N; v += gridDim.x * blockDim.x) {
+        rcnt[v] = 0;   // per-region edge counts, made by k_region_count next
+        rootof[v] = uf_find(parent, v);
+    }
+}
+
+__global__ void k_region_init(ForestArgs a, int* parent, int* size, int* intw, int* best, int* best2, int* minid,
+                              int* loc, uint8_t* in_tree)
+{
+    if (region_mode(a) < 0) return;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.N; v += gridDim.x * blockDim.x) {
+        loc[v] = INT_MAX;
+        parent[v] = v;
+        size[v] = 1;
+        intw[v] = 0;
+        best[v] = INT_MAX;
+        best2[v] = INT_MAX;
+        minid[v] = INT_MAX;
+        in_tree[2 * v] = 0;
+        in_tree[2 * v + 1] = 0;
+    }
+}
+
+// The region engine on an HDP layer: label the regions (lock-free
+// union-find), sort the region edges by region (the strict order kept inside
+// each), and resolve them region by region on persistent CTAs (k_fh_regions).
+// Every kernel reads the layer's risky flag: without a risky edge the regions
+// are the same-set regions and the pass is the segment tree's first; with one
+// they are the components of the edges that survive DT-Rule 1 and every pass
+// runs there (a.passes, a.crit_first).  With a.risky_only set a layer without
+// a risky edge makes every kernel return at once.
+static void launch_regions(Ctx& c, ForestArgs& a, const LayerDims& d)
+{
+    const int N = d.N;
+    k_cc_runs<<<cdiv(cdiv(d.W, CC_RUN) * d.H, 256), 256, 0, c.s>>>(a, c.parent);
+    const int g2 = min(cdiv(2 * N, 256), 4 * c.num_sms), g1 = min(cdiv(N, 256), 4 * c.num_sms);
+    k_cc_hook<<<g2, 256, 0, c.s>>>(a, c.parent);
+    int* rcnt = c.minid;   // free until k_region_init below
+    k_region_flatten<<<g1, 256, 0, c.s>>>(a, c.parent, c.rootof, rcnt);
+    int* nvalid = c.ints + IDX_TMP3;
+    int* nsmall = c.ints + IDX_CTR3;
+    int* nsmall_regions = c.ints + IDX_CTR4;
+    cudaMemsetAsync(nvalid, 0, sizeof(int), c.s);
+    cudaMemsetAsync(nsmall, 0, 2 * sizeof(int), c.s);   // and nsmall_regions
+    k_region_count<<<g2, 256, 0, c.s>>>(a, c.rootof, rcnt);
+    int rbits = 1;   // labels < N < 2^rbits, so no big key equals the all-ones "other" key
+    while ((1 << rbits) <= N) ++rbits;
+    int* sort_n = c.ints + IDX_RSORTN;
+    cudaMemsetAsync(sort_n, 0, sizeof(int), c.s);
+    k_region_keys<<<g2, 256, 0, c.s>>>(a, c.rootof, rcnt, rbits, (uint32_t*)c.listA, (uint32_t*)c.listB, nvalid,
+                                       nsmall, sort_n);
+    const int where = radix_sort((uint32_t*)c.listA, (uint32_t*)c.listB, (uint32_t*)c.raA, (uint32_t*)c.raB,
+                                 sort_n, 2 * N, rbits + 1, c.tmp, c.scan, c.s);
+    const uint32_t* rk = (const uint32_t*)(where ? c.raA : c.listA);
+    const uint32_t* rv = (const uint32_t*)(where ? c.raB : c.listB);
+    uint32_t* flags = (uint32_t*)c.rbA;
+    uint32_t* pos = (uint32_t*)c.rbB;
+    uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
+    k_class_flags<<<g2, 256, 0, c.s>>>(rk, nvalid, 0, flags);
+    scan_u32(flags, pos, nvalid, 2 * N, true, c.scan, total, c.s);
+    k_class_scatter<<<g2, 256, 0, c.s>>>(flags, pos, nvalid, c.cls_start, total, c.ints + IDX_NCLS);
+    int* wb_lo = c.rbA;     // buckets (at most 2N / RG_SMALL): the flag/scan buffers are free again
+    int* wb_hi = c.rbB;
+    const int nb = cdiv(2 * N, RG_SMALL);
+    k_fill_int_f<<<cdiv(nb, 256), 256, 0, c.s>>>(wb_lo, nb, INT_MAX);
+    cudaMemsetAsync(wb_hi, 0, sizeof(int) * (size_t)nb, c.s);
+    k_region_buckets<<<g1, 256, 0, c.s>>>(a, nvalid, nsmall, wb_lo, wb_hi, nsmall_regions);
+    k_region_init<<<g1, 256, 0, c.s>>>(a, c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, c.in_tree);
+    int* ticket = c.ints + IDX_TMP2;
+    cudaMemsetAsync(ticket, 0, sizeof(int), c.s);
+    static int rg_per_sm = 0;
+    if (rg_per_sm == 0) {
+        cudaFuncSetAttribute(k_fh_regions, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)regions_smem());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rg_per_sm, k_fh_regions, RG_THREADS, regions_smem());
+        if (rg_per_sm < 1) rg_per_sm = 1;
+    }
+    const int rg = min(rg_per_sm, c.tune.region_ctas_per_sm);
+    k_fh_regions<<<c.num_sms * rg, RG_THREADS, regions_smem(), c.s>>>(a, rv, nvalid, nsmall, nsmall_regions, wb_lo,
+                                                                     wb_hi, c.rootof, ticket);
+}
 
 void launch_forest(Ctx& c, int l, int hdp)
 {
@@ -1191,64 +1359,30 @@ void launch_forest(Ctx& c, int l, int hdp)
     if (!st_tree) {
         a.passes = 1;
         a.crit_first = 0;
-        coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
-        if (hdp) launch_risky(a, c);
-    } else if (hdp && N < c.tune.region_max_nodes) {
-        // HDP layer: regions.  Label the connected same-set regions
-        // (lock-free union-find), sort the edges by region, resolve the
-        // first pass region by region, then link by Boruvka.  With risky
-        // edges every step but the last returns at once and k_fh_risky runs
-        // both passes.
-        k_cc_runs<<<cdiv(cdiv(d.W, CC_RUN) * d.H, 256), 256, 0, c.s>>>(a, c.parent);
-        k_cc_hook<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.parent);
-        k_flatten<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.rootof, c.minid, N);
-        int* nvalid = c.ints + IDX_TMP3;
-        int* nsmall = c.ints + IDX_CTR3;
-        int* nsmall_regions = c.ints + IDX_CTR4;
-        cudaMemsetAsync(nvalid, 0, sizeof(int), c.s);
-        cudaMemsetAsync(nsmall, 0, 2 * sizeof(int), c.s);   // and nsmall_regions
-        int* rcnt = c.minid;   // free until k_forest_init below
-        cudaMemsetAsync(rcnt, 0, sizeof(int) * (size_t)N, c.s);
-        k_region_count<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, rcnt);
-        int rbits = 1;   // labels < N < 2^rbits, so no big key equals the all-ones "other" key
-        while ((1 << rbits) <= N) ++rbits;
-        k_region_keys<<<cdiv(2 * N, 256), 256, 0, c.s>>>(a, c.rootof, rcnt, rbits, (uint32_t*)c.listA,
-                                                          (uint32_t*)c.listB, nvalid, nsmall);
-        const int where = radix_sort((uint32_t*)c.listA, (uint32_t*)c.listB, (uint32_t*)c.raA, (uint32_t*)c.raB,
-                                     c.ints + IDX_NEDGES, 2 * N, rbits + 1, c.tmp, c.scan, c.s);
-        const uint32_t* rk = (const uint32_t*)(where ? c.raA : c.listA);
-        const uint32_t* rv = (const uint32_t*)(where ? c.raB : c.listB);
-        uint32_t* flags = (uint32_t*)c.rbA;
-        uint32_t* pos = (uint32_t*)c.rbB;
-        uint32_t* total = (uint32_t*)(c.ints + IDX_TMP0);
-        k_class_flags<<<cdiv(2 * N, 256), 256, 0, c.s>>>(rk, nvalid, 0, flags);
-        scan_u32(flags, pos, nvalid, 2 * N, true, c.scan, total, c.s);
-        k_class_scatter<<<cdiv(2 * N, 256), 256, 0, c.s>>>(flags, pos, nvalid, c.cls_start, total, c.ints + IDX_NCLS);
-        int* wb_lo = c.rbA;     // buckets (at most 2N / RG_SMALL): the flag/scan buffers are free again
-        int* wb_hi = c.rbB;
-        const int nb = cdiv(2 * N, RG_SMALL);
-        k_fill_int_f<<<cdiv(nb, 256), 256, 0, c.s>>>(wb_lo, nb, INT_MAX);
-        cudaMemsetAsync(wb_hi, 0, sizeof(int) * (size_t)nb, c.s);
-        k_region_buckets<<<cdiv(N, 256), 256, 0, c.s>>>(a, nvalid, nsmall, wb_lo, wb_hi, nsmall_regions);
-        k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
-        cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
-        int* ticket = c.ints + IDX_TMP2;
-        cudaMemsetAsync(ticket, 0, sizeof(int), c.s);
-        static int rg_per_sm = 0;
-        if (rg_per_sm == 0) {
-            cudaFuncSetAttribute(k_fh_regions, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RegionWin));
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rg_per_sm, k_fh_regions, RG_THREADS, sizeof(RegionWin));
-            if (rg_per_sm < 1) rg_per_sm = 1;
+        if (hdp && N < c.tune.region_max_nodes) {
+            // a risky HDP layer: its components region by region; every
+            // region kernel returns at once on the other layers, which
+            // Boruvka takes
+            a.risky_only = 1;
+            launch_regions(c, a, d);
+            a.risky_only = 0;
+            cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
+            cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
+            coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+        } else {
+            coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
+            if (hdp) launch_risky(a, c);
         }
-        const int rg = min(rg_per_sm, c.tune.region_ctas_per_sm);
-        k_fh_regions<<<c.num_sms * rg, RG_THREADS, sizeof(RegionWin), c.s>>>(a, rv, nvalid, nsmall, nsmall_regions,
-                                                                            wb_lo, wb_hi, c.rootof, ticket);
-        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
-        cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
+    } else if (hdp && N < c.tune.region_max_nodes) {
+        // HDP layer: regions.  Without a risky edge the first pass region by
+        // region, then the linking pass by Boruvka; a risky layer takes both
+        // passes region by region and Boruvka returns at once.
         a.passes = 2;
         a.crit_first = 1;
+        launch_regions(c, a, d);
+        cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
+        cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);
         coop_launch((const void*)k_boruvka, FOREST_THREADS, args, c.s, 1, nullptr, 0, bor_blocks);
-        launch_risky(a, c);
     } else if (!small) {
         // first pass by weight classes and windows, then the linking pass by Boruvka
         uint32_t* flags = c.sorted == c.keys0 ? c.keys1 : c.keys0;

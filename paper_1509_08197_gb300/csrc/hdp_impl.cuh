@@ -182,7 +182,7 @@ struct Ctx {
 // slots of Ctx::ints
 enum {
     IDX_NEDGES = 0, IDX_RISKY, IDX_NCLS, IDX_NARCS, IDX_N, IDX_CTR0, IDX_CTR1, IDX_CTR2, IDX_CTR3, IDX_CTR4,
-    IDX_K, IDX_NTREES, IDX_NLC, IDX_NUNITS, IDX_ENGINE, IDX_CHANGED, IDX_DRROUNDS, IDX_DRWINDOWS, IDX_NNODES, IDX_ESLOTS,
+    IDX_K, IDX_NTREES, IDX_NLC, IDX_NUNITS, IDX_ENGINE, IDX_CHANGED, IDX_DRROUNDS, IDX_DRWINDOWS, IDX_NNODES, IDX_ESLOTS, IDX_RSORTN,
     IDX_TMP0 = 24, IDX_TMP1, IDX_TMP2, IDX_TMP3, IDX_COUNT = 32
 };
 

@@ -21,11 +21,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _run_layers(hp, pair, check_costs=True, layers=None):
+def _run_layers(hp, pair, check_costs=True, layers=None, tuning=None):
     """Run every layer on both sides; return per-layer comparison records."""
     dev = torch.device("cuda:0")
     ctx = hdp.hdp_create(hp)
     try:
+        if tuning:
+            t = hdp.hdp_get_tuning(ctx)
+            for k, v in tuning.items():
+                setattr(t, k, v)
+            hdp.hdp_set_tuning(ctx, t)
         left = torch.from_numpy(pair.left).to(dev).contiguous()
         right = torch.from_numpy(pair.right).to(dev).contiguous()
         hdp.hdp_build_trees(ctx, left, right)
@@ -109,7 +114,7 @@ def test_random_tree(case):
         hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=1, mode="full", tree="rt", rt_seed=14)
     res = _run_layers(hp, pair)
     if case == "third_hdp_risky":
-        assert int(res[0][0]["info"][5]) == 1 and int(res[0][0]["info"][3]) == 6
+        assert int(res[0][0]["info"][5]) == 1 and int(res[0][0]["info"][3]) == 7
     for l, (g, o) in res.items():
         _assert_layer(l, g, o, hp, None)
 
@@ -177,18 +182,20 @@ def test_third_size_hdp(tree):
         _assert_layer(l, g, o, hp, None)
 
 
-@pytest.mark.parametrize("tree", ["mst", "st"])
-def test_risky_layers_take_the_reservation_engine(tree):
+@pytest.mark.parametrize("tree,one_cta", [("mst", False), ("st", False), ("mst", True), ("st", True)])
+def test_risky_layers_take_the_reservation_engine(tree, one_cta):
     # beta = 1/5: DT-Rule 2 joins many different sets, so the lower layers are
-    # "risky" and only reservations are exact there: the windowed engine with
-    # each local tree's TreeIntv in shared memory (engine 6)
+    # "risky" and only reservations are exact there: windows with each local
+    # tree's TreeIntv in shared memory, over each component of the edges that
+    # survive DT-Rule 1 on its own CTA (engine 7), or over the whole list on
+    # one CTA when the region engine is switched off (engine 6)
     pair = workload_pair("third")
     hp = hdp.HDPParams(width=463, height=370, max_disp=79, levels=3, tree=tree, beta=(1, 5))
-    res = _run_layers(hp, pair)
+    res = _run_layers(hp, pair, tuning=dict(region_max_nodes=1) if one_cta else None)
     risky = {l: int(g["info"][5]) for l, (g, o) in res.items()}
     engine = {l: int(g["info"][3]) for l, (g, o) in res.items()}
     assert risky[0] == 1 and risky[1] == 1, risky
-    assert all(engine[l] == 6 for l in risky if risky[l]), engine
+    assert all(engine[l] == (6 if one_cta else 7) for l in risky if risky[l]), engine
     for l, (g, o) in res.items():
         _assert_layer(l, g, o, hp, None)
 
