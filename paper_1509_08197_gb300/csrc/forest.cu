@@ -20,15 +20,19 @@
 //    criterion fails at its earliest pending edge is frozen for good.
 //  * Regions (segment-tree first pass of predicted layers without risky
 //    edges): connected same-set regions are independent, so persistent CTAs
-//    take whole regions (small ones packed together) window by window.
+//    take whole regions (small ones packed together) window by window.  On a
+//    risky layer the regions are the connected components of the edges that
+//    survive DT-Rule 1 (no edge joins two of them), and every pass runs there
+//    with the windows of the risky engine below.
 //  * Hybrid first pass (big full-range layers): a weight class with many
 //    edges is a Boruvka by edge id over the whole grid, for the same reason;
 //    runs of small classes form windows resolved as above.
 //  * Windows for risky HDP layers (an edge between different sets whose
 //    Jaccard ratio reaches beta, so DT-Rule 2 may join different sets and
-//    the regions are not independent): every pass over the whole list in one
-//    CTA, window by window, by deterministic reservations in shared memory,
-//    with each local tree's TreeIntv there too.  An edge that holds the
+//    same-set regions are not independent): every pass over the whole list
+//    (or over each component, above) in one CTA, window by window, by
+//    deterministic reservations in shared memory, with each local tree's
+//    TreeIntv there too.  An edge that holds the
 //    reservation of both its trees is decided on their current state,
 //    exactly as the sequential algorithm decides it.
 #include "hdp_impl.cuh"
