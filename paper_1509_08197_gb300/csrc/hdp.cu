@@ -1200,6 +1200,16 @@ extern "C" int hdp_cost_volume_bwd(hdp_ctx* ctx, float alpha, float tau_c, float
 // ------------------------------------------------------------------ batch ---
 #define HDP_BATCH_MAX 1024
 
+// pairs whose layers have the same sizes, mode and storage (their tiles fall
+// in the same classes at every level but the top one)
+static bool same_geometry(const Ctx& a, const Ctx& b)
+{
+    if (a.nlev != b.nlev || a.p.storage != b.p.storage || a.p.mode != b.p.mode) return false;
+    for (int l = 0; l < a.nlev; ++l)
+        if (a.dim[l].W != b.dim[l].W || a.dim[l].H != b.dim[l].H) return false;
+    return true;
+}
+
 extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_left, const uint8_t* const* d_right,
                                const int* pitch, int32_t* const* d_out)
 {
@@ -1229,34 +1239,54 @@ extern "C" int hdp_match_batch(hdp_ctx** ctxs, int n, const uint8_t* const* d_le
             if (rc) return rc;
         }
     } else {
-        // level by level: each pair prepares the level on its own stream (interval
-        // prediction, edges, forest, orders), then one aggregation launch per pass
-        // and tile class takes the tiles of every pair (a6-a7 of the batch in one
-        // launch per level), then the pairs go on
+        // level by level in groups of pairs of one geometry (the same layer sizes,
+        // so the same tile classes): each pair prepares the level on its own
+        // stream (interval prediction, edges, forest, orders), then one
+        // aggregation launch per pass and tile class takes the tiles of every
+        // pair of the group (a6-a7 in one launch per level), then the group's
+        // pairs go on.  Groups wait only for their own pairs, so one group's
+        // aggregation overlaps another's forests.
         Ctx* cs[HDP_BATCH_MAX];
+        int order[HDP_BATCH_MAX], gstart[HDP_BATCH_MAX + 1];
+        int ng = 0, m = 0;
         for (int i = 0; i < n; ++i) {
-            cs[i] = &ctxs[i]->c;
             ctxs[i]->use_side = 0;
             int rc = hdp_build_trees(ctxs[i], d_left[i], d_right[i], pitch[i]);
             ctxs[i]->use_side = 1;
             if (rc) return rc;
             ctxs[i]->c.refined = 0;
         }
+        // groups in order of first appearance, pairs in batch order inside each
+        for (int i = 0; i < n; ++i) {
+            bool seen = false;
+            for (int j = 0; j < i && !seen; ++j) seen = same_geometry(ctxs[i]->c, ctxs[j]->c);
+            if (seen) continue;
+            gstart[ng++] = m;
+            for (int j = i; j < n; ++j)
+                if (same_geometry(ctxs[i]->c, ctxs[j]->c)) order[m++] = j;
+        }
+        gstart[ng] = m;
+        for (int k = 0; k < n; ++k) cs[k] = &ctxs[order[k]]->c;
         for (int l = ctx->c.top; l >= 0; --l) {
-            for (int i = 0; i < n; ++i) {
-                int rc = run_level_pre(ctxs[i], l);
-                if (rc) return rc;
-                aggregate_clear(ctxs[i]->c);
-                if (i > 0) {
-                    TRY_CUDA(cudaEventRecord(ctxs[i]->join, ctxs[i]->c.s));
-                    TRY_CUDA(cudaStreamWaitEvent(ctx->c.s, ctxs[i]->join, 0));
+            for (int g = 0; g < ng; ++g) {
+                hdp_ctx* lead = ctxs[order[gstart[g]]];
+                for (int k = gstart[g]; k < gstart[g + 1]; ++k) {
+                    hdp_ctx* x = ctxs[order[k]];
+                    int rc = run_level_pre(x, l);
+                    if (rc) return rc;
+                    aggregate_clear(x->c);
+                    if (x != lead) {
+                        TRY_CUDA(cudaEventRecord(x->join, x->c.s));
+                        TRY_CUDA(cudaStreamWaitEvent(lead->c.s, x->join, 0));
+                    }
                 }
+                launch_aggregate_multi(cs + gstart[g], gstart[g + 1] - gstart[g], l, lead->c.s);
+                int rc = check_launch(lead, "hdp_match_batch");
+                if (rc) return rc;
+                TRY_CUDA(cudaEventRecord(lead->fork, lead->c.s));
+                for (int k = gstart[g] + 1; k < gstart[g + 1]; ++k)
+                    TRY_CUDA(cudaStreamWaitEvent(ctxs[order[k]]->c.s, lead->fork, 0));
             }
-            launch_aggregate_multi(cs, n, l, ctx->c.s);
-            int rc = check_launch(ctx, "hdp_match_batch");
-            if (rc) return rc;
-            TRY_CUDA(cudaEventRecord(ctx->fork, ctx->c.s));
-            for (int i = 1; i < n; ++i) TRY_CUDA(cudaStreamWaitEvent(ctxs[i]->c.s, ctx->fork, 0));
         }
         for (int i = 0; i < n; ++i)
             TRY_CUDA(cudaMemcpyAsync(d_out[i], ctxs[i]->c.disp[0], sizeof(int32_t) * ctxs[i]->c.dim[0].N,
