@@ -105,9 +105,12 @@ typedef struct {
 } hdp_params;
 
 /*
- * Launch-shape knobs (no counterpart in the paper).  Every setting gives the
+ * Launch-shape knobs (no counterpart in the paper).  The first six give the
  * same results bit for bit (the forest engines are exact, and the carries of
  * the aggregation are evaluated in a fixed order); only the speed changes.
+ * The three layout knobs below keep forests, orders and every other integer
+ * stage bit for bit, but a tile size fixes the order of the FP32 additions,
+ * so aggregated costs move within rounding and the WTA only at near ties.
  * Defaults in brackets; hdp_set_tuning rejects values outside the ranges.
  *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..8 [8] (each
  *                          kernel also stops at its own occupancy: 4 CTAs
@@ -129,6 +132,24 @@ typedef struct {
  *                          edges that survive DT-Rule 1; bigger layers take
  *                          the first pass by weight class and a risky layer
  *                          on one CTA, 0..1<<30 [1<<24]
+ * Aggregation layout: how many costs a tile holds and which kernel walks it.
+ *   tile_small_nodes       one-label-set layers (full range, the top layer)
+ *                          with fewer nodes use tiles of 512 costs (else the
+ *                          column kernel or tiles of 2048), 0..1<<30 [1<<17]
+ *   tile_small_nodes_hdp   predicted layers with fewer nodes use tiles of 512
+ *                          costs, bigger ones 1024, 0..1<<30 [1<<19]
+ *   col_min_labels         one-label-set layers of at least tile_small_nodes
+ *                          nodes whose rows hold at least this many label
+ *                          slots take the column kernel (a CTA per tile of
+ *                          8192 costs, a thread per two labels) instead of
+ *                          the warp kernel (a warp per tile, four labels per
+ *                          lane step), 64..257 [64] (257: never)
+ * A tuning whose layouts need more tiles than the context's look-back scratch
+ * holds is refused with HDP_ERR_ARG; hdp_create sizes it for the defaults
+ * and for one-set layers on the warp kernel (smaller tiles than the defaults
+ * on the biggest layer usually do not fit).
+ * A layer keeps the tile size its layout was built with until it is built
+ * again.
  */
 typedef struct {
     int agg_ctas_per_sm;
@@ -137,6 +158,9 @@ typedef struct {
     int one_cta_nodes;
     int boruvka_edges_per_cta;
     int region_max_nodes;
+    int tile_small_nodes;
+    int tile_small_nodes_hdp;
+    int col_min_labels;
 } hdp_tuning;
 
 /* Fill p with the paper's settings (Sec. 4.1) for a width x height image:

@@ -157,10 +157,13 @@ def load(path: str = LIB_PATH):
 
 
 class Tuning(ctypes.Structure):
-    """hdp_tuning: launch-shape knobs; every setting gives identical results."""
+    """hdp_tuning: launch-shape knobs.  The launch knobs give identical results; the layout knobs (tile sizes,
+    column or warp kernel) keep every integer stage identical and move aggregated costs within FP32 rounding."""
     _fields_ = [("agg_ctas_per_sm", ctypes.c_int), ("region_ctas_per_sm", ctypes.c_int),
                 ("big_class_edges", ctypes.c_int), ("one_cta_nodes", ctypes.c_int),
-                ("boruvka_edges_per_cta", ctypes.c_int), ("region_max_nodes", ctypes.c_int)]
+                ("boruvka_edges_per_cta", ctypes.c_int), ("region_max_nodes", ctypes.c_int),
+                ("tile_small_nodes", ctypes.c_int), ("tile_small_nodes_hdp", ctypes.c_int),
+                ("col_min_labels", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1297,7 +1297,7 @@ void launch_aggregate_ex(Ctx& c, int l, const float* Ein, float* vol_up, float* 
     // one launch per pass over every tile of the layer, in dependency order
     aggregate_clear(c);
     const bool fp16 = c.p.storage == HDP_STORE_FP16;
-    const int tf = layer_tile_floats(c, l);
+    const int tf = c.layer_tf[l];   // the size the layout was built with
     const int cap = c.tune.agg_ctas_per_sm;
     const int kp = (d.d + 1 + 3) / 4 * 4;
     if (tf == TILE_FLOATS_COL) {
@@ -1426,7 +1426,7 @@ int launch_aggregate_multi(Ctx* const* cs, int n, int l, cudaStream_t s)
                 int num_sms = 0, cap = 8;
                 for (; i < n && m.n < AGG_MULTI_MAX; ++i) {
                     Ctx& c = *cs[i];
-                    if ((c.p.storage == HDP_STORE_FP16) != (fp == 1) || layer_tile_floats(c, l) != tfs[k]) continue;
+                    if ((c.p.storage == HDP_STORE_FP16) != (fp == 1) || c.layer_tf[l] != tfs[k]) continue;
                     m.a[m.n++] = make_agg_args(c, l, nullptr, nullptr, nullptr);
                     num_sms = c.num_sms;
                     cap = min(cap, c.tune.agg_ctas_per_sm);
@@ -1439,7 +1439,7 @@ int launch_aggregate_multi(Ctx* const* cs, int n, int l, cudaStream_t s)
         }
     for (int i = 0; i < n; ++i) {
         Ctx& c = *cs[i];
-        if (layer_tile_floats(c, l) != TILE_FLOATS_COL) continue;
+        if (c.layer_tf[l] != TILE_FLOATS_COL) continue;
         const AggArgs a = make_agg_args(c, l, nullptr, nullptr, nullptr);
         const int kp = (c.dim[l].d + 1 + 3) / 4 * 4;
         launch_col<true>(a, c.p.storage == HDP_STORE_FP16, kp, c.num_sms, s);

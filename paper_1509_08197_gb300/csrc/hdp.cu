@@ -96,6 +96,26 @@ static T* carve(Ctx& c, size_t count)
 }
 
 // lay out every buffer; with c.arena == nullptr this only measures
+// look-back scratch entries (tiles) the layouts of every layer need under
+// tuning t: every tile but the last of a run is full; with one label set per
+// layer (full range, top layer) it holds tile_rows_of(kp, extra, tf) rows,
+// otherwise at least 4 * tile_rows_max(tf) costs (the narrowest rows); plus
+// one partial tile per (light level, width) run
+static size_t tiles_needed(const Ctx& c, const hdp_tuning& t)
+{
+    size_t tiles = 0;
+    for (int l = 0; l < c.nlev; ++l) {
+        const size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
+        const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.nlev - 1;
+        const int extra = c.p.storage == HDP_STORE_FP16 ? 4 : 0;
+        const int tf = tile_floats_for(c, l, t);
+        const size_t n = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp, extra, tf)
+                                 : (size_t)c.dim[l].N * kp / (4 * tile_rows_max(tf));
+        tiles = std::max(tiles, n);
+    }
+    return tiles + 2 * 2048 + 16;
+}
+
 static void layout_buffers(Ctx& c)
 {
     c.arena_used = 0;
@@ -207,22 +227,13 @@ static void layout_buffers(Ctx& c)
     c.scan4.aggv = carve<I4>(c, c.scan4.max_tiles);
     c.scan4.inclv = carve<I4>(c, c.scan4.max_tiles);
     c.scan4.ctr = carve<unsigned int>(c, 2);
-    size_t K = 0, tiles = 0;
-    for (int l = 0; l < c.nlev; ++l) {
-        size_t kp = (size_t)((c.dim[l].d + 1 + 3) / 4 * 4);
-        K = std::max(K, (size_t)c.dim[l].N * kp);
-        // every tile but the last of a run is full: with one label set per
-        // layer (full range, top layer) it holds tile_rows_of(kp, extra, tf) rows,
-        // otherwise at least 4 * tile_rows_max(tf) costs (the narrowest rows)
-        const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.nlev - 1;
-        const int extra = c.p.storage == HDP_STORE_FP16 ? 4 : 0;
-        const int tf = layer_tile_floats(c, l);
-        size_t t = one_set ? (size_t)c.dim[l].N / tile_rows_of((int)kp, extra, tf)
-                           : (size_t)c.dim[l].N * kp / (4 * tile_rows_max(tf));
-        tiles = std::max(tiles, t);
-    }
+    size_t K = 0;
+    for (int l = 0; l < c.nlev; ++l) K = std::max(K, (size_t)c.dim[l].N * (size_t)((c.dim[l].d + 1 + 3) / 4 * 4));
     c.vol_elems = K;
-    c.max_tiles = tiles + 2 * 2048 + 16;   // + one partial tile per (light level, width) run
+    // the defaults, and one-set layers on the warp kernel instead of the column kernel
+    hdp_tuning warp = c.tune;
+    warp.col_min_labels = 257;
+    c.max_tiles = std::max(tiles_needed(c, c.tune), tiles_needed(c, warp));
     c.tflags = carve<int>(c, 4 * c.max_tiles);   // look-back flags, then done flags, of both passes
     c.aggA = carve<float>(c, c.max_tiles * SCR_STRIDE);
     c.inclA = carve<float>(c, c.max_tiles * SCR_STRIDE);
@@ -499,6 +510,17 @@ static const char* tuning_error(const hdp_tuning& t)
     if (t.one_cta_nodes < 1024 || t.one_cta_nodes > (1 << 24)) return "one_cta_nodes out of 1024..1<<24";
     if (t.boruvka_edges_per_cta < 512 || t.boruvka_edges_per_cta > (1 << 20)) return "boruvka_edges_per_cta out of 512..1<<20";
     if (t.region_max_nodes < 0 || t.region_max_nodes > (1 << 30)) return "region_max_nodes out of 0..1<<30";
+    if (t.tile_small_nodes < 0 || t.tile_small_nodes > (1 << 30)) return "tile_small_nodes out of 0..1<<30";
+    if (t.tile_small_nodes_hdp < 0 || t.tile_small_nodes_hdp > (1 << 30)) return "tile_small_nodes_hdp out of 0..1<<30";
+    if (t.col_min_labels < COL_MIN_KP || t.col_min_labels > 257) return "col_min_labels out of 64..257";
+    return nullptr;
+}
+
+// a tuning this context can run: valid knobs, and layouts that fit its look-back scratch
+static const char* tuning_error(const Ctx& c, const hdp_tuning& t)
+{
+    if (const char* why = tuning_error(t)) return why;
+    if (tiles_needed(c, t) > c.max_tiles) return "these tile sizes need more look-back scratch than the context holds";
     return nullptr;
 }
 
@@ -512,7 +534,7 @@ extern "C" int hdp_get_tuning(const hdp_ctx* ctx, hdp_tuning* out)
 extern "C" int hdp_set_tuning(hdp_ctx* ctx, const hdp_tuning* t)
 {
     if (!ctx || !t) return HDP_ERR_ARG;
-    if (const char* why = tuning_error(*t)) return fail(ctx, HDP_ERR_ARG, why);
+    if (const char* why = tuning_error(ctx->c, *t)) return fail(ctx, HDP_ERR_ARG, why);
     ctx->c.tune = *t;
     drop_host_graph(ctx);   // captured with the old launch shapes
     return HDP_OK;
@@ -559,20 +581,28 @@ extern "C" int hdp_autotune(hdp_ctx* ctx, const uint8_t* d_left, const uint8_t* 
     float best = 0.f;
     int rc = tune_time(ctx, d_left, d_right, pitch, reps, &best);   // also warms up
     if (rc == HDP_OK) rc = tune_time(ctx, d_left, d_right, pitch, reps, &best);
-    static const int cand[6][5] = {{2048, 4096, 8192, 16384, 0},
+    // per knob a few candidates (0 ends a list); the layout knobs choose the
+    // tile sizes (how long a carry chain a tile covers) and, for one-set
+    // layers, the kernel (a thread per two labels or a warp per tile)
+    static const int cand[9][5] = {{2048, 4096, 8192, 16384, 0},
                                    {512, 1024, 2048, 4096, 0},
                                    {32768, 131072, 524288, 0, 0},
                                    {262144, 1 << 20, 1 << 24, 0, 0},
                                    {1, 2, 4, 0, 0},
-                                   {3, 4, 5, 0, 0}};
-    for (int k = 0; k < 6 && rc == HDP_OK; ++k) {
+                                   {4, 5, 6, 8, 0},
+                                   {1 << 15, 1 << 17, 1 << 19, 0, 0},
+                                   {1 << 17, 1 << 19, 1 << 21, 0, 0},
+                                   {64, 128, 257, 0, 0}};
+    for (int k = 0; k < 9 && rc == HDP_OK; ++k) {
         hdp_tuning keep = c.tune;
         for (int j = 0; j < 5 && cand[k][j] && rc == HDP_OK; ++j) {
             hdp_tuning t = keep;
             int* f = k == 0 ? &t.boruvka_edges_per_cta : k == 1 ? &t.big_class_edges : k == 2 ? &t.one_cta_nodes
-                   : k == 3 ? &t.region_max_nodes : k == 4 ? &t.region_ctas_per_sm : &t.agg_ctas_per_sm;
+                   : k == 3 ? &t.region_max_nodes : k == 4 ? &t.region_ctas_per_sm : k == 5 ? &t.agg_ctas_per_sm
+                   : k == 6 ? &t.tile_small_nodes : k == 7 ? &t.tile_small_nodes_hdp : &t.col_min_labels;
             if (*f == cand[k][j]) continue;
             *f = cand[k][j];
+            if (tuning_error(c, t)) continue;   // e.g. more tiles than the look-back scratch holds
             c.tune = t;
             float ms = 0.f;
             rc = tune_time(ctx, d_left, d_right, pitch, reps, &ms);

@@ -34,6 +34,8 @@
 #define AGG_MINB_1024 7
 #define AGG_MINB_512 5
 #define AGG_CTAS_DEFAULT 8
+// defaults of the layout knobs (hdp_tuning): below these node counts layers
+// take 512-float tiles
 #define SMALL_TILE_NODES (1 << 17)       // layers with one label set (full range, the top layer)
 #define SMALL_TILE_NODES_HDP (1 << 19)   // predicted layers (the 1390x1110 pair: layers 1-3)
 #define SCR_STRIDE 264   // floats per tile in the look-back scratch (256 labels + mass, padded)
@@ -60,7 +62,9 @@ struct CostK {
 
 struct Ctx {
     hdp_params p;
-    hdp_tuning tune = {AGG_CTAS_DEFAULT, 4, 2048, 131072, 4096, 1 << 24};
+    hdp_tuning tune = {AGG_CTAS_DEFAULT, 4, 2048, 131072, 4096, 1 << 24, SMALL_TILE_NODES, SMALL_TILE_NODES_HDP,
+                       COL_MIN_KP};
+    int layer_tf[HDP_MAX_LEVELS] = {};   // tile size each layer's layout was built with (launch_order)
     cudaStream_t s = nullptr;
     // side stream: the priors and interval tables of the predicted layers need
     // only that layer's images, so they run beside the coarser layers' work
@@ -188,13 +192,16 @@ enum {
 
 // image.cu
 // the aggregation tile size of layer l (see TILE_FLOATS_HDP)
-inline int layer_tile_floats(const Ctx& c, int l)
+// tile size of layer l's aggregation layout under tuning t
+inline int tile_floats_for(const Ctx& c, int l, const hdp_tuning& t)
 {
     const bool one_set = c.p.mode == HDP_MODE_FULL || l == c.top;
-    if (c.dim[l].N < (one_set ? SMALL_TILE_NODES : SMALL_TILE_NODES_HDP)) return TILE_FLOATS_SMALL;
-    if (one_set && (c.dim[l].d + 1 + 3) / 4 * 4 >= COL_MIN_KP) return TILE_FLOATS_COL;
+    if (c.dim[l].N < (one_set ? t.tile_small_nodes : t.tile_small_nodes_hdp)) return TILE_FLOATS_SMALL;
+    if (one_set && (c.dim[l].d + 1 + 3) / 4 * 4 >= t.col_min_labels) return TILE_FLOATS_COL;
     return one_set ? TILE_FLOATS : TILE_FLOATS_HDP;
 }
+// for a new layout (the aggregation then reads c.layer_tf[l])
+inline int layer_tile_floats(const Ctx& c, int l) { return tile_floats_for(c, l, c.tune); }
 
 void launch_level0(Ctx& c, int which, const uint8_t* d_img, int pitch);
 void launch_pyramid(Ctx& c);

@@ -478,8 +478,9 @@ void launch_order(Ctx& c, int l)
     // tiles
     k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
     k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
-    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0,
-                                   layer_tile_floats(c, l), c.ustart_flag);
+    c.layer_tf[l] = layer_tile_floats(c, l);   // the aggregation of this layout uses the same size
+    k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0, c.layer_tf[l],
+                                   c.ustart_flag);
     scan_u32(c.ustart_flag, c.uid, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NUNITS), s);
     k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
     cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);

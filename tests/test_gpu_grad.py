@@ -139,7 +139,7 @@ def test_soft_argmin_l1_and_autograd_chain():
             return float(np.abs(dr - o["gt"].ravel())[valid_np.ravel()].mean()), dr
         Lr, dr = Lfull(E64, GAMMA)
         assert np.abs(d.detach().cpu().numpy().ravel() - dr).max() < 1e-3
-        assert float(loss) == pytest.approx(Lr, rel=1e-4)
+        assert float(loss.detach()) == pytest.approx(Lr, rel=1e-4)
         h = 1e-6
         gEg = E.grad.cpu().numpy().reshape(-1, X)
         for _ in range(4):
