@@ -204,7 +204,7 @@ def test_cost_parameter_and_gamma_gradients_match_central_differences():
             Eo = oracle.cost_volume(o["Li"], o["gL"], o["Ri"], o["gR"], 0, X, *th)
             return _loss_oracle(o, Eo, o["wn"], gam, valid_np)
         th0 = _theta32(THETA)
-        assert float(loss) == pytest.approx(Lfull(th0, GAMMA), rel=1e-4)
+        assert float(loss.detach()) == pytest.approx(Lfull(th0, GAMMA), rel=1e-4)
         h = 1e-6
         g = theta.grad.cpu().numpy()
         for k in range(3):
@@ -239,7 +239,7 @@ def test_edge_weights_as_an_input():
         torch.cuda.synchronize()
         E64 = o["E"].astype(np.float32).astype(np.float64)
         wn = oracle.node_weights(W, H, o["parent"], w_np.astype(np.float64))
-        assert float(loss) == pytest.approx(_loss_oracle(o, E64, wn, GAMMA, valid_np), rel=1e-4)
+        assert float(loss.detach()) == pytest.approx(_loss_oracle(o, E64, wn, GAMMA, valid_np), rel=1e-4)
         gw = w.grad.cpu().numpy()
         tree = np.zeros(2 * H * W, bool)
         for v in np.flatnonzero(o["parent"] >= 0):
