@@ -115,7 +115,9 @@ typedef struct {
  *   agg_ctas_per_sm        aggregation CTAs per SM at most, 1..8 [8] (each
  *                          kernel also stops at its own occupancy: 4 CTAs
  *                          of 2048-float tiles, 7 of 1024, 5 of 512)
- *   region_ctas_per_sm     first-pass CTAs per SM on HDP layers, 1..4 [4]
+ *   region_ctas_per_sm     region-engine CTAs per SM, 1..4 [1] (the CTA with
+ *                          the largest region is the critical path: alone on
+ *                          its SM it runs faster)
  *   big_class_edges        first pass of big full-range layers: a weight class
  *                          with at least this many edges runs as a grid
  *                          Boruvka, smaller ones in shared-memory windows,

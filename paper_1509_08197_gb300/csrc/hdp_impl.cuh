@@ -62,7 +62,7 @@ struct CostK {
 
 struct Ctx {
     hdp_params p;
-    hdp_tuning tune = {AGG_CTAS_DEFAULT, 4, 2048, 131072, 4096, 1 << 24, SMALL_TILE_NODES, SMALL_TILE_NODES_HDP,
+    hdp_tuning tune = {AGG_CTAS_DEFAULT, 1, 2048, 131072, 4096, 1 << 24, SMALL_TILE_NODES, SMALL_TILE_NODES_HDP,
                        COL_MIN_KP};
     int layer_tf[HDP_MAX_LEVELS] = {};   // tile size each layer's layout was built with (launch_order)
     cudaStream_t s = nullptr;

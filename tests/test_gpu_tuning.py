@@ -28,7 +28,7 @@ def test_knobs_do_not_change_results(tree):
     ctx = hdp.hdp_create(hdp.HDPParams(width=W, height=H, max_disp=79, levels=3, tree=tree))
     try:
         t0 = hdp.hdp_get_tuning(ctx)
-        assert t0.as_dict() == dict(agg_ctas_per_sm=8, region_ctas_per_sm=4, big_class_edges=2048,
+        assert t0.as_dict() == dict(agg_ctas_per_sm=8, region_ctas_per_sm=1, big_class_edges=2048,
                                     one_cta_nodes=131072, boruvka_edges_per_cta=4096, region_max_nodes=1 << 24,
                                     tile_small_nodes=1 << 17, tile_small_nodes_hdp=1 << 19, col_min_labels=64)
         ref = _match(ctx, L, R, H, W)
