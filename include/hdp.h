@@ -317,6 +317,10 @@ int hdp_batch_graph_launch(hdp_ctx* ctx0);
  * The first call allocates four volume-sized buffers and the edge-weight
  * buffer in the context. */
 int hdp_aggregate_fwd(hdp_ctx* ctx, const float* d_E, float* d_C);
+/* The layer whose forest and layout are loaded (the one the calls above and
+ * below work on; volumes there hold width_l * height_l * (d_l + 1) floats),
+ * or -1 before hdp_build_trees.  No counterpart in the paper. */
+int hdp_tree_level(const hdp_ctx* ctx);
 int hdp_aggregate_bwd(hdp_ctx* ctx, const float* d_E, const float* d_gC, float* d_gE, float* d_gw, float* d_ggamma);
 int hdp_set_gamma(hdp_ctx* ctx, float gamma);
 int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const uint8_t* d_valid, float T,

@@ -144,6 +144,7 @@ def load(path: str = LIB_PATH):
         "hdp_cost_volume": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
         "hdp_cost_volume_bwd": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P]),
         "hdp_set_edge_weights": (I, [P, P]),
+        "hdp_tree_level": (I, [P]),
         "hdp_match_batch": (I, [P, I, P, P, P, P]),
         "hdp_batch_graph_capture": (I, [P, I, P, P, P, P, P]),
         "hdp_batch_graph_launch": (I, [P]),
@@ -470,14 +471,47 @@ def _optr(t):
     return None if t is None else _ptr(t)
 
 
+def hdp_tree_level(ctx: Context) -> int:
+    """The layer whose forest and layout are loaded, or -1 before hdp_build_trees."""
+    return int(load().hdp_tree_level(ctx.handle))
+
+
+def _loaded(ctx: Context):
+    """(N, X) of the loaded layer: pixels and labels of its volumes."""
+    l = hdp_tree_level(ctx)
+    if l < 0:
+        raise HDPError("no tree loaded (call hdp_build_trees)")
+    W, H, d = ctx.dims[l]
+    return W * H, d + 1
+
+
+def _f32n(t, n, what):
+    """A float32 CUDA tensor of exactly n elements (the kernels index n of them)."""
+    p = _f32(t)
+    if t.numel() != n:
+        raise TypeError(f"{what}: expected {n} float32 elements, got {t.numel()}")
+    return p
+
+
+def _u8n(t, n, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or t.numel() != n:
+        raise TypeError(f"{what}: expected a uint8 CUDA tensor of {n} elements")
+    return _ptr(t)
+
+
 def hdp_aggregate_fwd(ctx: Context, E, C):
     """C = A E over the loaded full-range tree; E, C: float32 (H, W, X) CUDA tensors."""
-    _check(ctx, load().hdp_aggregate_fwd(ctx.handle, _ptr(E), _ptr(C)), "hdp_aggregate_fwd")
+    N, X = _loaded(ctx)
+    _check(ctx, load().hdp_aggregate_fwd(ctx.handle, _f32n(E, N * X, "E"), _f32n(C, N * X, "C")),
+           "hdp_aggregate_fwd")
 
 
 def hdp_aggregate_bwd(ctx: Context, E, gC, gE, gw, ggamma):
     """dL/dE (H, W, X), dL/dw per grid edge id (2*H*W,), dL/dgamma (1,) from dL/dC."""
-    _check(ctx, load().hdp_aggregate_bwd(ctx.handle, _ptr(E), _ptr(gC), _ptr(gE), _ptr(gw), _ptr(ggamma)),
+    N, X = _loaded(ctx)
+    _check(ctx, load().hdp_aggregate_bwd(ctx.handle, _f32n(E, N * X, "E"), _f32n(gC, N * X, "gC"),
+                                         _f32n(gE, N * X, "gE"), _f32n(gw, 2 * N, "gw"), _f32n(ggamma, 1, "ggamma")),
            "hdp_aggregate_bwd")
 
 
@@ -486,8 +520,12 @@ def hdp_set_gamma(ctx: Context, gamma: float):
 
 
 def hdp_soft_argmin_l1(ctx: Context, C, gt=None, valid=None, T=1.0, disp=None, loss=None, gC=None):
-    _check(ctx, load().hdp_soft_argmin_l1(ctx.handle, _ptr(C), _optr(gt), _optr(valid), float(T), _optr(disp),
-                                          _optr(loss), _optr(gC)), "hdp_soft_argmin_l1")
+    N, X = _loaded(ctx)
+    _check(ctx, load().hdp_soft_argmin_l1(ctx.handle, _f32n(C, N * X, "C"), None if gt is None else _f32n(gt, N, "gt"),
+                                          None if valid is None else _u8n(valid, N, "valid"), float(T),
+                                          None if disp is None else _f32n(disp, N, "disp"),
+                                          None if loss is None else _f32n(loss, 1, "loss"),
+                                          None if gC is None else _f32n(gC, N * X, "gC")), "hdp_soft_argmin_l1")
 
 
 def _f32(t):
@@ -499,20 +537,25 @@ def _f32(t):
 
 def hdp_cost_volume(ctx: Context, alpha: float, tau_c: float, tau_g: float, E):
     """E (H, W, X) float32 CUDA tensor <- the matching cost with real-valued parameters."""
-    _check(ctx, load().hdp_cost_volume(ctx.handle, float(alpha), float(tau_c), float(tau_g), _f32(E)),
+    N, X = _loaded(ctx)
+    _check(ctx, load().hdp_cost_volume(ctx.handle, float(alpha), float(tau_c), float(tau_g), _f32n(E, N * X, "E")),
            "hdp_cost_volume")
 
 
 def hdp_cost_volume_bwd(ctx: Context, alpha: float, tau_c: float, tau_g: float, gE, gparams):
     """gparams (3,) float32 CUDA tensor <- dL/d(alpha, tau_c, tau_g) from gE = dL/dE."""
-    _check(ctx, load().hdp_cost_volume_bwd(ctx.handle, float(alpha), float(tau_c), float(tau_g), _f32(gE),
-                                           _f32(gparams)), "hdp_cost_volume_bwd")
+    N, X = _loaded(ctx)
+    _check(ctx, load().hdp_cost_volume_bwd(ctx.handle, float(alpha), float(tau_c), float(tau_g),
+                                           _f32n(gE, N * X, "gE"), _f32n(gparams, 3, "gparams")),
+           "hdp_cost_volume_bwd")
 
 
 def hdp_set_edge_weights(ctx: Context, w=None):
     """Real-valued weights per grid edge id (float32 CUDA tensor of 2*H*W) for the loaded tree, or None for the
     image's own."""
-    _check(ctx, load().hdp_set_edge_weights(ctx.handle, None if w is None else _f32(w)), "hdp_set_edge_weights")
+    N, _ = _loaded(ctx)
+    _check(ctx, load().hdp_set_edge_weights(ctx.handle, None if w is None else _f32n(w, 2 * N, "w")),
+           "hdp_set_edge_weights")
 
 
 def _batch_arrays(ctxs, lefts, rights, outs):
@@ -553,4 +596,4 @@ def exported_symbols():
             "hdp_graph_launch", "hdp_match_noalloc", "hdp_aggregate_fwd", "hdp_aggregate_bwd", "hdp_set_gamma",
             "hdp_soft_argmin_l1", "hdp_match_batch", "hdp_batch_graph_capture", "hdp_batch_graph_launch",
             "hdp_gt_down", "hdp_offset_hist", "hdp_gmm_em", "hdp_refine", "hdp_cost_volume", "hdp_cost_volume_bwd",
-            "hdp_set_edge_weights"]
+            "hdp_set_edge_weights", "hdp_tree_level"]

@@ -1140,6 +1140,12 @@ extern "C" int hdp_gmm_em(const unsigned long long* d_hist, int range, int K, in
 }
 
 // ------------------------------------------------------ differentiable path ---
+extern "C" int hdp_tree_level(const hdp_ctx* ctx)
+{
+    if (!ctx) return HDP_ERR_ARG;
+    return ctx->c.built ? ctx->c.tree_level : -1;
+}
+
 static int grad_ready(hdp_ctx* ctx)
 {
     Ctx& c = ctx->c;

@@ -175,6 +175,11 @@ def test_cost_volume_matches_oracle():
         assert np.abs(E.cpu().numpy().reshape(-1, X) - ref).max() <= 2e-6 * max(1.0, np.abs(ref).max())
         with pytest.raises(hdp.HDPError):
             hdp.hdp_cost_volume(ctx, 0.5, -1.0, 2.0, E)    # a negative truncation is refused
+        assert hdp.hdp_tree_level(ctx) == 0
+        with pytest.raises(TypeError):                    # a volume of the wrong size never reaches the kernels
+            hdp.hdp_cost_volume(ctx, *THETA, E[:-1].contiguous())
+        with pytest.raises(TypeError):
+            hdp.hdp_set_edge_weights(ctx, torch.zeros(2 * H * W - 1, device=dev))
     finally:
         hdp.hdp_destroy(ctx)
 
