@@ -20,11 +20,13 @@ import numpy as np
 import torch
 
 from . import (hdp_aggregate_bwd, hdp_aggregate_fwd, hdp_cost_volume, hdp_cost_volume_bwd, hdp_get_stage,
-               hdp_set_edge_weights, hdp_set_gamma, hdp_soft_argmin_l1)
+               hdp_set_edge_weights, hdp_set_gamma, hdp_soft_argmin_l1, hdp_tree_level)
 
 
 def _layer_shape(ctx, level=None):
-    l = ctx.top if level is None else level
+    l = hdp_tree_level(ctx) if level is None else level
+    if l < 0:
+        raise RuntimeError("no tree loaded (call hdp_build_trees)")
     W, H, d = ctx.dims[l]
     return l, H, W, d + 1
 
