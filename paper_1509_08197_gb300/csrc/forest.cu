@@ -900,7 +900,7 @@ __global__ void __launch_bounds__(LW_THREADS, 1) k_fh_hybrid(ForestArgs a, int* 
 // region depends only on the region's own edges, in the strict order.  The
 // edges are stably sorted by region (keeping the strict order inside each);
 // persistent CTAs take whole regions and resolve them window by window.
-#define RG_THREADS 512
+#define RG_THREADS 1024
 #define RG_EDGES 2048
 #define RG_SMALL (RG_EDGES / 2)   // regions of at most this many edges share windows
 typedef LocalWinT<RG_EDGES> RegionWin;
@@ -1074,7 +1074,7 @@ __host__ __device__ constexpr size_t regions_smem()
 // window per bucket of small regions.  Layers without a risky edge: the
 // segment tree's first pass (engine 5).  Risky layers: every pass, region by
 // region (engine 7).
-__global__ void __launch_bounds__(RG_THREADS) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
+__global__ void __launch_bounds__(RG_THREADS, 1) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
                                                            const int* d_nsmall, const int* d_nsmall_regions,
                                                            const int* wb_lo, const int* wb_hi, int* loc, int* ticket)
 {
