@@ -271,9 +271,10 @@ __device__ __forceinline__ int lw_find(int* parent, int x)
     return x;
 }
 
-// Union-find root in global memory.  L2 = false: plain loads (only this CTA
-// writes the union-find while the kernel runs); L2 = true: through L2 (other
-// SMs wrote it before the last grid barrier).
+// Union-find root in global memory.  L2 = false: plain loads (no other CTA
+// writes the entries this CTA reads while the kernel runs: one CTA, or
+// disjoint regions); L2 = true: through L2 (other SMs wrote them before the
+// last grid barrier).
 template <bool L2>
 __device__ __forceinline__ int g_find(int* parent, int v)
 {
@@ -1061,7 +1062,7 @@ __device__ void region_risky(const ForestArgs& a, const uint32_t* rkeys, int* lo
     for (int pass = 0; pass < a.passes; ++pass) {
         const long long kq = a.crit_first && pass == 0 ? a.kq : (1LL << 60);
         for (int base = s; base < e; base += RK_EDGES)
-            lw_window<true, RG_THREADS, RK_EDGES, true>(a, rkeys, loc, S, base, min(RK_EDGES, e - base), ST, kq);
+            lw_window<false, RG_THREADS, RK_EDGES, true>(a, rkeys, loc, S, base, min(RK_EDGES, e - base), ST, kq);
     }
 }
 
@@ -1071,7 +1072,11 @@ __host__ __device__ constexpr size_t regions_smem()
 }
 
 // Work items: every big region (its windows in order, on one CTA), then one
-// window per bucket of small regions.  Layers without a risky edge: the
+// window per bucket of small regions.  The windows read the union-find with
+// plain (L1-cached) loads: regions are disjoint, so no other CTA writes an
+// entry this CTA reads while the kernel runs (words of other regions that
+// share a cache line are never read here), and earlier kernels' writes are
+// visible by launch order.  Layers without a risky edge: the
 // segment tree's first pass (engine 5).  Risky layers: every pass, region by
 // region (engine 7).
 __global__ void __launch_bounds__(RG_THREADS, 1) k_fh_regions(ForestArgs a, const uint32_t* rkeys, const int* d_nvalid,
@@ -1098,13 +1103,13 @@ __global__ void __launch_bounds__(RG_THREADS, 1) k_fh_regions(ForestArgs a, cons
                 region_risky(a, rkeys, loc, rg_raw, s, e);
             } else {
                 for (int base = s; base < e; base += RG_EDGES)
-                    lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
+                    lw_window<false, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, base, min(RG_EDGES, e - base));
             }
         } else if (t - nbig < nbuckets) {
             const int lo = wb_lo[t - nbig], hi = wb_hi[t - nbig];
             if (lo < hi) {
                 if (mode) region_risky(a, rkeys, loc, rg_raw, lo, hi);
-                else lw_window<true, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, lo, hi - lo);
+                else lw_window<false, RG_THREADS, RG_EDGES>(a, rkeys, loc, S, lo, hi - lo);
             }
         } else {
             break;
