@@ -35,18 +35,12 @@ __device__ __forceinline__ int cost_px(uint2 a, uint2 b, const CostK& k)
     return k.A * min(sum, k.Tc) + k.B * min(dg, k.Tg);
 }
 
+// one centre, by one warp (sb: the warp's box in shared memory)
 template <typename P>
-__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const P* __restrict__ L, const P* __restrict__ R, int W,
-                                                         int H, int dl, CostK ck, unsigned long long* hist)
+__device__ __forceinline__ void prior_centre(const P* __restrict__ L, const P* __restrict__ R, int W, int dl,
+                                             const CostK& ck, unsigned long long* hist, int na, int wid, P* sb)
 {
-    // the 25 pixels of the box in the reference view are the same for every
-    // label: one copy per warp in shared memory
-    __shared__ P box[PRIOR_THREADS / 32][25];
     const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int na = W / 5, nb = H / 5;
-    if (wid >= na * nb) return;   // whole warps leave together
-    P* sb = box[threadIdx.x >> 5];
     const int cx = 5 * (wid % na) + 2, cy = 5 * (wid / na) + 2;
     if (lane < 25) sb[lane] = L[(size_t)(cy + lane / 5 - 2) * W + cx + lane % 5 - 2];
     __syncwarp();
@@ -85,6 +79,23 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const P* __restrict__ L
     if (lane == 0 && bx == dL) atomicAdd(hist + dL, 1ull);
 }
 
+// warps stride over the centres, so the grid may be smaller than the centres
+template <typename P>
+__global__ void __launch_bounds__(PRIOR_THREADS) k_prior(const P* __restrict__ L, const P* __restrict__ R, int W,
+                                                         int H, int dl, CostK ck, unsigned long long* hist)
+{
+    // the 25 pixels of the box in the reference view are the same for every
+    // label: one copy per warp in shared memory
+    __shared__ P box[PRIOR_THREADS / 32][25];
+    const int na = W / 5, nb = H / 5;
+    P* sb = box[threadIdx.x >> 5];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wid < na * nb; wid += nw) {   // whole warps
+        prior_centre(L, R, W, dl, ck, hist, na, wid, sb);
+        __syncwarp();
+    }
+}
+
 __global__ void k_prior_finish(const unsigned long long* hist, int dl, long long* prior, int uniform)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,7 +111,12 @@ void launch_prior(Ctx& c, int l, cudaStream_t s)
     if (!uniform) {
         int centres = (d.W / 5) * (d.H / 5);
         if (centres > 0) {
-            const int blocks = cdiv(centres * 32, PRIOR_THREADS);
+            // on the side stream at most four blocks per SM: the priors are
+            // needed layers later, and a full grid shares every SM with the
+            // latency-bound kernels of the coarser layers running meanwhile
+            // (the top layer's one-CTA first pass above all)
+            int blocks = cdiv(centres * 32, PRIOR_THREADS);
+            if (s == c.s2) blocks = min(blocks, 4 * c.num_sms);
             if (l == 0)
                 k_prior<uint2><<<blocks, PRIOR_THREADS, 0, s>>>(c.pk0[0], c.pk0[1], d.W, d.H, d.d,
                                                                   cost_consts(c, l), hist);
