@@ -111,12 +111,12 @@ void launch_prior(Ctx& c, int l, cudaStream_t s)
     if (!uniform) {
         int centres = (d.W / 5) * (d.H / 5);
         if (centres > 0) {
-            // on the side stream at most four blocks per SM: the priors are
+            // on the side stream at most three blocks per SM: the priors are
             // needed layers later, and a full grid shares every SM with the
             // latency-bound kernels of the coarser layers running meanwhile
             // (the top layer's one-CTA first pass above all)
             int blocks = cdiv(centres * 32, PRIOR_THREADS);
-            if (s == c.s2) blocks = min(blocks, 4 * c.num_sms);
+            if (s == c.s2) blocks = min(blocks, 3 * c.num_sms);
             if (l == 0)
                 k_prior<uint2><<<blocks, PRIOR_THREADS, 0, s>>>(c.pk0[0], c.pk0[1], d.W, d.H, d.d,
                                                                   cost_consts(c, l), hist);
