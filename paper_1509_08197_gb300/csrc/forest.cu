@@ -1117,6 +1117,33 @@ __global__ void __launch_bounds__(RG_THREADS, 1) k_fh_regions(ForestArgs a, cons
     }
 }
 
+// k_forest_init plus the stage's other starting state in one launch: no
+// forest edge yet, the counters, the engine and window statistics, and the
+// grid barrier's state (the error word is kept)
+__global__ void k_forest_start(int* parent, int* size, int* intw, int* best, int* best2, int* minid, int* loc,
+                               uint8_t* in_tree, int* ints, DevStatus* st, int N)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v == 0) {
+        for (int k = 0; k < 5; ++k) ints[IDX_CTR0 + k] = 0;
+        ints[IDX_ENGINE] = 0;
+        ints[IDX_DRROUNDS] = 0;
+        ints[IDX_DRWINDOWS] = 0;
+        st->bar_count = 0u;
+        st->bar_gen = 0u;
+    }
+    if (v >= N) return;
+    loc[v] = INT_MAX;
+    parent[v] = v;
+    size[v] = 1;
+    intw[v] = 0;
+    best[v] = INT_MAX;
+    best2[v] = INT_MAX;
+    minid[v] = INT_MAX;
+    in_tree[2 * v] = 0;
+    in_tree[2 * v + 1] = 0;
+}
+
 __global__ void k_fill_int_f(int* p, int n, int v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1342,12 +1369,8 @@ void launch_forest(Ctx& c, int l, int hdp)
     a.st = c.st;
     a.stats = c.ints + IDX_DRROUNDS;
 
-    k_forest_init<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof, N);
-    cudaMemsetAsync(c.in_tree, 0, 2 * (size_t)N, c.s);
-    cudaMemsetAsync(c.ints + IDX_CTR0, 0, 5 * sizeof(int), c.s);
-    cudaMemsetAsync(c.st, 0, 2 * sizeof(unsigned), c.s);   // barrier state (keeps err)
-    cudaMemsetAsync(c.ints + IDX_ENGINE, 0, sizeof(int), c.s);
-    cudaMemsetAsync(c.ints + IDX_DRROUNDS, 0, 2 * sizeof(int), c.s);   // and IDX_DRWINDOWS
+    k_forest_start<<<cdiv(N, 256), 256, 0, c.s>>>(c.parent, c.csize, c.intw, c.best, c.best2, c.minid, c.rootof,
+                                                  c.in_tree, c.ints, c.st, N);
 
     const bool st_tree = c.p.tree == HDP_TREE_ST;
     // layers below tune.one_cta_nodes run the first pass in one CTA (windowed

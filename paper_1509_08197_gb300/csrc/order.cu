@@ -30,11 +30,6 @@ __device__ __forceinline__ int arc_index(const uint32_t* aoff, const uint8_t* ad
 }
 __device__ __forceinline__ int first_dir(unsigned m) { return __ffs(m) - 1; }
 
-__global__ void k_set_ints(int* dst, int a, int b)
-{
-    dst[0] = a;
-    dst[1] = b;
-}
 
 __global__ void k_arc_count(const uint8_t* adj, int N, uint32_t* cnt)
 {
@@ -392,10 +387,30 @@ __global__ void k_tile_fill(const uint32_t* flag, const uint32_t* tid, const uin
     count_by_key(lvl_count, lv);
 }
 
-__global__ void k_fill_int(int* p, int n, int v)
+
+// The stage's counters and tables in one launch (none is touched before its
+// use below): the scan lengths N and N + 1 (with the slots after them, the
+// splitter count among them, zeroed), the tree count, slot N of both
+// ping-pong key buffers (the light-child counts' total), the run starts and
+// the per-level tile tables.
+__global__ void k_order_init(int* ints, int N, uint32_t* ka, uint32_t* kb, int* runstart, int* lvl_first,
+                             int* lvl_count)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        ints[IDX_N] = N;
+        ints[IDX_N + 1] = 0;
+        ints[IDX_TMP1] = N + 1;
+        ints[IDX_TMP1 + 1] = 0;
+        ints[IDX_NTREES] = 0;
+        ka[N] = 0u;
+        kb[N] = 0u;
+    }
+    if (i < 2048) runstart[i] = INT_MAX;
+    if (i < MAX_LIGHT_LEVELS) {
+        lvl_first[i] = INT_MAX;
+        lvl_count[i] = 0;
+    }
 }
 
 void launch_order(Ctx& c, int l)
@@ -405,7 +420,9 @@ void launch_order(Ctx& c, int l)
     cudaStream_t s = c.s;
     const int g = cdiv(N, 256);
     int* dN = c.ints + IDX_N;
-    k_set_ints<<<1, 1, 0, s>>>(dN, N, 0);
+    static_assert(MAX_LIGHT_LEVELS <= 2048, "one launch covers the tables");
+    static_assert(IDX_TMP1 + 1 == IDX_TMP2, "the splitter count follows the second scan length");
+    k_order_init<<<cdiv(2048, 256), 256, 0, s>>>(c.ints, N, c.ka, c.kb, c.runstart, c.lvl_first, c.lvl_count);
 
     // arcs and their successors
     uint32_t* cnt = c.ka;
@@ -415,8 +432,7 @@ void launch_order(Ctx& c, int l)
     // (layers of 64K..128K nodes take 1 in 32, so that their segment list is
     // short enough for the one-block ranking)
     const int lg = N >= (1 << 19) ? 5 : N >= (1 << 17) ? 4 : N >= (1 << 16) ? 5 : 3;
-    int* nspl = c.ints + IDX_TMP2;
-    cudaMemsetAsync(nspl, 0, sizeof(int), s);
+    int* nspl = c.ints + IDX_TMP2;   // zeroed by k_order_init
     int* sid = c.val;
     int* spl = c.succ2;
     int *owner = c.listA, *offs = c.listB, *rs = c.raA, *rv = c.rbA, *rs2 = c.raB, *rv2 = c.rbB;
@@ -452,7 +468,6 @@ void launch_order(Ctx& c, int l)
     k_tour_fill<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tpos_up, c.tbase, c.vals4, N, c.ints + IDX_NARCS, c.tour,
                                   c.st);
     scan_i4_inclusive(c.tour, c.tour, c.ints + IDX_NARCS, 2 * N, c.scan4, s);
-    cudaMemsetAsync(c.ints + IDX_NTREES, 0, sizeof(int), s);
     k_keys<<<g, 256, 0, s>>>(c.dtroot, c.tpos_down, c.tbase, c.nbase, c.tour, N, c.depth, c.pre2, c.pre3, c.light,
                              c.ints + IDX_NTREES);
 
@@ -468,22 +483,17 @@ void launch_order(Ctx& c, int l)
     k_rows<<<g, 256, 0, s>>>(ksorted, c.lay, c.rootof, c.par, c.pdir, c.weights, c.vals4, N, d.W, inv_scale, c.rowof,
                              c.kp, c.rdt, c.rs, lccnt, c.hdir, c.adj);
     // N + 1 entries so that lcoff[N] holds the total
-    int* dN1 = c.ints + IDX_TMP1;
-    k_set_ints<<<1, 1, 0, s>>>(dN1, N + 1, 0);
-    cudaMemsetAsync(lccnt + N, 0, sizeof(uint32_t), s);
+    int* dN1 = c.ints + IDX_TMP1;   // N + 1, and lccnt[N] = 0, from k_order_init
     scan_u32(lccnt, c.lcoff, dN1, N + 1, true, c.scan, (uint32_t*)(c.ints + IDX_NLC), s);
     k_rows2<<<g, 256, 0, s>>>(c.lay, c.rowof, c.par, c.pdir, c.hdir, c.adj, c.lcoff, N, d.W, c.prow, c.lcrow);
     scan_u32((const uint32_t*)c.kp, c.roff, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_K), s);
 
     // tiles
-    k_fill_int<<<cdiv(2048, 256), 256, 0, s>>>(c.runstart, 2048, INT_MAX);
     k_runstart<<<g, 256, 0, s>>>(ksorted, N, c.runstart);
     c.layer_tf[l] = layer_tile_floats(c, l);   // the aggregation of this layout uses the same size
     k_tile_flags<<<g, 256, 0, s>>>(ksorted, c.runstart, N, c.p.storage == HDP_STORE_FP16 ? 4 : 0, c.layer_tf[l],
                                    c.ustart_flag);
     scan_u32(c.ustart_flag, c.uid, dN, N, true, c.scan, (uint32_t*)(c.ints + IDX_NUNITS), s);
-    k_fill_int<<<1, MAX_LIGHT_LEVELS, 0, s>>>(c.lvl_first, MAX_LIGHT_LEVELS, INT_MAX);
-    cudaMemsetAsync(c.lvl_count, 0, sizeof(int) * MAX_LIGHT_LEVELS, s);
     k_tile_fill<<<g, 256, 0, s>>>(c.ustart_flag, c.uid, ksorted, N, c.ubeg, c.lvl_first, c.lvl_count, (int)c.max_tiles,
                                   c.st);
 
