@@ -11,21 +11,30 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("depths", ["mixed", "equal"])
+@pytest.mark.parametrize("depths", ["mixed", "equal", "groups"])
 def test_batch_equals_one_at_a_time(depths):
     # mixed depths: every pair runs its own chain; equal depths: level by level,
-    # one aggregation launch per pass and tile class over every pair's tiles
+    # one aggregation launch per pass and tile class over the tiles of every
+    # pair of a group of one geometry (here every pair is its own group);
+    # groups: two pairs of each of two geometries (different scenes and
+    # ranges), so each group's launches take the tiles of two pairs
     dev = torch.device("cuda:0")
-    specs = [("tiny", dict()), ("tiny", dict(width=77, height=41, max_disp=31)),
-             ("tiny", dict(width=120, height=90, max_disp=47)), ("third", dict())]
+    if depths == "groups":
+        specs = [("tiny", dict()), ("tiny", dict(width=77, height=41, max_disp=31)),
+                 ("tiny", dict(max_disp=23)), ("tiny", dict(width=77, height=41, max_disp=19))]
+    else:
+        specs = [("tiny", dict()), ("tiny", dict(width=77, height=41, max_disp=31)),
+                 ("tiny", dict(width=120, height=90, max_disp=47)), ("third", dict())]
     pairs, params = [], []
     for i, (name, over) in enumerate(specs):
         p = workload_pair(name, index=i, **over)
         pairs.append(p)
         H, W, _ = p.left.shape
         levels = (3 if W < 200 else 4) if depths == "mixed" else 3
+        # groups: the 96x72 pairs FP32 with MST, the 77x41 pairs FP16 with ST (one geometry per group)
+        storage = "fp16" if (i == 3 if depths != "groups" else i % 2 == 1) else "fp32"
         params.append(hdp.HDPParams(width=W, height=H, max_disp=p.max_disp, levels=levels,
-                                    tree="mst" if i % 2 == 0 else "st", storage="fp16" if i == 3 else "fp32"))
+                                    tree="mst" if i % 2 == 0 else "st", storage=storage))
     # two contexts on caller streams, two that own theirs
     ctxs = [hdp.hdp_create(hp, torch.cuda.Stream(device=dev)) if i < 2 else hdp.hdp_create_own_stream(hp)
             for i, hp in enumerate(params)]
