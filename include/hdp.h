@@ -341,12 +341,13 @@ int hdp_soft_argmin_l1(hdp_ctx* ctx, const float* d_C, const float* d_gt, const 
  *   alpha, tau_c, tau_g must be finite and tau_c, tau_g >= 0 (HDP_ERR_ARG);
  *   unlike hdp_params they need not sit on the 1/20, 1/3, 1/6 grids.
  *   hdp_set_edge_weights: real-valued weights for the loaded tree's edges,
- *     d_w[e] per grid edge id e (2 * width * height floats, intensity units,
- *     copied), so the similarities become exp(-d_w[e] / gamma); NULL returns
- *     to the image's integer weights.  The tree is not rebuilt.  Every later
- *     aggregation on this tree uses them (hdp_aggregate_fwd/bwd, whose
- *     dL/dgamma then sums d_w[e] dL/dw[e], hdp_set_gamma, hdp_match on the
- *     same layer) until hdp_build_trees loads a tree again.
+ *     d_w[e] per grid edge id e of the loaded layer (2 * width_l * height_l
+ *     floats, intensity units, copied), so the similarities become
+ *     exp(-d_w[e] / gamma); NULL returns to the image's integer weights.  The
+ *     tree is not rebuilt.  Every later aggregation on this tree uses them
+ *     (hdp_aggregate_fwd/bwd, whose dL/dgamma then sums d_w[e] dL/dw[e],
+ *     hdp_set_gamma, hdp_match on the same layer) until a tree is built again
+ *     (hdp_build_trees, or a run of another layer).
  * These calls, like hdp_aggregate_fwd, enqueue on the context's stream and
  * return without waiting. */
 int hdp_cost_volume(hdp_ctx* ctx, float alpha, float tau_c, float tau_g, float* d_E);
